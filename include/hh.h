@@ -1,0 +1,156 @@
+/*
+ * hh.h -- C ABI of the GB300 multipreconditioned directional-sweep Helmholtz solver.
+ *
+ * Problem (Section 1, Eq. (1a)-(1b)):  Delta u + k^2 u = f in (0,1)^2,
+ * du/dn - i k u = 0 on the boundary, discretised by P1 finite elements on the uniform
+ * right-triangle mesh with n x n cells (every cell cut along its SW-NE diagonal).
+ * Unknowns: the (n+1)^2 nodal values, node (i, j) at (i h, j h), h = 1/n, stored at
+ * index g = j * (n + 1) + i.  The linear system is A u = b with
+ * A = K - k^2 M - i k M_Gamma and b = -M f_I (load vector of the source).
+ *
+ * Preconditioners (Section 2, Eqs. (2)-(4)): for every selected direction d a double sweep
+ * (forward then backward block Gauss-Seidel) over N = strips non-overlapping strips of
+ * R = n / N node lines, the last strip visited owning one extra line.  The diagonal
+ * blocks are impedance-modified strip matrices: the strip's block of A whose cell layer on
+ * the already-swept side is replaced by the zeroth-order impedance condition of Eq. (4)
+ * (an approximate Schur complement of the block LU factorisation that a sweep is).
+ *
+ * Krylov method (Section 3): selective flexible multipreconditioned GMRES, x0 = 0, the t
+ * preconditioners applied concurrently every iteration; selection (Section 4): t = 2 ->
+ * each preconditioner gets the other one's new basis vector, t > 2 -> all get the sum.
+ *
+ * Data conventions for every vector argument:
+ *   complex128 interleaved (re, im) doubles, 2 * (n+1)^2 doubles per column, node order g;
+ *   several columns are stored one after the other (column stride 2 * (n+1)^2 doubles).
+ *   Pointers may be DEVICE pointers (cudaMalloc / torch CUDA tensors, on the handle's
+ *   device) or HOST pointers (pageable or pinned); host buffers are copied in and out by
+ *   the library inside the call.  The caller owns every buffer it passes.
+ *
+ * Errors: every entry point returns an hh_status; nothing is thrown across the ABI.  The
+ * message of the most recent failure in the calling thread is in hh_last_error().
+ */
+#ifndef HH_H
+#define HH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hh_handle hh_handle;
+typedef uint64_t hh_ticket;
+
+typedef enum {
+  HH_OK = 0,
+  HH_EINVAL = 1,       /* bad argument: n % strips != 0, R < 2, k <= 0, dirs == 0, NULL pointer, ... */
+  HH_ENOMEM = 2,       /* device allocation failed or the factors do not fit in free device memory */
+  HH_ENOCONV = 3,      /* maxit reached; x holds the best iterate */
+  HH_EBREAKDOWN = 4,   /* every new direction deflated before convergence; x holds the iterate */
+  HH_ENAN = 5,         /* NaN / Inf met in a norm */
+  HH_ETIMEOUT = 6,     /* a bounded device-side wait ran out; the kernel returned early */
+  HH_EPENDING = 7,     /* hh_poll: the ticket is not finished yet */
+  HH_ECUDA = 8         /* a CUDA runtime call failed */
+} hh_status;
+
+/* direction bits (Section 4 vocabulary: the direction of the FORWARD pass) */
+enum { HH_DIR_LR = 1, HH_DIR_RL = 2, HH_DIR_BT = 4, HH_DIR_TB = 8 };
+enum { HH_PREC_FP64 = 0, HH_PREC_FP32 = 1 };                 /* precision of factors + sweeps */
+enum { HH_SCHEME_AUTO = 0, HH_SCHEME_CROSS = 1, HH_SCHEME_SUM = 2 };
+
+typedef struct {
+  int precision;          /* HH_PREC_FP64 (default) or HH_PREC_FP32: complex64 strip factors and
+                             sweeps; the global residual, Gram-Schmidt and Hessenberg stay FP64 */
+  int scheme;             /* HH_SCHEME_AUTO: t=2 cross, t>2 sum */
+  int single_sweep;       /* 1: forward sweeps only (LR, RL, BT, TB of Section 4) */
+  int maxit;              /* iteration limit (default 200) */
+  double deflate_eta;     /* deflation threshold r_jj <= eta * ||w_j|| (default 1e-12) */
+  int bcr_depth;          /* reserved: 0 = block Thomas strip solves (the only value accepted) */
+  int64_t timeout_cycles; /* SM clock budget of every device-side wait (default 4e9) */
+  void* stream;           /* cudaStream_t to run on, or NULL for the handle's own stream */
+  int use_graph;          /* 1 (default): the Arnoldi step is replayed as a CUDA graph */
+  int profile;            /* 1: time every kernel class with CUDA events (hh_get_stats) */
+  int reserved[6];
+} hh_opts;
+
+typedef struct {
+  int iterations;             /* MPGMRES iterations (each adds up to t search directions) */
+  double rel_res_implicit;    /* |g_last| / ||b|| from the Hessenberg least-squares problem */
+  double rel_res_explicit;    /* ||b - A x|| / ||b|| recomputed in FP64 on the device */
+  double t_setup_ms, t_solve_ms;
+  hh_status status;
+} hh_result;
+
+typedef struct {
+  /* per kernel class: launches, summed device time (ms, only with opts.profile) and the
+     algorithmic bytes those launches must move (the roofline model of each kernel) */
+  int64_t sweep_launches;  double sweep_ms;  double sweep_bytes;
+  int64_t spmv_launches;   double spmv_ms;   double spmv_bytes;
+  int64_t gs_launches;     double gs_ms;     double gs_bytes;
+  int64_t setup_launches;  double setup_ms;  double setup_flops;
+  int64_t kernel_launches; /* every kernel this handle launched */
+  int64_t factor_bytes;    /* device bytes of the stored strip factors */
+  int factor_blocks;       /* distinct m x m blocks stored (R + 1) */
+  int m, ldf, columns;     /* nodes per line, padded leading dimension, sweep columns of last solve */
+  int64_t sweep_steps;     /* dependent block steps of one sweep launch */
+} hh_stats;
+
+/* Fill *o with the defaults listed above. */
+void hh_default_opts(hh_opts* o);
+
+/*
+ * Assemble nothing on the host: validate, allocate the factor store and run the strip
+ * setup on the device (Section 2: block LU of each strip; the Schur complements
+ * S_0 = D_bot, S_j = D_int - L S_{j-1}^{-1} U and their dense inverses).  Strips of equal
+ * size have equal matrices, so the R + 1 distinct m x m inverses are computed and stored
+ * once (m = n + 1).  dirs is a bitmask of HH_DIR_*; t = popcount(dirs).
+ * Errors: HH_EINVAL (n % strips, n / strips < 2, k <= 0, dirs == 0, n > 4096, out == NULL),
+ * HH_ENOMEM, HH_ECUDA, HH_ETIMEOUT.  On success *out owns device memory until hh_destroy.
+ */
+hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out);
+
+/* Solve A x = rhs to relative residual tol (Section 3, 4).  Blocking.  rhs, x: one column.
+ * x is written for HH_OK, HH_ENOCONV and HH_EBREAKDOWN; res may be NULL. */
+hh_status hh_solve(hh_handle* h, const double* rhs, double* x, double tol, hh_result* res);
+
+/* nrhs independent solves sharing every sweep launch (columns batched): rhs and x hold
+ * nrhs columns; res (may be NULL) receives nrhs results.  Returns the worst status. */
+hh_status hh_solve_batch(hh_handle* h, int nrhs, const double* rhs, double* x, double tol,
+                         hh_result* res);
+
+/* Asynchronous solve: queued on the handle's request loop (continuous batching: requests
+ * that share a handle join the next iteration's sweep launch as columns free up).
+ * rhs and x must stay valid until hh_poll returns something other than HH_EPENDING. */
+hh_status hh_submit(hh_handle* h, const double* rhs, double* x, double tol, hh_ticket* ticket);
+
+/* Never blocks.  HH_EPENDING while the ticket runs; otherwise the request's final status
+ * (and *res if res != NULL); a finished ticket can be polled once more, then it is freed. */
+hh_status hh_poll(hh_ticket ticket, hh_result* res);
+
+/* Load vector b = -M f_I of a sum of Gaussians (the benchmark source family of Section 4):
+ * src holds nsrc rows (x0, y0, sigma, amp_re, amp_im), HOST memory; rhs one column. */
+hh_status hh_assemble_rhs(hh_handle* h, int nsrc, const double* src, double* rhs);
+
+/* y = A x for ncols columns (FP64, matrix-free seven-point stencil of the P1 matrix). */
+hh_status hh_apply_operator(hh_handle* h, int ncols, const double* x, double* y);
+
+/* z = M_d^{-1} r for ncols columns and ONE direction bit (the handle's precision; a double
+ * sweep unless opts.single_sweep).  dir need not be in the handle's dirs. */
+hh_status hh_apply_preconditioner(hh_handle* h, uint32_t dir, int ncols, const double* r, double* z);
+
+/* Copy the stored inverse S_j^{-1} (j = 0..R) as complex128 row-major m x m into out. */
+hh_status hh_get_factor(hh_handle* h, int j, double* out);
+
+hh_status hh_get_stats(hh_handle* h, hh_stats* st);
+void hh_reset_stats(hh_handle* h);
+
+/* Release every device resource of the handle (pending tickets are cancelled). */
+void hh_destroy(hh_handle* h);
+
+/* Message of the last failure in this thread ("" if none).  Valid until the next call. */
+const char* hh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HH_H */

@@ -1,0 +1,135 @@
+// Shared device helpers: complex arithmetic, bounded grid barrier, P1 stencil coefficients.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hh.h"
+
+namespace hh {
+
+// ---------------------------------------------------------------- complex types
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+template <typename T> __host__ __device__ __forceinline__ T mk(double re, double im);
+template <> __host__ __device__ __forceinline__ float2 mk<float2>(double re, double im) {
+  return make_float2((float)re, (float)im);
+}
+template <> __host__ __device__ __forceinline__ double2 mk<double2>(double re, double im) {
+  return make_double2(re, im);
+}
+template <typename T> __host__ __device__ __forceinline__ T cadd(T a, T b) { T r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename T> __host__ __device__ __forceinline__ T csub(T a, T b) { T r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename T> __host__ __device__ __forceinline__ T cmul(T a, T b) {
+  T r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// acc += a * b
+template <typename T> __host__ __device__ __forceinline__ void cfma(T& acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename T> __host__ __device__ __forceinline__ void cfma_conj(T& acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+template <typename T, typename S> __host__ __device__ __forceinline__ T cscale(T a, S s) { T r; r.x = a.x * s; r.y = a.y * s; return r; }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ double2 to_d(double2 a) { return a; }
+
+template <typename T> __device__ __forceinline__ T shfl_down(T v, int o) {
+  T r; r.x = __shfl_down_sync(0xffffffffu, v.x, o); r.y = __shfl_down_sync(0xffffffffu, v.y, o); return r;
+}
+template <typename T> __device__ __forceinline__ T shfl_xor(T v, int o) {
+  T r; r.x = __shfl_xor_sync(0xffffffffu, v.x, o); r.y = __shfl_xor_sync(0xffffffffu, v.y, o); return r;
+}
+
+// ---------------------------------------------------------------- device error word
+enum DevErr { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_SINGULAR = 2, DEV_NAN = 3 };
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch.  *count starts at 0 for the
+// launch and only grows; `target` is the caller's running arrival target.  Every wait is
+// bounded by `budget` SM cycles: on expiry the device error word is set and false is
+// returned, so that every CTA leaves the kernel instead of spinning.
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned& target, int* err, long long budget) {
+  __shared__ int s_ok;
+  __syncthreads();
+  target += gridDim.x * gridDim.y;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_add(count, 1u);
+    long long t0 = clock64();
+    int ok = 1;
+    while (ld_acquire(count) < target) {
+      if (*(volatile int*)err != 0) { ok = 0; break; }
+      if (clock64() - t0 > budget) { atomicCAS(err, 0, (int)DEV_TIMEOUT); ok = 0; break; }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------- P1 stencil coefficients
+// Matrix A = K - k^2 M - i k M_Gamma on the (n+1)^2 grid, cells cut along SW-NE diagonals.
+// Right isosceles triangles with legs h: stiffness 1 at the right-angle vertex, 1/2 at the
+// two acute ones, -1/2 along a leg, 0 along the hypotenuse; mass h^2/12 (diag), h^2/24 (off);
+// boundary edge mass h/3 (diag), h/6 (off).
+//
+// A node line of type BOT has cells only above it (bottom boundary or a strip's facing
+// interface, both impedance), INT cells on both sides, TOP cells only below (impedance).
+enum LineType { LINE_BOT = 0, LINE_INT = 1, LINE_TOP = 2 };
+
+struct Coef {
+  double k, h;
+  int n;
+  // coupling of node (i, l) to (i, l-1): vertical edge shared by up to two triangles,
+  // plus the boundary edge mass on the sides x = 0, x = 1
+  __host__ __device__ double2 vert(int i) const {
+    int cnt = (i < n) + (i >= 1);
+    double re = cnt * (-0.5 - k * k * h * h / 24.0);
+    double im = (i == 0 || i == n) ? -k * h / 6.0 : 0.0;
+    return make_double2(re, im);
+  }
+  // coupling of node (i, l) to (i-1, l-1): the diagonal of one cell (hypotenuse of both halves)
+  __host__ __device__ double diag() const { return -k * k * h * h / 12.0; }
+  // coupling along a line between (i, l) and (i+1, l)
+  __host__ __device__ double2 horiz(int type) const {
+    int cnt = (type != LINE_TOP) + (type != LINE_BOT);
+    double re = cnt * (-0.5 - k * k * h * h / 24.0);
+    double im = (type != LINE_INT) ? -k * h / 6.0 : 0.0;
+    return make_double2(re, im);
+  }
+  // diagonal entry of node i on a line of the given type
+  __host__ __device__ double2 centre(int i, int type) const {
+    bool top = type == LINE_TOP, bot = type == LINE_BOT;
+    int kc = 0, ntri = 0, nbe = 0;
+    if (!top && i < n) { kc += 1; ntri += 2; }   // cell NE of the node: two acute corners
+    if (!top && i >= 1) { kc += 1; ntri += 1; }  // cell NW: one right-angle corner
+    if (!bot && i >= 1) { kc += 1; ntri += 2; }  // cell SW: two acute corners
+    if (!bot && i < n) { kc += 1; ntri += 1; }   // cell SE: one right-angle corner
+    if (bot || top) nbe += (i >= 1) + (i < n);
+    if (i == 0 || i == n) nbe += (!bot) + (!top);
+    double re = kc - k * k * h * h / 12.0 * ntri;
+    double im = -k * h / 3.0 * nbe;
+    return make_double2(re, im);
+  }
+};
+
+__host__ __device__ __forceinline__ int line_type(int l, int n) {
+  return l == 0 ? LINE_BOT : (l == n ? LINE_TOP : LINE_INT);
+}
+
+}  // namespace hh

@@ -1,0 +1,126 @@
+// Host-side engine: one per hh_handle.  Owns the device, stream, strip factors and the
+// Krylov slots; the kernels live in setup.cu, sweep.cu and krylov.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hh.h"
+#include "common.cuh"
+
+namespace hh {
+
+void set_error(const std::string& msg);
+
+// One step of the batched sweep (see sweep.cu): out line <- / -= F_f * x, where
+// x = Rin[base_line] + sign * C(src line), C = coupling to the line below (L) or above (U).
+struct SweepOp {
+  int f;          // factor block
+  int out_line;   // V line that receives the result
+  int out_sub;    // 0: V = z, 1: V -= z
+  int zsave;      // -1 or Zt slot that also receives z
+  int base_line;  // Rin line added to x, or -1
+  int cpl;        // 0 none, 1 lower (line below), 2 upper (line above)
+  int cpl_src;    // 0: V[cpl_line], 1: Zt[0], 2: Zt[1]
+  int cpl_line;
+  int cpl_neg;    // 1: x -= C(src)
+  int pad[3];
+};
+
+std::vector<SweepOp> build_schedule(int n, int N, bool double_sweep);
+
+// Direction codes of the BT frame mapping (node of the BT frame -> node of the grid).
+enum DirCode { DC_BT = 0, DC_TB = 1, DC_LR = 2, DC_RL = 3 };
+
+struct SlotState;  // per right-hand side Krylov state (device arrays, see krylov.cu)
+
+class Engine {
+ public:
+  // configuration
+  int device = 0, num_sms = 0, coop_per_sm = 1;
+  double k = 0;
+  int n = 0, m = 0, N = 0, R = 0, ldf = 0;
+  int precision = HH_PREC_FP64;
+  std::vector<int> dir_codes;  // DirCode per preconditioner, in order LR, RL, BT, TB of the bits
+  int t = 0;
+  hh_opts opts{};
+  Coef coef{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+
+  // device buffers
+  void* factors = nullptr;  // (R+1) blocks of m x ldf complex (precision-dependent)
+  unsigned* bar = nullptr;  // grid barrier counter
+  int* err = nullptr;       // device error word
+  SweepOp* d_ops = nullptr; // sweep schedule (double sweep)
+  int nops_double = 0;
+  SweepOp* d_ops_single = nullptr;
+  int nops_single = 0;
+  size_t bytes_allocated = 0;
+
+  // statistics
+  enum KClass { K_SWEEP = 0, K_SPMV = 1, K_GS = 2, K_SETUP = 3, K_NCLASS = 4 };
+  struct Tick { cudaEvent_t a, b; int cls; double bytes, flops; };
+  std::vector<Tick> pending_ticks;
+  std::vector<cudaEvent_t> event_pool;
+  int64_t launches[K_NCLASS] = {0, 0, 0, 0};
+  double ms[K_NCLASS] = {0, 0, 0, 0};
+  double bytes[K_NCLASS] = {0, 0, 0, 0};
+  double flops[K_NCLASS] = {0, 0, 0, 0};
+  int64_t kernel_launches = 0;
+  double setup_ms_total = 0;
+  int last_columns = 0;
+  Tick cur_tick[K_NCLASS];
+  bool tick_open[K_NCLASS] = {false, false, false, false};
+
+  // request loop (hh_submit / hh_poll)
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool worker_started = false, stopping = false;
+  struct Request;
+  std::deque<Request*> queue;
+  std::mutex solve_mu;  // serialises solves on the engine (blocking calls vs request loop)
+
+  ~Engine();
+  int init(double k, int n, int strips, uint32_t dirs, const hh_opts* o);
+  int factor();
+
+  // helpers
+  int dmalloc(void** p, size_t bytes);
+  void dfree(void* p);
+  unsigned grid_for(size_t work, int threads = 256) const;
+  cudaError_t launch_coop(const void* fn, int grid, int block, size_t smem, void** args, int grid_y = 1);
+  int check_device_error(const char* where);
+  void set_cuda_error(cudaError_t e, const char* where);
+  void count_launch(int n = 1) { kernel_launches += n; }
+  void tick_begin(int cls);
+  void tick_end(int cls, double bytes, double flops);
+  void collect_ticks();
+
+  // operations (device pointers, column stride = m*m complex128)
+  int apply_operator(int ncols, const double2* x, double2* y);
+  int apply_preconditioner_dev(int dcode, int ncols, const double2* r, double2* z, bool single);
+  int assemble_rhs(int nsrc, const double* src_host, double2* rhs);
+  int solve_batch_dev(int nrhs, const double2* rhs, double2* x, double tol, hh_result* res);
+
+  // sweep on packed columns: Rin (lines x m x C) -> V, with C = ncols
+  int run_sweep(const void* Rin, void* V, void* Zt, int C, bool single);
+  size_t sweep_elem() const { return precision == HH_PREC_FP32 ? 8 : 16; }
+
+  // sweep workspaces (grown on demand)
+  void* w_rin = nullptr;
+  void* w_v = nullptr;
+  void* w_zt = nullptr;
+  size_t w_cap_cols = 0;
+  int ensure_sweep_ws(int C);
+};
+
+}  // namespace hh

@@ -1,0 +1,205 @@
+// Strip setup: block LU (Thomas) of the impedance-modified strip matrix (Section 2: a
+// sweep is block forward/backward substitution of a block LU factorisation whose Schur
+// complements are approximated by the impedance condition of Eq. (4)).
+//
+// Every strip visited before the last one has the same matrix (lines 0..R-1: facing line
+// of type BOT, then R-1 lines of type INT whose far-side rows equal A's); the last strip
+// has R+1 lines, its last of type TOP.  The block LU of both shares
+//     S_0 = D_BOT,   S_j = D_INT - L S_{j-1}^{-1} U   (j = 1..R-1),
+// and the last strip adds S_R = D_TOP - L S_{R-1}^{-1} U.  The R+1 dense inverses
+// F_j = S_j^{-1} (m x m, m = n+1) are the stored factors.  L couples a line to the line
+// below (vertical edge + cell diagonal), U = L^T.
+#include <cstdio>
+#include <vector>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace hh {
+
+// S = D_type - L X U  (X = previous inverse, or none for S_0); also writes column 0 of S.
+template <typename R>
+__global__ void schur_kernel(const typename Cx<R>::T* __restrict__ X, int ldx, int has_prev, int type,
+                             Coef cf, typename Cx<R>::T* S, int ld, int m, typename Cx<R>::T* col0) {
+  using T = typename Cx<R>::T;
+  const size_t total = (size_t)m * m;
+  const double dg = cf.diag();
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / m), b = (int)(idx % m);
+    double2 d = make_double2(0.0, 0.0);
+    if (a == b) d = cf.centre(a, type);
+    else if (a - b == 1 || b - a == 1) d = cf.horiz(type);
+    T v = mk<T>(d.x, d.y);
+    if (has_prev) {
+      const double2 va = cf.vert(a), vb = cf.vert(b);
+      const T tva = mk<T>(va.x, va.y), tvb = mk<T>(vb.x, vb.y);
+      const T tvab = cmul(tva, tvb);
+      T acc = mk<T>(0, 0);
+      cfma(acc, tvab, X[(size_t)a * ldx + b]);
+      if (b >= 1) cfma(acc, cscale(tva, (R)dg), X[(size_t)a * ldx + b - 1]);
+      if (a >= 1) cfma(acc, cscale(tvb, (R)dg), X[(size_t)(a - 1) * ldx + b]);
+      if (a >= 1 && b >= 1) { T x = X[(size_t)(a - 1) * ldx + b - 1]; acc = cadd(acc, cscale(x, (R)(dg * dg))); }
+      v = csub(v, acc);
+    }
+    S[(size_t)a * ld + b] = v;
+    if (b == 0) col0[a] = v;
+  }
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting of one m x m complex matrix.
+// Ping-pong buffers A/B (step p reads the one of parity p, writes the other); row i of the
+// working matrix is owned by CTA i mod gridDim.x.  Column p of the source is kept
+// contiguous in col[p & 1] for the pivot search.  Pivot rows are recorded in piv.
+template <typename R>
+__global__ void __launch_bounds__(256) gj_kernel(typename Cx<R>::T* A, typename Cx<R>::T* B,
+                                                 typename Cx<R>::T* col, int* piv, int m, int ld,
+                                                 unsigned* bar, int* err, long long budget) {
+  using T = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* prow = reinterpret_cast<T*>(smem_raw);
+  __shared__ R s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_q;
+  __shared__ T s_inv;
+  unsigned target = 0;
+  const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int p = 0; p < m; ++p) {
+    const T* src = (p & 1) ? B : A;
+    T* dst = (p & 1) ? A : B;
+    const T* colp = col + (size_t)(p & 1) * m;
+    T* coln = col + (size_t)((p + 1) & 1) * m;
+    R best = (R)-1;
+    int bi = m;
+    for (int i = p + threadIdx.x; i < m; i += blockDim.x) {
+      const R v = cabs2(__ldcg(colp + i));
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const R ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < nw; ++w)
+        if (s_val[w] > best || (s_val[w] == best && s_idx[w] < bi)) { best = s_val[w]; bi = s_idx[w]; }
+      s_q = bi;
+      if (!(best > (R)0) || !isfinite(best)) {
+        s_q = -1;
+        if (blockIdx.x == 0) atomicCAS(err, 0, (int)DEV_SINGULAR);
+      } else {
+        const T pv = __ldcg(colp + bi);
+        const R inv2 = (R)1 / cabs2(pv);
+        s_inv = mk<T>(pv.x * inv2, -pv.y * inv2);
+        if (blockIdx.x == 0) piv[p] = bi;
+      }
+    }
+    __syncthreads();
+    const int q = s_q;
+    if (q < 0) return;  // every CTA sees the same pivot column: all leave together
+    const T inv = s_inv;
+    const T* qrow = src + (size_t)q * ld;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) prow[c] = (c == p) ? inv : cmul(__ldcg(qrow + c), inv);
+    __syncthreads();
+    for (int i = blockIdx.x; i < m; i += gridDim.x) {
+      T* drow = dst + (size_t)i * ld;
+      if (i == p) {
+        for (int c = threadIdx.x; c < m; c += blockDim.x) {
+          drow[c] = prow[c];
+          if (c == p + 1) coln[i] = prow[c];
+        }
+      } else {
+        const T* srow = src + (size_t)((i == q) ? p : i) * ld;
+        const T f = __ldcg(srow + p);
+        for (int c = threadIdx.x; c < m; c += blockDim.x) {
+          T v;
+          if (c == p) {
+            v = cmul(f, inv);
+            v.x = -v.x; v.y = -v.y;
+          } else {
+            v = __ldcg(srow + c);
+            const T fp = cmul(f, prow[c]);
+            v = csub(v, fp);
+          }
+          drow[c] = v;
+          if (c == p + 1) coln[i] = v;
+        }
+      }
+    }
+    if (p + 1 < m) {
+      if (!grid_sync(bar, target, err, budget)) return;
+    }
+  }
+}
+
+// Column permutation that undoes the row interchanges: F[:, c] = W[:, src[c]] where src is
+// obtained by applying the interchanges (p, piv[p]) for p = m-1 down to 0.
+__global__ void gj_perm_index(const int* piv, int* srcidx, int m) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int c = 0; c < m; ++c) srcidx[c] = c;
+    for (int p = m - 1; p >= 0; --p) {
+      int q = piv[p];
+      if (q < 0 || q >= m) q = p;  // an aborted inversion leaves pivots unset
+      const int t = srcidx[p]; srcidx[p] = srcidx[q]; srcidx[q] = t;
+    }
+  }
+}
+
+template <typename R>
+__global__ void gj_permute(const typename Cx<R>::T* W, int ldw, const int* srcidx, typename Cx<R>::T* F, int ldf, int m) {
+  using T = typename Cx<R>::T;
+  const size_t total = (size_t)m * ldf;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / ldf), c = (int)(idx % ldf);
+    F[idx] = (c < m) ? __ldcg(W + (size_t)i * ldw + srcidx[c]) : mk<T>(0, 0);
+  }
+}
+
+template <typename R>
+int factor_impl(Engine& E) {
+  using T = typename Cx<R>::T;
+  const int m = E.m, ld = E.ldf, Rr = E.R;
+  T* F = reinterpret_cast<T*>(E.factors);
+  T *bufA = nullptr, *bufB = nullptr, *col = nullptr;
+  int *piv = nullptr, *srcidx = nullptr;
+  const size_t mat = (size_t)m * ld * sizeof(T);
+  if (E.dmalloc((void**)&bufA, mat) || E.dmalloc((void**)&bufB, mat) || E.dmalloc((void**)&col, 2 * m * sizeof(T)) ||
+      E.dmalloc((void**)&piv, m * sizeof(int)) || E.dmalloc((void**)&srcidx, m * sizeof(int))) {
+    E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
+    return HH_ENOMEM;
+  }
+  int grid = E.num_sms < m ? E.num_sms : m;
+  const size_t smem = (size_t)m * sizeof(T);
+  int status = HH_OK;
+  for (int j = 0; j <= Rr && status == HH_OK; ++j) {
+    const int type = (j == 0) ? LINE_BOT : (j == Rr ? LINE_TOP : LINE_INT);
+    const T* X = j ? F + (size_t)(j - 1) * m * ld : nullptr;
+    E.tick_begin(Engine::K_SETUP);
+    schur_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(X, ld, j ? 1 : 0, type, E.coef, bufA, ld, m, col);
+    E.count_launch();
+    cudaMemsetAsync(E.bar, 0, sizeof(unsigned), E.stream);
+    cudaMemsetAsync(piv, 0, m * sizeof(int), E.stream);
+    void* args[] = {(void*)&bufA, (void*)&bufB, (void*)&col, (void*)&piv, (void*)&m, (void*)&ld,
+                    (void*)&E.bar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
+    cudaError_t ce = E.launch_coop((const void*)gj_kernel<R>, grid, 256, smem, args);
+    if (ce != cudaSuccess) { E.set_cuda_error(ce, "gj_kernel launch"); status = HH_ECUDA; break; }
+    const T* W = ((m - 1) & 1) ? bufA : bufB;
+    gj_perm_index<<<1, 1, 0, E.stream>>>(piv, srcidx, m);
+    E.count_launch();
+    gj_permute<R><<<E.grid_for((size_t)m * ld), 256, 0, E.stream>>>(W, ld, srcidx, F + (size_t)j * m * ld, ld, m);
+    E.count_launch();
+    E.tick_end(Engine::K_SETUP, 0.0, (double)m * m * m * 8.0);
+    status = E.check_device_error("strip setup");
+  }
+  cudaStreamSynchronize(E.stream);
+  E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
+  if (status == HH_OK) status = E.check_device_error("strip setup");
+  return status;
+}
+
+int Engine::factor() {
+  return precision == HH_PREC_FP32 ? factor_impl<float>(*this) : factor_impl<double>(*this);
+}
+
+}  // namespace hh

@@ -1,0 +1,226 @@
+"""GPU parity: every entry point of the C ABI against the CPU oracle on the same seeded
+inputs, element by element, at sizes the oracle finishes in seconds.
+
+Tolerances.  FP64 paths: the stencil apply and the load vector are a few FP64 operations
+per entry (1e-13 relative); the strip factors, sweeps and solutions differ from the
+oracle only by rounding order of LAPACK's banded LU versus block Thomas with explicit
+inverses, amplified by the conditioning of the strip blocks (1e-10 relative).  The
+solution of the FP64 solver must match the oracle's to 1e-10 relative with the same
+iteration count.  FP32 sweeps: complex64 factors (unit roundoff 6e-8) amplified by the
+block conditioning give ~1e-4 relative agreement with the FP64 sweep; the FP32 solve must
+reach the tolerance within the oracle's iterations + 2.
+"""
+import numpy as np
+import pytest
+
+import hh_inputs
+import paper_2408_11929_gb300 as hh
+from oracle import direct, fem, mpgmres, solver, sweep
+
+pytestmark = pytest.mark.gpu
+
+# (k, n, strips): several tiles, ragged line counts (R = 8, 16, 2), last strip R + 1
+CASES = [(20.0, 32, 4), (15.0, 40, 5), (30.0, 48, 3), (12.0, 16, 8)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+@pytest.mark.parametrize("k,n,N", CASES)
+def test_operator_apply(k, n, N):
+    A, *_ = fem.global_system(k, n)
+    x = hh_inputs.random_vector(A.shape[0], 3, seed=1)
+    with hh.Handle(k, n, N) as h:
+        y = h.apply_operator(np.ascontiguousarray(x.ravel()), 3).reshape(3, -1)
+    for c in range(3):
+        assert rel(y[c], A @ x[c]) < 1e-13
+
+
+@pytest.mark.parametrize("k,n,N", CASES[:2])
+def test_load_vector(k, n, N):
+    src = np.array([[0.3, 0.6, 0.05, 1.0, 0.0], [0.71, 0.22, 0.08, -0.5, 2.0]])
+    _, K, M, MG = fem.global_system(k, n)
+    b_ref = fem.load_vector(n, M, MG, fem.gaussian_source(n, src))
+    with hh.Handle(k, n, N) as h:
+        b = h.assemble_rhs(src)
+    assert rel(b, b_ref) < 1e-13
+
+
+@pytest.mark.parametrize("k,n,N", [(20.0, 32, 4), (12.0, 16, 8)])
+def test_strip_factors_fp64(k, n, N):
+    """F_0 = D_bot^{-1}, F_j = (D_int - L F_{j-1} U)^{-1}, F_R = (D_top - L F_{R-1} U)^{-1}, with the
+    line blocks taken from the oracle's global matrix (bottom line, an interior line, top line)."""
+    A, *_ = fem.global_system(k, n)
+    Ad = A.toarray()
+    m, R = n + 1, n // N
+    blk = lambda a, b: Ad[a * m:(a + 1) * m, b * m:(b + 1) * m]
+    Dbot, Dint, Dtop = blk(0, 0), blk(1, 1), blk(n, n)
+    L = blk(1, 0)
+    U = blk(0, 1)
+    ref = [np.linalg.inv(Dbot)]
+    for j in range(1, R):
+        ref.append(np.linalg.inv(Dint - L @ ref[-1] @ U))
+    ref.append(np.linalg.inv(Dtop - L @ ref[-1] @ U))
+    with hh.Handle(k, n, N) as h:
+        for j in range(R + 1):
+            assert rel(h.get_factor(j), ref[j]) < 1e-11, j
+
+
+@pytest.mark.parametrize("k,n,N", CASES)
+@pytest.mark.parametrize("double", [True, False])
+def test_preconditioner_fp64(k, n, N, double):
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], 2, seed=2)
+    with hh.Handle(k, n, N, single_sweep=0 if double else 1) as h:
+        for d in sweep.DIRECTIONS:
+            sw = sweep.Sweeper(A, k, n, N, d)
+            z = h.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 2).reshape(2, -1)
+            for c in range(2):
+                assert rel(z[c], sw.apply(r[c], double)) < 1e-10, (d, c)
+
+
+@pytest.mark.parametrize("k,n,N", CASES[:2])
+def test_preconditioner_fp32(k, n, N):
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], 4, seed=3)
+    with hh.Handle(k, n, N, precision="fp32") as h:
+        for d in sweep.DIRECTIONS:
+            sw = sweep.Sweeper(A, k, n, N, d)
+            z = h.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
+            for c in range(4):
+                assert rel(z[c], sw.apply(r[c])) < 2e-4, (d, c)
+
+
+@pytest.mark.parametrize("dirs", ["LR+RL+BT+TB", "LR+BT", "BT", "RL+BT+TB", "TB+LR"])
+def test_solve_fp64_matches_oracle(dirs):
+    k, n, N = 20.0, 32, 4
+    P = solver.Problem(k, n, N, dirs)
+    src = hh_inputs.centre_source()
+    b = P.rhs(src)
+    # the handle orders preconditioners LR, RL, BT, TB; the oracle keeps the string order
+    order = [d for d in ("LR", "RL", "BT", "TB") if d in dirs.split("+")]
+    ref = solver.Problem(k, n, N, "+".join(order)).solve(b, tol=1e-8)
+    with hh.Handle(k, n, N, dirs) as h:
+        x, res = h.solve(b, tol=1e-8)
+    assert res.status == hh.HH_OK
+    assert res.iterations == ref.iterations
+    assert rel(x, ref.x) < 1e-10
+    assert res.rel_res_explicit < 1e-8
+    assert abs(res.rel_res_implicit - ref.history[-1]) < 1e-3 * ref.history[-1]
+
+
+def test_solve_batch_matches_single_solves():
+    k, n, N = 25.0, 48, 4
+    srcs = hh_inputs.random_sources(3, seed=7, complex_amp=True)
+    P = solver.Problem(k, n, N)
+    B = np.stack([P.rhs(s) for s in srcs])
+    with hh.Handle(k, n, N) as h:
+        X, res = h.solve_batch(np.ascontiguousarray(B.ravel()), 3, tol=1e-8)
+        X = X.reshape(3, -1)
+        for r in range(3):
+            ref = P.solve(B[r], tol=1e-8)
+            assert res[r].status == hh.HH_OK
+            assert res[r].iterations == ref.iterations
+            assert rel(X[r], ref.x) < 1e-10
+
+
+def test_device_pointers_torch():
+    torch = pytest.importorskip("torch")
+    k, n, N = 20.0, 32, 4
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    ref = P.solve(b, tol=1e-8)
+    bt = torch.from_numpy(b).cuda()
+    with hh.Handle(k, n, N) as h:
+        xt, res = h.solve(bt, tol=1e-8)
+        assert xt.is_cuda
+        assert res.iterations == ref.iterations
+        assert rel(xt.cpu().numpy(), ref.x) < 1e-10
+        bd = torch.zeros(b.size, dtype=torch.complex128, device="cuda")
+        h.assemble_rhs(hh_inputs.centre_source(), out=bd)
+        assert rel(bd.cpu().numpy(), b) < 1e-13
+
+
+def test_one_strip_is_exact():
+    k, n = 18.0, 24
+    P = solver.Problem(k, n, 1)
+    b = P.rhs(hh_inputs.centre_source())
+    with hh.Handle(k, n, 1) as h:
+        x, res = h.solve(b, tol=1e-10)
+    assert res.status == hh.HH_OK and res.iterations == 1
+    assert rel(x, direct.solve(P.A, b, n)) < 1e-10
+
+
+def test_zero_rhs():
+    with hh.Handle(10.0, 16, 4) as h:
+        x, res = h.solve(np.zeros(17 * 17, dtype=np.complex128), tol=1e-8)
+    assert res.status == hh.HH_OK and res.iterations == 0
+    assert np.all(x == 0)
+
+
+def test_maxit_reports_noconv():
+    k, n, N = 20.0, 32, 4
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    ref = P.solve(b, tol=1e-12, maxit=3)
+    with hh.Handle(k, n, N, maxit=3) as h:
+        x, res = h.solve(b, tol=1e-12)
+    assert res.status == hh.HH_ENOCONV and res.iterations == 3
+    assert rel(x, ref.x) < 1e-10
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A cycle budget of 1 makes the first grid barrier of the strip setup give up; the
+    kernel returns, the call reports HH_ETIMEOUT and the device stays usable."""
+    with pytest.raises(hh.HHError) as e:
+        hh.Handle(10.0, 16, 4, timeout_cycles=1)
+    assert e.value.status == hh.HH_ETIMEOUT
+    with hh.Handle(10.0, 16, 4) as h:
+        x, res = h.solve(h.assemble_rhs(hh_inputs.centre_source()), tol=1e-8)
+    assert res.status == hh.HH_OK
+
+
+def test_submit_poll_matches_solve():
+    import time
+    k, n, N = 20.0, 32, 4
+    srcs = hh_inputs.random_sources(4, seed=11)
+    with hh.Handle(k, n, N) as h:
+        bs = [h.assemble_rhs(s) for s in srcs]
+        xs = [np.zeros_like(b) for b in bs]
+        tickets = [h.submit(b, x, tol=1e-8) for b, x in zip(bs, xs)]
+        done = {}
+        t0 = time.time()
+        while len(done) < len(tickets) and time.time() - t0 < 60:
+            for t in tickets:
+                if t not in done:
+                    st, res = h.poll(t)
+                    if st != hh.HH_EPENDING:
+                        done[t] = (st, res)
+            time.sleep(0.001)
+        assert len(done) == len(tickets)
+        for b, x, t in zip(bs, xs, tickets):
+            xr, rr = h.solve(b, tol=1e-8)
+            assert done[t][0] == hh.HH_OK
+            assert done[t][1].iterations == rr.iterations
+            assert rel(x, xr) < 1e-12
+
+
+def test_fp32_sweeps_solve():
+    k, n, N = 40.0, 64, 4
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    ref = P.solve(b, tol=1e-6)
+    tight = P.solve(b, tol=1e-10)
+    with hh.Handle(k, n, N, precision="fp32") as h:
+        x, res = h.solve(b, tol=1e-6)
+    assert res.status == hh.HH_OK
+    assert res.iterations <= ref.iterations + 2
+    assert res.rel_res_explicit < 1.5e-6
+    assert rel(x, tight.x) < 1e-5
