@@ -1,0 +1,386 @@
+"""Benchmark: time-to-1e-6 and solves/s of the multipreconditioned sweep solver at k=400.
+
+Workload (default): k = 400, n = 1024 (1,050,625 unknowns), 32 strips of 32 node lines,
+four double sweeps LR+RL+BT+TB in one persistent launch per iteration, one Gaussian
+source at (0.5, 0.5), tolerance 1e-6, complex64 strip factors and sweeps, complex128
+Krylov side.  One step = one hh_solve from the assembled load vector to tol with the strip
+factors already set up (the setup time is reported separately, like the FP64 form).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  With N > 1 (torchrun) every rank solves its own copies
+(replicas only: the method has no exchange step on one problem) and value is the total
+number of solves of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import hh_inputs  # noqa: E402
+
+METRIC = "time-to-1e-6 residual & solves/s at k=400, FP32-sweep vs FP64; p50/p99 latency"
+WORKLOAD = "k400_n1024"
+L2_BYTES = 129 * 2 ** 20
+
+
+def workload_desc(w) -> dict:
+    return {
+        "workload": f"{w.name}: k={w.k:g}, n={w.n} ({w.dofs:,} unknowns), {w.strips} strips of {w.n // w.strips} "
+                    f"node lines, double sweeps {w.dirs} in one launch, {w.nrhs} RHS (Gaussian sigma=0.05 at "
+                    f"(0.5,0.5)), tol {w.tol:g}, complex64 factors+sweeps, complex128 Krylov",
+        "k": w.k, "n": w.n, "strips": w.strips, "dirs": w.dirs, "nrhs": w.nrhs, "tol": w.tol,
+        "l2": "inputs larger than L2: the complex64 factor store streamed by every sweep (33 blocks x 8.4 MB) "
+              "and each 16.8 MB Krylov vector exceed the 129 MB L2; no flush between steps",
+    }
+
+
+# ---------------------------------------------------------------------- distributed helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(elapsed_s: float, units: float, ws: int):
+    """Max of the per-rank times and sum of the per-rank units (torch.distributed)."""
+    if ws == 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ---------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------- peaks / traffic
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2408_11929_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on the
+    current sweep kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != sweep_source_hash():
+        return None
+    e = d.get("workloads", {}).get(workload)
+    return None if e is None else float(e["dram_bytes_per_launch"])
+
+
+# ---------------------------------------------------------------------- oracle (CPU) baseline
+CPU_SAMPLE_CODE = r"""
+import json, sys, time, os
+import numpy as np
+sys.path.insert(0, %(root)r)
+from oracle import fem, sweep
+k, n, N, iters, nsolve = %(k)r, %(n)r, %(N)r, %(iters)r, %(nsolve)r
+R = n // N
+t0 = time.time()
+D, glob = sweep.strip_matrix(k, n, 0, R - 1, "row", 1)
+t_asm = time.time() - t0
+t0 = time.time()
+lu = sweep.BandLU(D, n + 2)
+t_fact = time.time() - t0
+rng = np.random.default_rng(0)
+r = rng.standard_normal(D.shape[0]) + 1j * rng.standard_normal(D.shape[0])
+t0 = time.time()
+for _ in range(nsolve):
+    lu.solve(r)
+t_solve = (time.time() - t0) / nsolve
+A, K, M, MG = fem.global_system(k, n)
+x = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+t0 = time.time()
+for _ in range(3):
+    A @ x
+t_mv = (time.time() - t0) / 3
+print(json.dumps(dict(t_asm=t_asm, t_fact=t_fact, t_solve=t_solve, t_mv=t_mv)))
+"""
+
+
+def oracle_sample(w, iters: int, nsolve: int = 6) -> dict:
+    """Times the oracle on one strip of the workload in a single-threaded subprocess and
+    scales it to one full solve: iterations x directions x (2N - 1) strip solves + matvecs
+    (Gram-Schmidt and the strip factorisation excluded, as the GPU step excludes setup)."""
+    code = CPU_SAMPLE_CODE % dict(root=ROOT, k=w.k, n=w.n, N=w.strips, iters=iters, nsolve=nsolve)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    t_dirs = len(w.dirs.split("+"))
+    per_iter = t_dirs * ((2 * w.strips - 1) * d["t_solve"] + d["t_mv"])
+    t_solve_est = iters * per_iter
+    d.update(iters=iters, per_iter_s=per_iter, solve_s_est=t_solve_est)
+    return d
+
+
+# ---------------------------------------------------------------------- GPU arm
+def golden(w):
+    p = os.path.join(ROOT, "tests", "golden", f"{w.name}.json")
+    return json.load(open(p)) if os.path.exists(p) else None
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    import __graft_entry__
+    import paper_2408_11929_gb300 as hh
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    w = hh_inputs.workload(WORKLOAD)
+    stream = torch.cuda.Stream()
+    src = w.sources[0]
+    peaks = measured_peaks()
+
+    with torch.cuda.stream(stream):
+        h = hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", profile=1, stream=stream.cuda_stream)
+        setup_ms = h.stats()["setup_ms"]
+        b = torch.from_numpy(h.assemble_rhs(src)).to(f"cuda:{local}")
+        x = torch.zeros_like(b)
+        for _ in range(args.warmup):
+            _, res = h.solve(b, x, tol=w.tol)
+        torch.cuda.synchronize()
+        h.reset_stats()
+        clk = ClockSampler(local)
+        clk.start()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iters = []
+        for _ in range(args.steps):
+            _, res = h.solve(b, x, tol=w.tol)
+            iters.append(res.iterations)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        clocks = clk.stop()
+        elapsed = e0.elapsed_time(e1) / 1000.0
+        st = h.stats()
+        status = res.status
+        rel_exp = res.rel_res_explicit
+        x_host = x.cpu().numpy()
+
+        # end to end through the C ABI with host buffers (copies inside the timed region)
+        b_host = b.cpu().numpy()
+        xh = np.zeros_like(b_host)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h.solve(b_host, xh, tol=w.tol)
+        e2e_s = time.perf_counter() - t0
+        h.close()
+
+    tmax, units = aggregate(elapsed, float(args.steps), ws)
+    e2e_max, e2e_units = aggregate(e2e_s, float(args.steps), ws)
+    out = None
+    if rank == 0:
+        nsw = max(1, st["sweep_launches"])
+        sweep_bytes = st["sweep_bytes"] / nsw
+        sweep_ms = st["sweep_ms"] / nsw if st["sweep_ms"] > 0 else None
+        achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms else None
+        traffic = ncu_traffic(WORKLOAD)
+        g = golden(w)
+        err = None
+        iters_oracle = None
+        if g is not None:
+            idx = np.array(g["sample_nodes"])
+            r0 = g["rhs"]["0"]
+            xt = np.array(r0["tight_x_sample_re"]) + 1j * np.array(r0["tight_x_sample_im"])
+            err = float(np.linalg.norm(x_host[idx] - xt) / np.linalg.norm(xt))
+            iters_oracle = r0["iterations"]
+        out = {
+            "metric": METRIC, "value": units / tmax, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 sweeps + c128 Krylov", "data": "synthetic",
+            "config": workload_desc(w),
+            "time_to_tol_ms": tmax / args.steps * 1e3, "iterations": iters[-1], "iterations_oracle": iters_oracle,
+            "status": hh.STATUS_NAMES[status], "rel_res_explicit": rel_exp, "setup_ms": setup_ms,
+            "error_vs_oracle_tight": err,
+            "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,4>",
+                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": sweep_ms,
+                         "launches": st["sweep_launches"], "peak_src": peaks["src"] + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "e2e": {"value": e2e_units / e2e_max, "unit": "solves/s", "h2d_bytes_per_step": int(b_host.nbytes),
+                    "d2h_bytes_per_step": int(xh.nbytes)},
+            "gpu_launches": int(st["kernel_launches"]),
+            "clocks": clocks,
+            "phase_ms_per_step": {"sweep": st["sweep_ms"] / args.steps, "spmv": st["spmv_ms"] / args.steps,
+                                  "gram_schmidt": st["gs_ms"] / args.steps},
+        }
+    return out
+
+
+def run_fp64(w, local):
+    """The FP64 GPU form of the same solve (complex128 factors and sweeps), for the
+    FP32-vs-FP64 comparison: setup time and one timed solve after one warm-up."""
+    import torch
+    import paper_2408_11929_gb300 as hh
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp64", stream=stream.cuda_stream)
+        setup_ms = h.stats()["setup_ms"]
+        b = torch.from_numpy(h.assemble_rhs(w.sources[0])).to(f"cuda:{local}")
+        x = torch.zeros_like(b)
+        h.solve(b, x, tol=w.tol)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, res = h.solve(b, x, tol=w.tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h.close()
+    return {"ms_per_solve": e0.elapsed_time(e1), "iterations": res.iterations, "setup_ms": setup_ms,
+            "rel_res_explicit": res.rel_res_explicit}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    w = hh_inputs.workload(WORKLOAD)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        g = golden(w)
+        iters = g["rhs"]["0"]["iterations"] if g else 20
+        for _ in range(args.warmup):
+            oracle_sample(w, iters, nsolve=2)
+        vals = []
+        t0 = time.time()
+        for _ in range(args.steps):
+            d = oracle_sample(w, iters, nsolve=2)
+            vals.append(d["solve_s_est"])
+        v = len(vals) / sum(vals)
+        sample = (f"per step: one 32-line k=400 strip assembled and factorised (zgbtrf), 2 timed strip solves "
+                  f"(zgbtrs) and 3 global matvecs, scaled to a full solve = {iters} iterations x "
+                  f"{len(w.dirs.split('+'))} directions x {2 * w.strips - 1} strip solves (+ matvecs)")
+        line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": workload_desc(w),
+                "impl": "reference",
+                "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": time.time() - t0}
+        print(json.dumps(line), flush=True)
+        return
+
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    out = run_gpu(args, ws, rank, local)
+    if rank == 0:
+        if not args.no_fp64:
+            out["fp64"] = run_fp64(w, local)
+            out["fp32_speedup_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["ms_per_step"]
+        if not args.no_cpu:
+            d = oracle_sample(w, out["iterations_oracle"] or out["iterations"])
+            out["cpu_baseline"] = {
+                "value": 1.0 / d["solve_s_est"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": (f"one 32-line k=400 strip factorised (zgbtrf, {d['t_fact']:.1f} s, excluded like the GPU "
+                           f"setup), {6} timed strip solves ({d['t_solve'] * 1e3:.0f} ms each) and 3 global matvecs "
+                           f"({d['t_mv'] * 1e3:.0f} ms), scaled to {d['iters']} iterations x 4 directions x "
+                           f"{2 * w.strips - 1} strip solves; single thread (OMP/OPENBLAS_NUM_THREADS=1)"),
+                "host_cores_available": os.cpu_count()}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

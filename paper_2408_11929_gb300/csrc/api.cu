@@ -154,6 +154,8 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
     own_stream = true;
   }
   coop_per_sm = std::max(1, qr_blocks_per_sm());
+  if (sweep_smem(1) > 220 * 1024)
+    return (set_error("n too large: the sweep kernel's factor rows and line tiles exceed shared memory"), HH_EINVAL);
 
   const size_t fbytes = (size_t)(R + 1) * m * ldf * sweep_elem();
   size_t free_b = 0, total_b = 0;

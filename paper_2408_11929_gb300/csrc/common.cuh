@@ -82,6 +82,51 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned& target, int
   return s_ok != 0;
 }
 
+// ---------------------------------------------------------------- TMA bulk copies + mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// one arrival that also announces `bytes` of transaction traffic for the current phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier.  On expiry the error word is set and the
+// wait is retried once more (same budget) so that copies still in flight can land before
+// the caller leaves the kernel.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err, long long budget) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > budget) {
+      atomicCAS(err, 0, (int)DEV_TIMEOUT);
+      const long long t1 = clock64();
+      while (!mbar_try_wait(bar, parity) && clock64() - t1 < budget) {
+      }
+      return false;
+    }
+  }
+  return true;
+}
+// orders this thread's generic-proxy accesses with its later async-proxy (TMA) accesses
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
 // ---------------------------------------------------------------- P1 stencil coefficients
 // Matrix A = K - k^2 M - i k M_Gamma on the (n+1)^2 grid, cells cut along SW-NE diagonals.
 // Right isosceles triangles with legs h: stiffness 1 at the right-angle vertex, 1/2 at the

@@ -114,6 +114,10 @@ class Engine {
   // sweep on packed columns: Rin (lines x m x C) -> V, with C = ncols
   int run_sweep(const void* Rin, void* V, void* Zt, int C, bool single);
   size_t sweep_elem() const { return precision == HH_PREC_FP32 ? 8 : 16; }
+  int sweep_ct() const { return precision == HH_PREC_FP32 ? 4 : 2; }  // columns per tile
+  int sweep_rows_per_cta() const;
+  int sweep_grid() const;
+  size_t sweep_smem(int nbuf) const;
 
   // sweep workspaces (grown on demand)
   void* w_rin = nullptr;

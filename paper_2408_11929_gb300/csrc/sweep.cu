@@ -74,183 +74,313 @@ __device__ __forceinline__ int code_of(int4 codes, int d) {
   return d == 0 ? codes.x : (d == 1 ? codes.y : (d == 2 ? codes.z : codes.w));
 }
 
+// Column-tile layout of the sweep arrays: X[line][tile][node][ct], ct = CT columns per
+// tile (4 for complex64, 2 for complex128), so that one tile of one node line is a
+// contiguous m * CT block that one bulk copy moves.  Columns beyond C are zero padding.
 template <typename R>
 __global__ void pack_kernel(const double2* const* __restrict__ srcptr, const double* __restrict__ scale, int C,
-                            int t, int4 codes, int n, typename Cx<R>::T* __restrict__ X) {
+                            int t, int4 codes, int n, int ct, int ntile, typename Cx<R>::T* __restrict__ X) {
   using T = typename Cx<R>::T;
   const int m = n + 1;
-  const size_t total = (size_t)m * m * C;
+  const size_t total = (size_t)m * m * ntile * ct;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % C);
-    const size_t node = idx / C;
-    const int l = (int)(node / m), i = (int)(node % m);
-    int io, jo;
-    frame_map(code_of(codes, c % t), i, l, n, io, jo);
-    const double2 v = srcptr[c][(size_t)jo * m + io];
-    const double s = scale[c];
-    X[idx] = mk<T>(v.x * s, v.y * s);
+    const int cc = (int)(idx % ct);
+    size_t q = idx / ct;
+    const int i = (int)(q % m);
+    q /= m;
+    const int tile = (int)(q % ntile);
+    const int l = (int)(q / ntile);
+    const int c = tile * ct + cc;
+    T v = mk<T>(0, 0);
+    if (c < C) {
+      int io, jo;
+      frame_map(code_of(codes, c % t), i, l, n, io, jo);
+      const double2 a = srcptr[c][(size_t)jo * m + io];
+      const double s = scale[c];
+      v = mk<T>(a.x * s, a.y * s);
+    }
+    X[idx] = v;
   }
 }
 
 template <typename R>
-__global__ void unpack_kernel(const typename Cx<R>::T* __restrict__ X, int C, int t, int4 codes, int n,
-                              double2* __restrict__ dst, size_t stride) {
+__global__ void unpack_kernel(const typename Cx<R>::T* __restrict__ X, int C, int t, int4 codes, int n, int ct,
+                              int ntile, double2* __restrict__ dst, size_t stride) {
   const int m = n + 1;
-  const size_t total = (size_t)m * m * C;
+  const size_t total = (size_t)m * m * ntile * ct;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % C);
-    const size_t node = idx / C;
-    const int l = (int)(node / m), i = (int)(node % m);
+    const int cc = (int)(idx % ct);
+    size_t q = idx / ct;
+    const int i = (int)(q % m);
+    q /= m;
+    const int tile = (int)(q % ntile);
+    const int l = (int)(q / ntile);
+    const int c = tile * ct + cc;
+    if (c >= C) continue;
     int io, jo;
     frame_map(code_of(codes, c % t), i, l, n, io, jo);
     dst[(size_t)c * stride + (size_t)jo * m + io] = to_d(X[idx]);
   }
 }
 
-// Persistent sweep.  CTA b owns rows [b*rp, min(m, (b+1)*rp)) of every block step.  Each
-// step: every CTA builds the full input line x (m x CT columns, in shared memory) from
-// Rin and the coupled line, multiplies its rows of F_f by it (one warp per row and column
-// group, warp-shuffle reduction), writes its rows of the output, then all CTAs meet at a
-// bounded grid barrier.  Columns are processed in tiles of CT that fit shared memory.
-template <typename R, int CC>
-__global__ void __launch_bounds__(256) sweep_kernel(const typename Cx<R>::T* __restrict__ F, int ldf, int m,
-                                                    int C, int CT, const typename Cx<R>::T* __restrict__ Rin,
-                                                    typename Cx<R>::T* V, typename Cx<R>::T* Zt,
-                                                    const SweepOp* __restrict__ ops, int nops, Coef cf,
-                                                    unsigned* bar, int* err, long long budget) {
+template <typename R>
+struct SweepParams {
   using T = typename Cx<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* vert_s = reinterpret_cast<T*>(smem_raw);
-  T* x_s = vert_s + ((m + 1) & ~1);
-  const int rp = (m + gridDim.x - 1) / gridDim.x;
+  const T* F;        // factor blocks, m x ldf each
+  const T* Rin;      // packed right-hand sides (lines x tiles x m x CT)
+  T* V;              // sweep output (same layout)
+  T* Zt;             // two line buffers for the backward chains
+  const SweepOp* ops;
+  Coef cf;
+  unsigned* bar;
+  int* err;
+  long long budget;
+  int ldf, m, ntile, nops, rp;
+};
+
+// Persistent sweep, one CTA per SM.  CTA b owns rows [b rp, (b+1) rp) of every block step.
+// Per step: the CTA's rows of the factor block F_f arrive in shared memory by a bulk copy
+// issued one step ahead (double buffer) so that HBM streaming overlaps the barrier; after
+// the grid barrier the coupled line and the right-hand-side line arrive by bulk copy, the
+// input x = Rin +- C(src) is formed in shared memory, every thread multiplies its slice of
+// the node index for all of the CTA's rows and the tile's CT columns, a butterfly warp
+// reduction and a cross-warp sum give the outputs, and the CTA writes its rows.
+template <typename R, int CT, int RP, int NBUF>
+__global__ void __launch_bounds__(256, 1) sweep_tma_kernel(SweepParams<R> p) {
+  using T = typename Cx<R>::T;
+  constexpr int NV = RP * CT * 2;          // real partial sums per thread
+  constexpr int PER = NV / 32;             // values per lane after the butterfly
+  static_assert(NV == 32 || NV == 64, "butterfly expects 32 or 64 values");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int m = p.m, rp = p.rp, ldf = p.ldf;
+  const int lineT = m * CT;
+  T* Fbuf = reinterpret_cast<T*>(smem_raw);
+  T* Sbuf = Fbuf + (size_t)NBUF * rp * ldf;
+  T* Bbuf = Sbuf + lineT;
+  T* vert_s = Bbuf + lineT;
+  R* red = reinterpret_cast<R*>(vert_s + ((m + 1) & ~1));
+  uint64_t* mb = reinterpret_cast<uint64_t*>(red + 8 * 64);
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int r0 = blockIdx.x * rp;
-  const int r1 = min(m, r0 + rp);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const size_t lineC = (size_t)m * C;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double2 v = cf.vert(i);
+  const int nr = max(0, min(m, r0 + rp) - r0);
+  const unsigned fbytes = (unsigned)(nr * ldf * sizeof(T));
+  const unsigned lbytes = (unsigned)(lineT * sizeof(T));
+  const size_t lstride = (size_t)p.ntile * lineT;
+
+  for (int i = tid; i < m; i += blockDim.x) {
+    const double2 v = p.cf.vert(i);
     vert_s[i] = mk<T>(v.x, v.y);
   }
-  const R dg = (R)cf.diag();
-  unsigned target = 0;
+  const R dg = (R)p.cf.diag();
+  if (tid == 0) {
+    mbar_init(&mb[0], 1);
+    mbar_init(&mb[1], 1);
+    mbar_init(&mb[2], 1);
+    fence_proxy_async();
+    if (nr > 0) {
+      mbar_expect_tx(&mb[0], fbytes);
+      bulk_g2s(Fbuf, p.F + (size_t)p.ops[0].f * m * ldf + (size_t)r0 * ldf, fbytes, &mb[0]);
+    }
+  }
   __syncthreads();
-  for (int op = 0; op < nops; ++op) {
-    const SweepOp o = ops[op];
-    const T* src = (o.cpl_src == 0) ? V + (size_t)o.cpl_line * lineC : Zt + (size_t)(o.cpl_src - 1) * lineC;
-    const T* base = o.base_line >= 0 ? Rin + (size_t)o.base_line * lineC : nullptr;
-    const T* Fb = F + (size_t)o.f * m * ldf;
-    T* out = V + (size_t)o.out_line * lineC;
-    T* zs = o.zsave >= 0 ? Zt + (size_t)o.zsave * lineC : nullptr;
-    for (int c0 = 0; c0 < C; c0 += CT) {
-      const int ct = min(CT, C - c0);
-      for (int idx = threadIdx.x; idx < m * ct; idx += blockDim.x) {
-        const int i = idx / ct, cc = idx - i * ct;
-        const size_t g = (size_t)i * C + c0 + cc;
-        T v = base ? __ldg(base + g) : mk<T>(0, 0);
+  unsigned target = 0, lphase = 0;
+  for (int op = 0; op < p.nops; ++op) {
+    const SweepOp o = p.ops[op];
+    const int fb = (NBUF == 2) ? (op & 1) : 0;
+    const unsigned fpar = (NBUF == 2) ? ((op >> 1) & 1) : (op & 1);
+    if (NBUF == 2 && tid == 0 && nr > 0 && op + 1 < p.nops) {
+      fence_proxy_async();
+      mbar_expect_tx(&mb[(op + 1) & 1], fbytes);
+      bulk_g2s(Fbuf + (size_t)((op + 1) & 1) * rp * ldf, p.F + (size_t)p.ops[op + 1].f * m * ldf + (size_t)r0 * ldf,
+               fbytes, &mb[(op + 1) & 1]);
+    }
+    const T* src = (o.cpl_src == 0) ? p.V + (size_t)o.cpl_line * lstride : p.Zt + (size_t)(o.cpl_src - 1) * lstride;
+    const T* base = o.base_line >= 0 ? p.Rin + (size_t)o.base_line * lstride : nullptr;
+    T* out = p.V + (size_t)o.out_line * lstride;
+    T* zs = o.zsave >= 0 ? p.Zt + (size_t)o.zsave * lstride : nullptr;
+    const bool need_f = nr > 0;
+    for (int tile = 0; tile < p.ntile; ++tile) {
+      const unsigned nb = (o.cpl ? lbytes : 0u) + (base ? lbytes : 0u);
+      if (tid == 0) {
+        int ok = 1;
+        if (nb) {
+          fence_proxy_async();
+          mbar_expect_tx(&mb[2], nb);
+          if (o.cpl) bulk_g2s(Sbuf, src + (size_t)tile * lineT, lbytes, &mb[2]);
+          if (base) bulk_g2s(Bbuf, base + (size_t)tile * lineT, lbytes, &mb[2]);
+          ok = mbar_wait(&mb[2], lphase & 1, p.err, p.budget);
+        }
+        if (ok && tile == 0 && need_f) ok = mbar_wait(&mb[fb], fpar, p.err, p.budget);
+        s_ok = ok;
+      }
+      if (nb) ++lphase;
+      __syncthreads();
+      if (!s_ok) return;
+      // x = base +- C(src), formed in place in Bbuf
+      for (int idx = tid; idx < lineT; idx += blockDim.x) {
+        const int i = idx / CT;
+        T v = base ? Bbuf[idx] : mk<T>(0, 0);
         if (o.cpl) {
-          T cp = cmul(vert_s[i], __ldcg(src + g));
-          if (o.cpl == 1 && i >= 1) { const T y = __ldcg(src + g - C); cp.x += dg * y.x; cp.y += dg * y.y; }
-          if (o.cpl == 2 && i + 1 < m) { const T y = __ldcg(src + g + C); cp.x += dg * y.x; cp.y += dg * y.y; }
+          T cp = cmul(vert_s[i], Sbuf[idx]);
+          if (o.cpl == 1 && i >= 1) { const T y = Sbuf[idx - CT]; cp.x += dg * y.x; cp.y += dg * y.y; }
+          if (o.cpl == 2 && i + 1 < m) { const T y = Sbuf[idx + CT]; cp.x += dg * y.x; cp.y += dg * y.y; }
           v = o.cpl_neg ? csub(v, cp) : cadd(v, cp);
         }
-        x_s[idx] = v;
+        Bbuf[idx] = v;
       }
       __syncthreads();
-      const int ngrp = ct / CC;
-      const int nwork = (r1 > r0 ? r1 - r0 : 0) * ngrp;
-      for (int w = wid; w < nwork; w += nw) {
-        const int row = r0 + w / ngrp, cg = (w % ngrp) * CC;
-        T acc[CC];
+      const T* Fr = Fbuf + (size_t)fb * rp * ldf;
+      for (int g0 = 0; g0 < nr; g0 += RP) {
+        const int ng = min(RP, nr - g0);
+        R acc[NV];
 #pragma unroll
-        for (int q = 0; q < CC; ++q) acc[q] = mk<T>(0, 0);
-        const T* Fr = Fb + (size_t)row * ldf;
-        for (int i = lane; i < m; i += 32) {
-          const T fv = __ldg(Fr + i);
-          const T* xr = x_s + i * ct + cg;
+        for (int q = 0; q < NV; ++q) acc[q] = 0;
+        for (int i = tid; i < m; i += blockDim.x) {
+          T xv[CT];
 #pragma unroll
-          for (int q = 0; q < CC; ++q) cfma(acc[q], fv, xr[q]);
+          for (int c = 0; c < CT; ++c) xv[c] = Bbuf[i * CT + c];
+#pragma unroll
+          for (int rr = 0; rr < RP; ++rr) {
+            if (rr < ng) {
+              const T f = Fr[(size_t)(g0 + rr) * ldf + i];
+#pragma unroll
+              for (int c = 0; c < CT; ++c) {
+                const int q = (rr * CT + c) * 2;
+                acc[q] = fma(f.x, xv[c].x, acc[q]);
+                acc[q] = fma(-f.y, xv[c].y, acc[q]);
+                acc[q + 1] = fma(f.x, xv[c].y, acc[q + 1]);
+                acc[q + 1] = fma(f.y, xv[c].x, acc[q + 1]);
+              }
+            }
+          }
         }
+        // butterfly: after the offset-o round every lane keeps the half selected by (lane & o)
 #pragma unroll
-        for (int q = 0; q < CC; ++q)
+        for (int o2 = 16, half = NV / 2; o2 >= 1; o2 >>= 1, half >>= 1) {
+          const bool up = (lane & o2) != 0;
 #pragma unroll
-          for (int s = 16; s; s >>= 1) acc[q] = cadd(acc[q], shfl_xor(acc[q], s));
-        if (lane < CC) {
-          T z = acc[0];
-#pragma unroll
-          for (int q = 1; q < CC; ++q)
-            if (lane == q) z = acc[q];
-          const size_t g = (size_t)row * C + c0 + cg + lane;
-          if (o.out_sub) out[g] = csub(__ldcg(out + g), z);
-          else out[g] = z;
-          if (zs) zs[g] = z;
+          for (int q = 0; q < half; ++q) {
+            const R send = up ? acc[q] : acc[q + half];
+            const R keep = up ? acc[q + half] : acc[q];
+            acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o2);
+          }
         }
+        // lane holds values [lane * PER, lane * PER + PER)
+#pragma unroll
+        for (int q = 0; q < PER; ++q) red[wid * 64 + lane * PER + q] = acc[q];
+        __syncthreads();
+        if (tid < NV / 2) {
+          R re = 0, im = 0;
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            re += red[w * 64 + 2 * tid];
+            im += red[w * 64 + 2 * tid + 1];
+          }
+          const int rr = tid / CT, c = tid % CT;
+          if (rr < ng) {
+            const size_t g = (size_t)tile * lineT + (size_t)(r0 + g0 + rr) * CT + c;
+            T z;
+            z.x = re;
+            z.y = im;
+            if (o.out_sub) out[g] = csub(__ldcg(out + g), z);
+            else out[g] = z;
+            if (zs) zs[g] = z;
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
-    if (op + 1 < nops) {
-      if (!grid_sync(bar, target, err, budget)) return;
+    if (NBUF == 1 && tid == 0 && nr > 0 && op + 1 < p.nops) {
+      fence_proxy_async();
+      mbar_expect_tx(&mb[0], fbytes);
+      bulk_g2s(Fbuf, p.F + (size_t)p.ops[op + 1].f * m * ldf + (size_t)r0 * ldf, fbytes, &mb[0]);
+    }
+    if (op + 1 < p.nops) {
+      if (!grid_sync(p.bar, target, p.err, p.budget)) {
+        // let this CTA's outstanding factor copy land before leaving
+        if (tid == 0 && nr > 0) mbar_wait(&mb[(NBUF == 2) ? ((op + 1) & 1) : 0],
+                                          (NBUF == 2) ? (((op + 1) >> 1) & 1) : ((op + 1) & 1), p.err, p.budget);
+        return;
+      }
+      if (tid == 0) fence_proxy_async();
     }
   }
 }
 
 int Engine::ensure_sweep_ws(int C) {
-  if ((size_t)C <= w_cap_cols) return HH_OK;
+  const int ct = sweep_ct();
+  const int ntile = (C + ct - 1) / ct;
+  if ((size_t)ntile * ct <= w_cap_cols) return HH_OK;
   dfree(w_rin); dfree(w_v); dfree(w_zt);
   w_rin = w_v = w_zt = nullptr;
   w_cap_cols = 0;
-  const size_t line = (size_t)m * C * sweep_elem();
+  const size_t line = (size_t)m * ntile * ct * sweep_elem();
   if (dmalloc(&w_rin, line * m) || dmalloc(&w_v, line * m) || dmalloc(&w_zt, line * 2)) return HH_ENOMEM;
-  w_cap_cols = C;
+  w_cap_cols = (size_t)ntile * ct;
   return HH_OK;
 }
 
-template <typename R, int CC>
-static cudaError_t launch_sweep_t(Engine& E, const void* Rin, void* V, void* Zt, int C, bool single) {
+// Shared memory of the sweep kernel for NBUF factor buffers.
+size_t Engine::sweep_smem(int nbuf) const {
+  const size_t e = sweep_elem();
+  const int rp = sweep_rows_per_cta();
+  return (size_t)nbuf * rp * ldf * e + 2 * (size_t)m * sweep_ct() * e + (size_t)((m + 1) & ~1) * e +
+         8 * 64 * (e / 2) + 3 * sizeof(uint64_t);
+}
+int Engine::sweep_rows_per_cta() const { return (m + num_sms - 1) / num_sms; }
+int Engine::sweep_grid() const {
+  const int rp = sweep_rows_per_cta();
+  return (m + rp - 1) / rp;
+}
+
+template <typename R, int CT, int NBUF>
+static cudaError_t launch_sweep_t(Engine& E, const void* Rin, void* V, void* Zt, int ntile, bool single) {
   using T = typename Cx<R>::T;
-  const int m = E.m;
-  const int grid = std::min(E.num_sms, m);
-  const size_t cap = 200 * 1024;
-  const size_t vert_bytes = (size_t)((m + 1) & ~1) * sizeof(T);
-  int CT = (int)((cap - vert_bytes) / ((size_t)m * sizeof(T)));
-  CT = std::min(CT, C);
-  CT = (CT / CC) * CC;
-  if (CT < CC) CT = CC;
-  const size_t smem = vert_bytes + (size_t)m * CT * sizeof(T);
-  auto fn = sweep_kernel<R, CC>;
+  SweepParams<R> p;
+  p.F = reinterpret_cast<const T*>(E.factors);
+  p.Rin = reinterpret_cast<const T*>(Rin);
+  p.V = reinterpret_cast<T*>(V);
+  p.Zt = reinterpret_cast<T*>(Zt);
+  p.ops = single ? E.d_ops_single : E.d_ops;
+  p.nops = single ? E.nops_single : E.nops_double;
+  p.cf = E.coef;
+  p.bar = E.bar;
+  p.err = E.err;
+  p.budget = E.opts.timeout_cycles;
+  p.ldf = E.ldf;
+  p.m = E.m;
+  p.ntile = ntile;
+  p.rp = E.sweep_rows_per_cta();
+  const size_t smem = E.sweep_smem(NBUF);
+  auto fn = sweep_tma_kernel<R, CT, 8, NBUF>;
   cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const T* Fp = reinterpret_cast<const T*>(E.factors);
-  const T* Rp = reinterpret_cast<const T*>(Rin);
-  T* Vp = reinterpret_cast<T*>(V);
-  T* Zp = reinterpret_cast<T*>(Zt);
-  const SweepOp* ops = single ? E.d_ops_single : E.d_ops;
-  int nops = single ? E.nops_single : E.nops_double;
-  int ldf = E.ldf;
-  long long budget = E.opts.timeout_cycles;
-  void* args[] = {(void*)&Fp, (void*)&ldf, (void*)&E.m, (void*)&C, (void*)&CT, (void*)&Rp, (void*)&Vp, (void*)&Zp,
-                  (void*)&ops, (void*)&nops, (void*)&E.coef, (void*)&E.bar, (void*)&E.err, (void*)&budget};
+  void* args[] = {(void*)&p};
   cudaMemsetAsync(E.bar, 0, sizeof(unsigned), E.stream);
-  return E.launch_coop((const void*)fn, grid, 256, smem, args);
+  return E.launch_coop((const void*)fn, E.sweep_grid(), 256, smem, args);
 }
 
 int Engine::run_sweep(const void* Rin, void* V, void* Zt, int C, bool single) {
   const int nops = single ? nops_single : nops_double;
+  const int ct = sweep_ct();
+  const int ntile = (C + ct - 1) / ct;
   const double elem = (double)sweep_elem();
-  const double fbytes = (double)nops * m * m * elem + 2.0 * m * m * C * elem;
+  // algorithmic bytes: every block step streams one m x m factor block once for all columns,
+  // the right-hand-side lines are read once and the output lines written once
+  const double fbytes = (double)nops * m * m * elem + 2.0 * m * m * (double)ntile * ct * elem;
+  const int nbuf = sweep_smem(2) <= 220 * 1024 ? 2 : 1;
+  if (sweep_smem(nbuf) > 220 * 1024) {
+    set_error("grid too large for the sweep kernel's shared-memory tiles");
+    return HH_EINVAL;
+  }
   tick_begin(K_SWEEP);
   cudaError_t ce;
-  int cc = (C % 4 == 0) ? 4 : ((C % 2 == 0) ? 2 : 1);
-  // the shared-memory input tile must hold at least one column group
-  while (cc > 1 && (size_t)m * cc * sweep_elem() > 190 * 1024) cc >>= 1;
-  if (precision == HH_PREC_FP32) {
-    ce = cc == 4 ? launch_sweep_t<float, 4>(*this, Rin, V, Zt, C, single)
-                 : (cc == 2 ? launch_sweep_t<float, 2>(*this, Rin, V, Zt, C, single)
-                            : launch_sweep_t<float, 1>(*this, Rin, V, Zt, C, single));
-  } else {
-    ce = cc == 4 ? launch_sweep_t<double, 4>(*this, Rin, V, Zt, C, single)
-                 : (cc == 2 ? launch_sweep_t<double, 2>(*this, Rin, V, Zt, C, single)
-                            : launch_sweep_t<double, 1>(*this, Rin, V, Zt, C, single));
-  }
-  tick_end(K_SWEEP, fbytes, (double)nops * m * m * C * 8.0);
+  if (precision == HH_PREC_FP32)
+    ce = nbuf == 2 ? launch_sweep_t<float, 4, 2>(*this, Rin, V, Zt, ntile, single)
+                   : launch_sweep_t<float, 4, 1>(*this, Rin, V, Zt, ntile, single);
+  else
+    ce = nbuf == 2 ? launch_sweep_t<double, 2, 2>(*this, Rin, V, Zt, ntile, single)
+                   : launch_sweep_t<double, 2, 1>(*this, Rin, V, Zt, ntile, single);
+  tick_end(K_SWEEP, fbytes, (double)nops * m * m * ntile * ct * 8.0);
   last_columns = C;
   if (ce != cudaSuccess) { set_cuda_error(ce, "sweep launch"); return HH_ECUDA; }
   return HH_OK;
@@ -260,14 +390,16 @@ int Engine::run_sweep(const void* Rin, void* V, void* Zt, int C, bool single) {
 template <typename R>
 static void launch_pack_t(Engine& E, const double2* const* srcptr, const double* scale, int C, int t, int4 codes,
                           void* X) {
-  pack_kernel<R><<<E.grid_for((size_t)E.m * E.m * C), 256, 0, E.stream>>>(srcptr, scale, C, t, codes, E.n,
-                                                                           reinterpret_cast<typename Cx<R>::T*>(X));
+  const int ct = E.sweep_ct(), ntile = (C + ct - 1) / ct;
+  pack_kernel<R><<<E.grid_for((size_t)E.m * E.m * ntile * ct), 256, 0, E.stream>>>(
+      srcptr, scale, C, t, codes, E.n, ct, ntile, reinterpret_cast<typename Cx<R>::T*>(X));
   E.count_launch();
 }
 template <typename R>
 static void launch_unpack_t(Engine& E, const void* X, int C, int t, int4 codes, double2* dst, size_t stride) {
-  unpack_kernel<R><<<E.grid_for((size_t)E.m * E.m * C), 256, 0, E.stream>>>(
-      reinterpret_cast<const typename Cx<R>::T*>(X), C, t, codes, E.n, dst, stride);
+  const int ct = E.sweep_ct(), ntile = (C + ct - 1) / ct;
+  unpack_kernel<R><<<E.grid_for((size_t)E.m * E.m * ntile * ct), 256, 0, E.stream>>>(
+      reinterpret_cast<const typename Cx<R>::T*>(X), C, t, codes, E.n, ct, ntile, dst, stride);
   E.count_launch();
 }
 
