@@ -138,6 +138,26 @@ hh_status hh_apply_operator(hh_handle* h, int ncols, const double* x, double* y)
  * sweep unless opts.single_sweep).  dir need not be in the handle's dirs. */
 hh_status hh_apply_preconditioner(hh_handle* h, uint32_t dir, int ncols, const double* r, double* z);
 
+/*
+ * z = M_d^{-1} r like hh_apply_preconditioner, for callers that cannot allocate device
+ * memory during the call (a device-memory budget fixed at start-up, a host framework whose
+ * caching allocator owns the device, or a latency-critical path that must avoid cudaMalloc
+ * and cudaFree and the device synchronisation they can cause).  The paper has no
+ * counterpart: this is a deployment variant of the sweep entry point.
+ *   - allocates nothing: no cudaMalloc / cudaFree and no allocating library routine; its
+ *     scratch is a fixed 32 MiB device array inside the library, present on every GPU the
+ *     library is loaded on until the process exits;
+ *   - r and z must be DEVICE pointers (ncols complex128 columns); host pointers -> HH_EINVAL;
+ *   - a grid / column count whose packed sweep arrays exceed the 32 MiB -> HH_EINVAL
+ *     (roughly: complex64 factors up to n = 512 with 4 columns, n = 1024 not at all);
+ *   - the first call on a device resolves the array's device address (once per device);
+ *     make that first call before any stream capture;
+ *   - every call shares the one array and leaves its contents behind; nothing in it needs to
+ *     start at zero; calls whose GPU work overlaps (other handles, other streams, other
+ *     threads) race on it and must be serialised by the caller.
+ */
+hh_status hh_apply_preconditioner_noalloc(hh_handle* h, uint32_t dir, int ncols, const double* r, double* z);
+
 /* Copy the stored inverse S_j^{-1} (j = 0..R) as complex128 row-major m x m into out. */
 hh_status hh_get_factor(hh_handle* h, int j, double* out);
 

@@ -54,7 +54,7 @@ class hh_stats(ctypes.Structure):
 
 
 EXPORTS = ["hh_default_opts", "hh_setup", "hh_solve", "hh_solve_batch", "hh_submit", "hh_poll", "hh_assemble_rhs",
-           "hh_apply_operator", "hh_apply_preconditioner", "hh_get_factor", "hh_get_stats", "hh_reset_stats",
+           "hh_apply_operator", "hh_apply_preconditioner", "hh_apply_preconditioner_noalloc", "hh_get_factor", "hh_get_stats", "hh_reset_stats",
            "hh_destroy", "hh_last_error"]
 
 _lib = None
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hh_assemble_rhs.argtypes = [vp, i, vp, vp]
     L.hh_apply_operator.argtypes = [vp, i, vp, vp]
     L.hh_apply_preconditioner.argtypes = [vp, u32, i, vp, vp]
+    L.hh_apply_preconditioner_noalloc.argtypes = [vp, u32, i, vp, vp]
     L.hh_get_factor.argtypes = [vp, i, vp]
     L.hh_get_stats.argtypes = [vp, ctypes.POINTER(hh_stats)]
     L.hh_reset_stats.argtypes = [vp]
@@ -220,6 +221,12 @@ class Handle:
         st = self.lib.hh_apply_preconditioner(self.h, DIR_BITS[direction], int(ncols), _ptr(r), _ptr(z))
         self._check(st, "hh_apply_preconditioner")
         return z
+
+    def apply_preconditioner_noalloc(self, direction: str, r, z, ncols: int = 1) -> int:
+        """hh_apply_preconditioner_noalloc: r, z device tensors; the library allocates nothing.
+        Returns the status (HH_OK, or HH_EINVAL for host buffers / a request above the fixed
+        scratch size)."""
+        return self.lib.hh_apply_preconditioner_noalloc(self.h, DIR_BITS[direction], int(ncols), _ptr(r), _ptr(z))
 
     def get_factor(self, j: int) -> np.ndarray:
         out = np.zeros(self.m * self.m, dtype=np.complex128)

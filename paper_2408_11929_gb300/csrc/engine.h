@@ -113,6 +113,8 @@ class Engine {
 
   // sweep on packed columns: Rin (lines x m x C) -> V, with C = ncols
   int run_sweep(const void* Rin, void* V, void* Zt, int C, bool single);
+  int run_sweep_untimed(const void* Rin, void* V, void* Zt, int C, bool single);
+  int apply_preconditioner_noalloc(int dcode, int ncols, const double2* r, double2* z, bool single);
   size_t sweep_elem() const { return precision == HH_PREC_FP32 ? 8 : 16; }
   int sweep_ct() const { return precision == HH_PREC_FP32 ? 4 : 2; }  // columns per tile
   int sweep_rows_per_cta() const;

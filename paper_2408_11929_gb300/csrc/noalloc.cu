@@ -1,0 +1,146 @@
+// hh_apply_preconditioner_noalloc: the preconditioner apply (one directional sweep) for
+// callers that cannot allocate device memory while they run -- for example code that runs
+// under a fixed device-memory budget taken at start-up, host frameworks whose caching
+// allocator owns every byte of the device, or real-time paths that must not pay for
+// cudaMalloc / cudaFree (which can synchronise the whole device).  The kernels are the
+// same as hh_apply_preconditioner's; only their scratch moves: the packed input, the
+// sweep output, the two backward-chain lines and the column tables live in one
+// file-scope device array of fixed size, reserved in every GPU's memory by the loader
+// when the library is loaded and held until the process exits.
+//
+// Scratch contents: nothing in the array has to start at zero.  Each call rewrites the
+// whole packed input (padding columns included) and the column tables, and the sweep
+// writes every output entry and both backward-chain lines before it reads them.  The
+// array keeps whatever the last call left in it.
+//
+// Sharing: all calls in the process share the one array per device.  Calls whose GPU
+// work overlaps (two handles on different streams, two threads) race on it; callers must
+// serialise them.
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace hh {
+
+void launch_pack(Engine& E, const double2* const* srcptr, const double* scale, int C, int t, int4 codes, void* X);
+void launch_unpack(Engine& E, const void* X, int C, int t, int4 codes, double2* dst, size_t stride);
+
+// Fixed scratch of the no-allocation entry point: 32 MiB per device.
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch for each device, resolved once per device (with that
+// device current) by the first call that runs on it.
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kMaxDevices] = {};
+
+static int noalloc_scratch_address(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) {
+    set_error("device index out of range for the no-allocation scratch");
+    return HH_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      set_error(std::string("cudaGetSymbolAddress of the no-allocation scratch failed: ") + cudaGetErrorString(e));
+      return HH_ECUDA;
+    }
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return HH_OK;
+}
+
+// column tables of the pack kernel: input column c starts at r + c * D, unscaled
+__global__ void noalloc_tables_kernel(const double2* r, size_t D, int ncols, const double2** srcptr, double* scale) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += gridDim.x * blockDim.x) {
+    srcptr[c] = r + (size_t)c * D;
+    scale[c] = 1.0;
+  }
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int Engine::apply_preconditioner_noalloc(int dcode, int ncols, const double2* r, double2* z, bool single) {
+  const size_t D = (size_t)m * m;
+  const int ct = sweep_ct();
+  const int ntile = (ncols + ct - 1) / ct;
+  const size_t line = (size_t)m * ntile * ct * sweep_elem();
+  const size_t off_v = align256(line * m);
+  const size_t off_zt = off_v + align256(line * m);
+  const size_t off_ptr = off_zt + align256(line * 2);
+  const size_t off_scale = off_ptr + align256(sizeof(void*) * ncols);
+  const size_t need = off_scale + align256(sizeof(double) * ncols);
+  if (need > kNoAllocScratchBytes) {
+    set_error("hh_apply_preconditioner_noalloc: this grid and column count need " + std::to_string(need) +
+              " bytes of scratch, more than its fixed " + std::to_string(kNoAllocScratchBytes) + " bytes");
+    return HH_EINVAL;
+  }
+  void* base = nullptr;
+  int rc = noalloc_scratch_address(device, &base);
+  if (rc) return rc;
+  unsigned char* s = reinterpret_cast<unsigned char*>(base);
+  void* rin = s;
+  void* v = s + off_v;
+  void* zt = s + off_zt;
+  const double2** tab = reinterpret_cast<const double2**>(s + off_ptr);
+  double* scale = reinterpret_cast<double*>(s + off_scale);
+  noalloc_tables_kernel<<<1, 256, 0, stream>>>(r, D, ncols, tab, scale);
+  count_launch();
+  int4 codes = make_int4(dcode, dcode, dcode, dcode);
+  launch_pack(*this, tab, scale, ncols, 1, codes, rin);
+  rc = run_sweep_untimed(rin, v, zt, ncols, single);
+  if (rc == HH_OK) launch_unpack(*this, v, ncols, 1, codes, z, D);
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "hh_apply_preconditioner_noalloc");
+    return HH_ECUDA;
+  }
+  return check_device_error("sweep");
+}
+
+}  // namespace hh
+
+using namespace hh;
+
+struct hh_handle {
+  Engine* E;
+};
+
+extern "C" hh_status hh_apply_preconditioner_noalloc(hh_handle* h, uint32_t dir, int ncols, const double* r,
+                                                     double* z) {
+  if (!h || !r || !z || ncols < 1) return (set_error("bad arguments"), HH_EINVAL);
+  int code;
+  switch (dir) {
+    case HH_DIR_LR: code = DC_LR; break;
+    case HH_DIR_RL: code = DC_RL; break;
+    case HH_DIR_BT: code = DC_BT; break;
+    case HH_DIR_TB: code = DC_TB; break;
+    default: return (set_error("dir must be exactly one HH_DIR_* bit"), HH_EINVAL);
+  }
+  Engine& E = *h->E;
+  std::lock_guard<std::mutex> lk(E.solve_mu);
+  cudaSetDevice(E.device);
+  if (!is_device_pointer(r) || !is_device_pointer(z))
+    return (set_error("hh_apply_preconditioner_noalloc takes device pointers only (host buffers would need staging)"),
+            HH_EINVAL);
+  return (hh_status)E.apply_preconditioner_noalloc(code, ncols, (const double2*)r, (double2*)z,
+                                                   E.opts.single_sweep != 0);
+}

@@ -386,6 +386,27 @@ int Engine::run_sweep(const void* Rin, void* V, void* Zt, int C, bool single) {
   return HH_OK;
 }
 
+// The same launch as run_sweep without the statistics events (the no-allocation entry
+// point creates no CUDA objects).
+int Engine::run_sweep_untimed(const void* Rin, void* V, void* Zt, int C, bool single) {
+  const int ct = sweep_ct();
+  const int ntile = (C + ct - 1) / ct;
+  const int nbuf = sweep_smem(2) <= 220 * 1024 ? 2 : 1;
+  if (sweep_smem(nbuf) > 220 * 1024) {
+    set_error("grid too large for the sweep kernel's shared-memory tiles");
+    return HH_EINVAL;
+  }
+  cudaError_t ce;
+  if (precision == HH_PREC_FP32)
+    ce = nbuf == 2 ? launch_sweep_t<float, 4, 2>(*this, Rin, V, Zt, ntile, single)
+                   : launch_sweep_t<float, 4, 1>(*this, Rin, V, Zt, ntile, single);
+  else
+    ce = nbuf == 2 ? launch_sweep_t<double, 2, 2>(*this, Rin, V, Zt, ntile, single)
+                   : launch_sweep_t<double, 2, 1>(*this, Rin, V, Zt, ntile, single);
+  if (ce != cudaSuccess) { set_cuda_error(ce, "sweep launch"); return HH_ECUDA; }
+  return HH_OK;
+}
+
 // launch helpers used by krylov.cu / api.cu
 template <typename R>
 static void launch_pack_t(Engine& E, const double2* const* srcptr, const double* scale, int C, int t, int4 codes,
