@@ -10,8 +10,8 @@ One iteration:
   2. Block classical Gram-Schmidt against the current basis V, done twice (CGS2); the
      projection coefficients of both passes are summed into the new Hessenberg columns.
   3. The t columns of W are then orthonormalised one after the other, in preconditioner
-     order, against the new vectors already accepted in this iteration (again twice),
-     giving a real positive diagonal r_jj.  Column j is DEFLATED (its Z column dropped)
+     order, each by classical Gram-Schmidt against the new vectors already accepted in this
+     iteration (again twice), giving a real positive diagonal r_jj.  Column j is DEFLATED (its Z column dropped)
      when r_jj <= eta * ||w_j||, ||w_j|| taken after step 2.
   4. The Hessenberg matrix stays scalar upper Hessenberg; the previous complex Givens
      rotations are applied to each new column and one new rotation zeroes its
@@ -107,11 +107,12 @@ def solve(A, precs, b: np.ndarray, tol: float = 1e-8, maxit: int = 200, scheme: 
         for j in range(t):
             w = W[j]
             for _ in range(passes):
-                for q, vq in enumerate(new_v):
-                    c = np.vdot(vq, w)
-                    nip += 1
-                    w = w - c * vq
-                    Rnew[q, j] += c
+                if new_v:
+                    Vn = np.array(new_v).T               # accepted new vectors of this block
+                    c = Vn.conj().T @ w
+                    nip += len(new_v)
+                    w = w - Vn @ c
+                    Rnew[:len(new_v), j] += c
             rjj = np.linalg.norm(w)
             nip += 1
             if rjj <= eta * nu[j] or rjj == 0.0:
