@@ -319,6 +319,41 @@ def run_fp64(w, local):
             "rel_res_explicit": res.rel_res_explicit}
 
 
+def run_sweep_only(args):
+    """One direction's double sweep on 4 columns (the column count of one 4-direction solve
+    iteration), k = 0.39 n, timed with CUDA events on the launching stream."""
+    import torch
+    import __graft_entry__
+    import paper_2408_11929_gb300 as hh
+    __graft_entry__.build()
+    k = 400.0 * args.n / 1024
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = hh.Handle(k, args.n, args.strips, "LR+RL+BT+TB", precision=args.precision, profile=1,
+                      stream=stream.cuda_stream)
+        dofs = (args.n + 1) ** 2
+        r = torch.from_numpy(np.ascontiguousarray(hh_inputs.random_vector(dofs, 4, seed=1).ravel())).cuda()
+        z = torch.zeros_like(r)
+        for _ in range(args.warmup):
+            h.apply_preconditioner("BT", r, 4, z)
+        h.reset_stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            h.apply_preconditioner("BT", r, 4, z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = h.stats()
+        h.close()
+    ms = st["sweep_ms"] / max(1, st["sweep_launches"])
+    print(json.dumps({"mode": "sweep", "n": args.n, "strips": args.strips, "precision": args.precision,
+                      "sweep_ms": ms, "steps_per_launch": st["sweep_steps"],
+                      "us_per_step": ms * 1e3 / st["sweep_steps"],
+                      "GBps": st["sweep_bytes"] / max(1, st["sweep_launches"]) / (ms / 1e3) / 1e9,
+                      "total_ms": e0.elapsed_time(e1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,7 +362,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep"],
+                    help="sweep: time hh_apply_preconditioner alone (4 columns) -- the profiling case")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--strips", type=int, default=32)
+    ap.add_argument("--precision", default="fp32")
     args = ap.parse_args()
+    if args.mode == "sweep":
+        run_sweep_only(args)
+        return
     ws, rank, local = dist_env()
     w = hh_inputs.workload(WORKLOAD)
 

@@ -154,24 +154,16 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
     own_stream = true;
   }
   coop_per_sm = std::max(1, qr_blocks_per_sm());
-  if (sweep_smem(1) > 220 * 1024)
-    return (set_error("n too large: the sweep kernel's factor rows and line tiles exceed shared memory"), HH_EINVAL);
 
-  const size_t fbytes = (size_t)(R + 1) * m * ldf * sweep_elem();
+  const size_t fbytes = (size_t)factor_blocks() * m * ldf * sweep_elem();
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   if (fbytes + (64ull << 20) > free_b) return (set_error("strip factors do not fit in free device memory"), HH_ENOMEM);
   if (dmalloc(&factors, fbytes) || dmalloc((void**)&bar, 64) || dmalloc((void**)&err, 64)) return HH_ENOMEM;
   cudaMemsetAsync(bar, 0, 64, stream);
   cudaMemsetAsync(err, 0, 64, stream);
-  auto sd = build_schedule(n, N, true);
-  auto ss = build_schedule(n, N, false);
-  nops_double = (int)sd.size();
-  nops_single = (int)ss.size();
-  if (dmalloc((void**)&d_ops, sd.size() * sizeof(SweepOp)) || dmalloc((void**)&d_ops_single, ss.size() * sizeof(SweepOp)))
-    return HH_ENOMEM;
-  cudaMemcpyAsync(d_ops, sd.data(), sd.size() * sizeof(SweepOp), cudaMemcpyHostToDevice, stream);
-  cudaMemcpyAsync(d_ops_single, ss.data(), ss.size() * sizeof(SweepOp), cudaMemcpyHostToDevice, stream);
+  steps_double = build_steps(n, N, true);
+  steps_single = build_steps(n, N, false);
   cudaStreamSynchronize(stream);
 
   cudaEvent_t a, b;
@@ -200,8 +192,8 @@ Engine::~Engine() {
   if (stream) cudaStreamSynchronize(stream);
   collect_ticks();
   for (auto ev : event_pool) cudaEventDestroy(ev);
-  dfree(factors); dfree(bar); dfree(err); dfree(d_ops); dfree(d_ops_single);
-  dfree(w_rin); dfree(w_v); dfree(w_zt);
+  dfree(factors); dfree(bar); dfree(err);
+  dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
@@ -435,12 +427,12 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->setup_ms = E.setup_ms_total;
   st->setup_flops = E.flops[Engine::K_SETUP];
   st->kernel_launches = E.kernel_launches;
-  st->factor_bytes = (int64_t)(E.R + 1) * E.m * E.ldf * (int64_t)E.sweep_elem();
-  st->factor_blocks = E.R + 1;
+  st->factor_bytes = (int64_t)E.factor_blocks() * E.m * E.ldf * (int64_t)E.sweep_elem();
+  st->factor_blocks = E.factor_blocks();
   st->m = E.m;
   st->ldf = E.ldf;
   st->columns = E.last_columns;
-  st->sweep_steps = E.opts.single_sweep ? E.nops_single : E.nops_double;
+  st->sweep_steps = (int64_t)(E.opts.single_sweep ? E.steps_single.size() : E.steps_double.size());
   return HH_OK;
 }
 

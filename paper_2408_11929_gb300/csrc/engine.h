@@ -19,22 +19,21 @@ namespace hh {
 
 void set_error(const std::string& msg);
 
-// One step of the batched sweep (see sweep.cu): out line <- / -= F_f * x, where
-// x = Rin[base_line] + sign * C(src line), C = coupling to the line below (L) or above (U).
-struct SweepOp {
-  int f;          // factor block
-  int out_line;   // V line that receives the result
-  int out_sub;    // 0: V = z, 1: V -= z
-  int zsave;      // -1 or Zt slot that also receives z
-  int base_line;  // Rin line added to x, or -1
-  int cpl;        // 0 none, 1 lower (line below), 2 upper (line above)
-  int cpl_src;    // 0: V[cpl_line], 1: Zt[0], 2: Zt[1]
-  int cpl_line;
-  int cpl_neg;    // 1: x -= C(src)
-  int pad[3];
+// One step of the batched sweep (see sweep.cu): for strips s0 .. s0+ns-1,
+//   out[out_j] (set / -= / +=) F_f * x,   x = base[base_j] +- C(src[src_j], strip s + src_ds)
+// with C the identity or the coupling to the line below (L) / above (U), and optionally the
+// result also accumulated into acc[acc_j].  Buffers: SB_RIN (packed right-hand sides), SB_V
+// (sweep result), SB_W (corrections).
+enum SweepBuf { SB_NONE = 0, SB_RIN = 1, SB_V = 2, SB_W = 3 };
+struct SweepStep {
+  int f, s0, ns;
+  int base, base_j;
+  int src, src_j, src_ds, cpl, neg;
+  int out, out_j, out_mode;
+  int acc, acc_j, acc_mode;
 };
 
-std::vector<SweepOp> build_schedule(int n, int N, bool double_sweep);
+std::vector<SweepStep> build_steps(int n, int N, bool double_sweep);
 
 // Direction codes of the BT frame mapping (node of the BT frame -> node of the grid).
 enum DirCode { DC_BT = 0, DC_TB = 1, DC_LR = 2, DC_RL = 3 };
@@ -56,13 +55,10 @@ class Engine {
   bool own_stream = false;
 
   // device buffers
-  void* factors = nullptr;  // (R+1) blocks of m x ldf complex (precision-dependent)
+  void* factors = nullptr;  // R+3 blocks of m x ldf complex: F_0..F_R, G, K (setup.cu)
   unsigned* bar = nullptr;  // grid barrier counter
   int* err = nullptr;       // device error word
-  SweepOp* d_ops = nullptr; // sweep schedule (double sweep)
-  int nops_double = 0;
-  SweepOp* d_ops_single = nullptr;
-  int nops_single = 0;
+  std::vector<SweepStep> steps_double, steps_single;  // sweep schedules
   size_t bytes_allocated = 0;
 
   // statistics
@@ -111,20 +107,24 @@ class Engine {
   int assemble_rhs(int nsrc, const double* src_host, double2* rhs);
   int solve_batch_dev(int nrhs, const double2* rhs, double2* x, double tol, hh_result* res);
 
-  // sweep on packed columns: Rin (lines x m x C) -> V, with C = ncols
-  int run_sweep(const void* Rin, void* V, void* Zt, int C, bool single);
-  int run_sweep_untimed(const void* Rin, void* V, void* Zt, int C, bool single);
+  // sweep on packed columns (strip-interleaved layout, C columns): Rin -> V, W = corrections
+  int run_sweep(const void* Rin, void* V, void* W, int C, bool single);
+  int run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool single, void* partial,
+                        size_t partial_bytes);  // partial: split-K slices (or nullptr)
   int apply_preconditioner_noalloc(int dcode, int ncols, const double2* r, double2* z, bool single);
   size_t sweep_elem() const { return precision == HH_PREC_FP32 ? 8 : 16; }
-  int sweep_ct() const { return precision == HH_PREC_FP32 ? 4 : 2; }  // columns per tile
-  int sweep_rows_per_cta() const;
-  int sweep_grid() const;
-  size_t sweep_smem(int nbuf) const;
+  size_t sweep_ws_bytes(int C) const;          // bytes of one packed sweep array
+  double sweep_flops(int C, bool single) const;
+  double sweep_bytes(int C, bool single) const;
+  int factor_blocks() const { return R + 3; }
 
   // sweep workspaces (grown on demand)
   void* w_rin = nullptr;
   void* w_v = nullptr;
-  void* w_zt = nullptr;
+  void* w_w = nullptr;
+  void* w_partial = nullptr;   // split-K slices of the sweep GEMM steps
+  size_t w_partial_bytes = 0;
+  size_t sweep_partial_bytes(int C) const;
   size_t w_cap_cols = 0;
   int ensure_sweep_ws(int C);
 };

@@ -668,7 +668,7 @@ int Engine::solve_batch_dev(int nrhs, const double2* b, double2* x, double tol, 
     vblocks.push_back(Vk);
     // preconditioners: every (rhs, direction) pair is one sweep column
     launch_pack(*this, S.srcptr, S.scale, C, t, codes, w_rin);
-    rc = run_sweep(w_rin, w_v, w_zt, C, opts.single_sweep != 0);
+    rc = run_sweep(w_rin, w_v, w_w, C, opts.single_sweep != 0);
     if (rc) break;
     launch_unpack(*this, w_v, C, t, codes, Zk, D);
     // W = A Z_k
@@ -800,7 +800,7 @@ int Engine::apply_preconditioner_dev(int dcode, int ncols, const double2* r, dou
   cudaMemcpyAsync(ds, hs.data(), sizeof(double) * ncols, cudaMemcpyHostToDevice, stream);
   int4 codes = make_int4(dcode, dcode, dcode, dcode);
   launch_pack(*this, dp, ds, ncols, 1, codes, w_rin);
-  int rc = run_sweep(w_rin, w_v, w_zt, ncols, single);
+  int rc = run_sweep(w_rin, w_v, w_w, ncols, single);
   if (rc == HH_OK) launch_unpack(*this, w_v, ncols, 1, codes, z, D);
   cudaError_t e = cudaStreamSynchronize(stream);
   dfree(dp);

@@ -4,14 +4,14 @@
 // allocator owns every byte of the device, or real-time paths that must not pay for
 // cudaMalloc / cudaFree (which can synchronise the whole device).  The kernels are the
 // same as hh_apply_preconditioner's; only their scratch moves: the packed input, the
-// sweep output, the two backward-chain lines and the column tables live in one
+// sweep output, the correction array, the column tables and the split-K slices live in one
 // file-scope device array of fixed size, reserved in every GPU's memory by the loader
 // when the library is loaded and held until the process exits.
 //
 // Scratch contents: nothing in the array has to start at zero.  Each call rewrites the
-// whole packed input (padding columns included) and the column tables, and the sweep
-// writes every output entry and both backward-chain lines before it reads them.  The
-// array keeps whatever the last call left in it.
+// whole packed input (padding entries included) and the column tables, and every sweep step
+// writes the lines it produces before a later step reads them.  The array keeps whatever
+// the last call left in it.
 //
 // Sharing: all calls in the process share the one array per device.  Calls whose GPU
 // work overlaps (two handles on different streams, two threads) race on it; callers must
@@ -79,14 +79,15 @@ static bool is_device_pointer(const void* p) {
 
 int Engine::apply_preconditioner_noalloc(int dcode, int ncols, const double2* r, double2* z, bool single) {
   const size_t D = (size_t)m * m;
-  const int ct = sweep_ct();
-  const int ntile = (ncols + ct - 1) / ct;
-  const size_t line = (size_t)m * ntile * ct * sweep_elem();
-  const size_t off_v = align256(line * m);
-  const size_t off_zt = off_v + align256(line * m);
-  const size_t off_ptr = off_zt + align256(line * 2);
+  const size_t arr = sweep_ws_bytes(ncols);
+  const size_t off_v = align256(arr);
+  const size_t off_w = off_v + align256(arr);
+  const size_t off_ptr = off_w + align256(arr);
   const size_t off_scale = off_ptr + align256(sizeof(void*) * ncols);
   const size_t need = off_scale + align256(sizeof(double) * ncols);
+  // whatever is left of the array holds split-K slices of the GEMM steps (fewer slices, or
+  // none, when it is small)
+  const size_t off_part = need;
   if (need > kNoAllocScratchBytes) {
     set_error("hh_apply_preconditioner_noalloc: this grid and column count need " + std::to_string(need) +
               " bytes of scratch, more than its fixed " + std::to_string(kNoAllocScratchBytes) + " bytes");
@@ -98,14 +99,15 @@ int Engine::apply_preconditioner_noalloc(int dcode, int ncols, const double2* r,
   unsigned char* s = reinterpret_cast<unsigned char*>(base);
   void* rin = s;
   void* v = s + off_v;
-  void* zt = s + off_zt;
+  void* w = s + off_w;
   const double2** tab = reinterpret_cast<const double2**>(s + off_ptr);
   double* scale = reinterpret_cast<double*>(s + off_scale);
   noalloc_tables_kernel<<<1, 256, 0, stream>>>(r, D, ncols, tab, scale);
   count_launch();
   int4 codes = make_int4(dcode, dcode, dcode, dcode);
   launch_pack(*this, tab, scale, ncols, 1, codes, rin);
-  rc = run_sweep_untimed(rin, v, zt, ncols, single);
+  const size_t part_bytes = kNoAllocScratchBytes > off_part ? kNoAllocScratchBytes - off_part : 0;
+  rc = run_sweep_untimed(rin, v, w, ncols, single, part_bytes ? s + off_part : nullptr, part_bytes);
   if (rc == HH_OK) launch_unpack(*this, v, ncols, 1, codes, z, D);
   cudaError_t e = cudaStreamSynchronize(stream);
   if (rc) return rc;

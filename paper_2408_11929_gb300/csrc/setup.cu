@@ -9,11 +9,18 @@
 // and the last strip adds S_R = D_TOP - L S_{R-1}^{-1} U.  The R+1 dense inverses
 // F_j = S_j^{-1} (m x m, m = n+1) are the stored factors.  L couples a line to the line
 // below (vertical edge + cell diagonal), U = L^T.
+//
+// For the sweep's interface chains (sweep.cu) setup also forms, for the strips visited
+// before the last one, the first-line response of the strip inverse at its last line,
+//     Y_0 = F_0,  Y_j = -F_j L Y_{j-1}   (j = 1..R-1),   Y_{R-1} = D^{-1}[R-1, 0],
+// and stores G = Y_{R-1} L and K = Y_{R-1}^T U (D is complex symmetric, so
+// D^{-1}[0, R-1] = Y_{R-1}^T) as blocks R+1 and R+2.
 #include <cstdio>
 #include <vector>
 
 #include "common.cuh"
 #include "engine.h"
+#include "gemm.cuh"
 
 namespace hh {
 
@@ -156,6 +163,76 @@ __global__ void gj_permute(const typename Cx<R>::T* W, int ldw, const int* srcid
   }
 }
 
+// Z = L Y   (row a of Z couples line-node a to nodes a and a-1 of the line below)
+template <typename R>
+__global__ void lmul_kernel(const typename Cx<R>::T* __restrict__ Y, typename Cx<R>::T* __restrict__ Z, int m, int ld,
+                            Coef cf) {
+  using T = typename Cx<R>::T;
+  const R dg = (R)cf.diag();
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)m * m; idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / m), b = (int)(idx % m);
+    const double2 va = cf.vert(a);
+    T v = cmul(mk<T>(va.x, va.y), Y[(size_t)a * ld + b]);
+    if (a >= 1) { const T y = Y[(size_t)(a - 1) * ld + b]; v.x += dg * y.x; v.y += dg * y.y; }
+    Z[(size_t)a * ld + b] = v;
+  }
+}
+
+// G = Y L and K = Y^T U (L[p][p] = vert(p), L[p][p-1] = diag; U[p][p] = vert(p), U[p][p+1] = diag)
+template <typename R>
+__global__ void interface_kernel(const typename Cx<R>::T* __restrict__ Y, typename Cx<R>::T* __restrict__ G,
+                                 typename Cx<R>::T* __restrict__ K, int m, int ld, Coef cf) {
+  using T = typename Cx<R>::T;
+  const R dg = (R)cf.diag();
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)m * ld; idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / ld), b = (int)(idx % ld);
+    if (b >= m) { G[idx] = mk<T>(0, 0); K[idx] = mk<T>(0, 0); continue; }
+    const double2 vb = cf.vert(b);
+    const T tvb = mk<T>(vb.x, vb.y);
+    T g = cmul(Y[(size_t)a * ld + b], tvb);
+    if (b + 1 < m) { const T y = Y[(size_t)a * ld + b + 1]; g.x += dg * y.x; g.y += dg * y.y; }
+    T k = cmul(Y[(size_t)b * ld + a], tvb);
+    if (b >= 1) { const T y = Y[(size_t)(b - 1) * ld + a]; k.x += dg * y.x; k.y += dg * y.y; }
+    G[idx] = g;
+    K[idx] = k;
+  }
+}
+
+template <typename R>
+int interface_blocks(Engine& E, typename Cx<R>::T* bufA, typename Cx<R>::T* bufB) {
+  using T = typename Cx<R>::T;
+  const int m = E.m, ld = E.ldf, Rr = E.R;
+  T* F = reinterpret_cast<T*>(E.factors);
+  const size_t blk = (size_t)m * ld;
+  const T* Y = F;  // Y_0 = F_0
+  T* Yn[2] = {bufA, bufB};
+  T* Z = nullptr;
+  if (E.dmalloc((void**)&Z, blk * sizeof(T))) return HH_ENOMEM;
+  for (int j = 1; j <= Rr - 1; ++j) {
+    lmul_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(Y, Z, m, ld, E.coef);
+    E.tick_begin(Engine::K_SETUP);
+    if constexpr (sizeof(R) == 4) {  // 64 x 64 tiles (33 KB of shared memory for complex64)
+      dim3 grid((m + 63) / 64, (m + 63) / 64);
+      dense_gemm_kernel<R, 64, 64, 4, 4><<<grid, 256, 0, E.stream>>>(F + (size_t)j * blk, ld, Z, ld, Yn[j & 1], ld, m,
+                                                                     -1.0);
+    } else {               // 32 x 32 tiles for complex128 (same shared memory)
+      dim3 grid((m + 31) / 32, (m + 31) / 32);
+      dense_gemm_kernel<R, 32, 32, 2, 2><<<grid, 256, 0, E.stream>>>(F + (size_t)j * blk, ld, Z, ld, Yn[j & 1], ld, m,
+                                                                     -1.0);
+    }
+    E.tick_end(Engine::K_SETUP, 0.0, 8.0 * m * (double)m * m);
+    E.count_launch(2);
+    Y = Yn[j & 1];
+  }
+  interface_kernel<R><<<E.grid_for(blk), 256, 0, E.stream>>>(Y, F + (size_t)(Rr + 1) * blk, F + (size_t)(Rr + 2) * blk,
+                                                             m, ld, E.coef);
+  E.count_launch();
+  cudaError_t ce = cudaStreamSynchronize(E.stream);
+  E.dfree(Z);
+  if (ce != cudaSuccess) { E.set_cuda_error(ce, "interface blocks"); return HH_ECUDA; }
+  return HH_OK;
+}
+
 template <typename R>
 int factor_impl(Engine& E) {
   using T = typename Cx<R>::T;
@@ -193,8 +270,9 @@ int factor_impl(Engine& E) {
     status = E.check_device_error("strip setup");
   }
   cudaStreamSynchronize(E.stream);
-  E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
   if (status == HH_OK) status = E.check_device_error("strip setup");
+  if (status == HH_OK) status = interface_blocks<R>(E, bufA, bufB);
+  E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
   return status;
 }
 

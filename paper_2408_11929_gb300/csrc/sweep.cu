@@ -1,63 +1,114 @@
-// Batched directional double sweeps (Section 2, Eqs. (2)-(3)) as one persistent launch.
+// Batched directional double sweeps (Section 2, Eqs. (2)-(3)).
 //
 // Frame.  The mesh (cells cut along SW-NE diagonals) is invariant under the transpose
 // (i, j) -> (j, i) and the half-turn (i, j) -> (n-i, n-j), and so is A.  The four sweeps
 // are images of the bottom-to-top sweep BT under these maps (LR = transpose, TB = half
 // turn, RL = both, each with its strips mapped alike, the last strip visited owning the
-// extra line).  Every preconditioner application is therefore a BT sweep of a permuted
-// copy of its input: the pack kernel writes each (right-hand side, direction) pair as one
-// column of a line-major array X[line][node][column], one persistent kernel sweeps all
-// columns together -- every factor block read once per step serves all directions and
-// right-hand sides -- and the unpack kernel maps the columns back.
+// extra line).  Every preconditioner application is therefore a BT sweep of a permuted copy
+// of its input: the pack kernel writes each (right-hand side, direction) pair as one column
+// and all columns are swept together -- every strip factor read serves all directions,
+// right-hand sides and strips -- and the unpack kernel maps the columns back.
 //
-// Sweep in the BT frame, strips s = 0..N-1 of lines [sR, sR+R-1] (last: R+1 lines), with
-// the block Thomas factors F_j = S_j^{-1} of the strip matrix (setup.cu):
-//   forward  (strip s, j = 0..len-1): y_j = F_j (r_j - L y_{j-1})  (y_{-1}: last line of strip s-1)
-//            then x_j = y_j - F_j U x_{j+1} for j = len-2..0     (v_s = x)
-//   backward (strip s = N-2..0): z_{R-1} = F_{R-1} U u_{s+1}(first line),
-//            z_j = F_j (-U z_{j+1}), u_j = v_j - z_j            (u_{N-1} = v_{N-1}, Section 2)
-// L couples a line to the one below (vertical edge, cell diagonal), U = L^T to the one above.
+// Strip-interleaved layout.  Strip s (s = 0..N-1) owns BT-frame lines s R + j, j = 0..R-1
+// (the last strip also j = R).  Sweep arrays are X[j][i][s][c]: line-in-strip j, node i,
+// strip s, column c, so that one step of a block-Thomas recurrence over all strips is one
+// GEMM  F_j (m x m) * X[j] (m x N C).
+//
+// The double sweep (block Gauss-Seidel forward then backward over the strips) is computed
+// exactly, reorganised so that only the interface values travel from strip to strip:
+//   F1  w_s = D^{-1} r_s for every strip at once (block Thomas, 2R+1 GEMM steps);
+//   F2  interface chain t_s = w_s[R-1] - G t_{s-1},  G = D^{-1}[R-1, 0] L       (N-2 steps),
+//       where t_s is the last line of the forward solution v_s;
+//   F3  v_s = w_s + D^{-1} e_0 (-L t_{s-1}) for s >= 1 (block Thomas with a right-hand side
+//       on the first line only, 2R+1 GEMM steps; the last lines already hold t_s);
+//   B1  interface chain of the backward sweep on the first lines:
+//       u_s[0] = v_s[0] - K u_{s+1}[0],  K = D^{-1}[0, R-1] U = (D^{-1}[R-1, 0])^T U  (N-1 steps;
+//       D is complex symmetric, so D^{-1}[0, R-1] is the transpose of D^{-1}[R-1, 0]);
+//   B2  u_s[j] = v_s[j] - (D^{-1} e_{R-1} U u_{s+1}[0])[j] for j = R-1..1 (R-1 GEMM steps);
+//       u_{N-1} = v_{N-1} (one solve in the last strip, Section 2).
+// F_j are the block-Thomas inverses of the strip matrix, G and K come from setup.cu.
+// A single (forward-only) sweep stops after F3.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
 
 #include "common.cuh"
 #include "engine.h"
+#include "gemm.cuh"
 
 namespace hh {
 
-std::vector<SweepOp> build_schedule(int n, int N, bool double_sweep) {
-  std::vector<SweepOp> ops;
-  const int R = n / N;
-  auto mk_op = [](int f, int out_line, int out_sub, int zsave, int base, int cpl, int src, int cline, int neg) {
-    SweepOp o{};
-    o.f = f; o.out_line = out_line; o.out_sub = out_sub; o.zsave = zsave; o.base_line = base;
-    o.cpl = cpl; o.cpl_src = src; o.cpl_line = cline; o.cpl_neg = neg;
-    return o;
+std::vector<SweepStep> build_steps(int n, int N, bool double_sweep) {
+  std::vector<SweepStep> st;
+  const int R = n / N, last = N - 1;
+  const int FG = R + 1, FK = R + 2;  // block indices of G and K
+  auto mk_step = [](int f, int s0, int ns) {
+    SweepStep x{};
+    x.f = f; x.s0 = s0; x.ns = ns;
+    x.base = SB_NONE; x.src = SB_NONE; x.cpl = XC_NONE; x.acc = SB_NONE;
+    return x;
   };
-  for (int s = 0; s < N; ++s) {
-    const int a = s * R, len = (s == N - 1) ? R + 1 : R;
-    for (int j = 0; j < len; ++j) {
-      const int l = a + j;
-      ops.push_back(mk_op(j, l, 0, -1, l, l > 0 ? 1 : 0, 0, l - 1, 1));
+  // F1: forward elimination, all strips (line R only in the last strip)
+  for (int j = 0; j <= R; ++j) {
+    SweepStep x = mk_step(j, j == R ? last : 0, j == R ? 1 : N);
+    x.base = SB_RIN; x.base_j = j;
+    if (j >= 1) { x.src = SB_V; x.src_j = j - 1; x.cpl = XC_LOWER; x.neg = 1; }
+    x.out = SB_V; x.out_j = j; x.out_mode = OUT_SET;
+    st.push_back(x);
+  }
+  // F1: back substitution (line R-1 has a successor only in the last strip)
+  for (int j = R - 1; j >= 0; --j) {
+    SweepStep x = mk_step(j, j == R - 1 ? last : 0, j == R - 1 ? 1 : N);
+    x.src = SB_V; x.src_j = j + 1; x.cpl = XC_UPPER;
+    x.out = SB_V; x.out_j = j; x.out_mode = OUT_SUB;
+    st.push_back(x);
+  }
+  if (N >= 2) {
+    // F2: interface chain on the last lines
+    for (int s = 1; s <= N - 2; ++s) {
+      SweepStep x = mk_step(FG, s, 1);
+      x.src = SB_V; x.src_j = R - 1; x.src_ds = -1; x.cpl = XC_IDENT;
+      x.out = SB_V; x.out_j = R - 1; x.out_mode = OUT_SUB;
+      st.push_back(x);
     }
-    for (int j = len - 2; j >= 0; --j) {
-      const int l = a + j;
-      ops.push_back(mk_op(j, l, 1, -1, -1, 2, 0, l + 1, 0));
+    // F3: responses to the first-line coupling -L t_{s-1}, strips 1..N-1 (corrections in W)
+    for (int j = 0; j <= R; ++j) {
+      SweepStep x = mk_step(j, j == R ? last : 1, j == R ? 1 : N - 1);
+      x.src = (j == 0) ? SB_V : SB_W;
+      x.src_j = (j == 0) ? R - 1 : j - 1;
+      x.src_ds = (j == 0) ? -1 : 0;
+      x.cpl = XC_LOWER; x.neg = 1;
+      x.out = SB_W; x.out_j = j; x.out_mode = OUT_SET;
+      if (j == R) { x.acc = SB_V; x.acc_j = R; x.acc_mode = OUT_ADD; }
+      st.push_back(x);
+    }
+    for (int j = R - 1; j >= 0; --j) {
+      SweepStep x = mk_step(j, j == R - 1 ? last : 1, j == R - 1 ? 1 : N - 1);
+      x.src = SB_W; x.src_j = j + 1; x.cpl = XC_UPPER;
+      x.out = SB_W; x.out_j = j; x.out_mode = OUT_SUB;
+      x.acc = SB_V; x.acc_j = j; x.acc_mode = OUT_ADD;
+      st.push_back(x);
     }
   }
-  if (double_sweep) {
+  if (double_sweep && N >= 2) {
+    // B1: interface chain on the first lines, last strip first
     for (int s = N - 2; s >= 0; --s) {
-      const int a = s * R, b = a + R - 1;
-      ops.push_back(mk_op(R - 1, b, 1, 0, -1, 2, 0, b + 1, 0));
-      int slot = 0;
-      for (int j = R - 2; j >= 0; --j) {
-        ops.push_back(mk_op(j, a + j, 1, 1 - slot, -1, 2, 1 + slot, 0, 1));
-        slot = 1 - slot;
-      }
+      SweepStep x = mk_step(FK, s, 1);
+      x.src = SB_V; x.src_j = 0; x.src_ds = 1; x.cpl = XC_IDENT;
+      x.out = SB_V; x.out_j = 0; x.out_mode = OUT_SUB;
+      st.push_back(x);
+    }
+    // B2: responses to the last-line coupling U u_{s+1}[0], lines R-1..1 of strips 0..N-2
+    for (int j = R - 1; j >= 1; --j) {
+      SweepStep x = mk_step(j, 0, N - 1);
+      if (j == R - 1) { x.src = SB_V; x.src_j = 0; x.src_ds = 1; x.cpl = XC_UPPER; x.neg = 0; }
+      else { x.src = SB_W; x.src_j = j + 1; x.cpl = XC_UPPER; x.neg = 1; }
+      x.out = SB_W; x.out_j = j; x.out_mode = OUT_SET;
+      x.acc = SB_V; x.acc_j = j; x.acc_mode = OUT_SUB;
+      st.push_back(x);
     }
   }
-  return ops;
+  return st;
 }
 
 // BT-frame node (i, l) of a column with direction code c -> grid node (io, jo)
@@ -74,353 +125,271 @@ __device__ __forceinline__ int code_of(int4 codes, int d) {
   return d == 0 ? codes.x : (d == 1 ? codes.y : (d == 2 ? codes.z : codes.w));
 }
 
-// Column-tile layout of the sweep arrays: X[line][tile][node][ct], ct = CT columns per
-// tile (4 for complex64, 2 for complex128), so that one tile of one node line is a
-// contiguous m * CT block that one bulk copy moves.  Columns beyond C are zero padding.
+// X[j][i][s][c] <- scale * src (frame-mapped); entries (j = R, s < N-1) are padding (zero).
 template <typename R>
 __global__ void pack_kernel(const double2* const* __restrict__ srcptr, const double* __restrict__ scale, int C,
-                            int t, int4 codes, int n, int ct, int ntile, typename Cx<R>::T* __restrict__ X) {
+                            int t, int4 codes, int n, int N, int Rl, typename Cx<R>::T* __restrict__ X) {
   using T = typename Cx<R>::T;
   const int m = n + 1;
-  const size_t total = (size_t)m * m * ntile * ct;
+  const size_t total = (size_t)(Rl + 1) * m * N * C;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int cc = (int)(idx % ct);
-    size_t q = idx / ct;
+    const int c = (int)(idx % C);
+    size_t q = idx / C;
+    const int s = (int)(q % N);
+    q /= N;
     const int i = (int)(q % m);
-    q /= m;
-    const int tile = (int)(q % ntile);
-    const int l = (int)(q / ntile);
-    const int c = tile * ct + cc;
+    const int j = (int)(q / m);
     T v = mk<T>(0, 0);
-    if (c < C) {
+    if (j < Rl || s == N - 1) {
       int io, jo;
-      frame_map(code_of(codes, c % t), i, l, n, io, jo);
+      frame_map(code_of(codes, c % t), i, s * Rl + j, n, io, jo);
       const double2 a = srcptr[c][(size_t)jo * m + io];
-      const double s = scale[c];
-      v = mk<T>(a.x * s, a.y * s);
+      const double sc = scale[c];
+      v = mk<T>(a.x * sc, a.y * sc);
     }
     X[idx] = v;
   }
 }
 
 template <typename R>
-__global__ void unpack_kernel(const typename Cx<R>::T* __restrict__ X, int C, int t, int4 codes, int n, int ct,
-                              int ntile, double2* __restrict__ dst, size_t stride) {
+__global__ void unpack_kernel(const typename Cx<R>::T* __restrict__ X, int C, int t, int4 codes, int n, int N, int Rl,
+                              double2* __restrict__ dst, size_t stride) {
   const int m = n + 1;
-  const size_t total = (size_t)m * m * ntile * ct;
+  const size_t total = (size_t)(Rl + 1) * m * N * C;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int cc = (int)(idx % ct);
-    size_t q = idx / ct;
+    const int c = (int)(idx % C);
+    size_t q = idx / C;
+    const int s = (int)(q % N);
+    q /= N;
     const int i = (int)(q % m);
-    q /= m;
-    const int tile = (int)(q % ntile);
-    const int l = (int)(q / ntile);
-    const int c = tile * ct + cc;
-    if (c >= C) continue;
+    const int j = (int)(q / m);
+    if (j == Rl && s != N - 1) continue;
     int io, jo;
-    frame_map(code_of(codes, c % t), i, l, n, io, jo);
+    frame_map(code_of(codes, c % t), i, s * Rl + j, n, io, jo);
     dst[(size_t)c * stride + (size_t)jo * m + io] = to_d(X[idx]);
   }
 }
 
+// Narrow step (at most 8 columns: the interface chains and the last strip's extra line
+// of a single right-hand side).  The CTA forms x (m x ncols) in shared memory, then one warp
+// per output row walks the row of A with two complex entries per lane per load and sums
+// across the warp with shuffles.
 template <typename R>
-struct SweepParams {
+__global__ void __launch_bounds__(256) line_gemv_kernel(const typename Cx<R>::T* __restrict__ A, int lda, int m,
+                                                        LineOperand<typename Cx<R>::T> op, Coef cf) {
   using T = typename Cx<R>::T;
-  const T* F;        // factor blocks, m x ldf each
-  const T* Rin;      // packed right-hand sides (lines x tiles x m x CT)
-  T* V;              // sweep output (same layout)
-  T* Zt;             // two line buffers for the backward chains
-  const SweepOp* ops;
-  Coef cf;
-  unsigned* bar;
-  int* err;
-  long long budget;
-  int ldf, m, ntile, nops, rp;
-};
-
-// Persistent sweep, one CTA per SM.  CTA b owns rows [b rp, (b+1) rp) of every block step.
-// Per step: the CTA's rows of the factor block F_f arrive in shared memory by a bulk copy
-// issued one step ahead (double buffer) so that HBM streaming overlaps the barrier; after
-// the grid barrier the coupled line and the right-hand-side line arrive by bulk copy, the
-// input x = Rin +- C(src) is formed in shared memory, every thread multiplies its slice of
-// the node index for all of the CTA's rows and the tile's CT columns, a butterfly warp
-// reduction and a cross-warp sum give the outputs, and the CTA writes its rows.
-template <typename R, int CT, int RP, int NBUF>
-__global__ void __launch_bounds__(256, 1) sweep_tma_kernel(SweepParams<R> p) {
-  using T = typename Cx<R>::T;
-  constexpr int NV = RP * CT * 2;          // real partial sums per thread
-  constexpr int PER = NV / 32;             // values per lane after the butterfly
-  static_assert(NV == 32 || NV == 64, "butterfly expects 32 or 64 values");
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int m = p.m, rp = p.rp, ldf = p.ldf;
-  const int lineT = m * CT;
-  T* Fbuf = reinterpret_cast<T*>(smem_raw);
-  T* Sbuf = Fbuf + (size_t)NBUF * rp * ldf;
-  T* Bbuf = Sbuf + lineT;
-  T* vert_s = Bbuf + lineT;
-  R* red = reinterpret_cast<R*>(vert_s + ((m + 1) & ~1));
-  uint64_t* mb = reinterpret_cast<uint64_t*>(red + 8 * 64);
-  __shared__ int s_ok;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int r0 = blockIdx.x * rp;
-  const int nr = max(0, min(m, r0 + rp) - r0);
-  const unsigned fbytes = (unsigned)(nr * ldf * sizeof(T));
-  const unsigned lbytes = (unsigned)(lineT * sizeof(T));
-  const size_t lstride = (size_t)p.ntile * lineT;
-
-  for (int i = tid; i < m; i += blockDim.x) {
-    const double2 v = p.cf.vert(i);
-    vert_s[i] = mk<T>(v.x, v.y);
-  }
-  const R dg = (R)p.cf.diag();
-  if (tid == 0) {
-    mbar_init(&mb[0], 1);
-    mbar_init(&mb[1], 1);
-    mbar_init(&mb[2], 1);
-    fence_proxy_async();
-    if (nr > 0) {
-      mbar_expect_tx(&mb[0], fbytes);
-      bulk_g2s(Fbuf, p.F + (size_t)p.ops[0].f * m * ldf + (size_t)r0 * ldf, fbytes, &mb[0]);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  const int ncols = op.ns * op.C;
+  const int N = op.N, C = op.C;
+  const double2 ve = cf.vert(0), vi = cf.vert(1);
+  const T vert_edge = mk<T>(ve.x, ve.y), vert_int = mk<T>(vi.x, vi.y);
+  const R dg = (R)cf.diag();
+  const int total = m * ncols;
+  // x: every thread first loads all its inputs, then forms its entries
+  constexpr int PT = 8;  // entries per thread per pass
+  for (int base_idx = threadIdx.x * PT; base_idx < total; base_idx += blockDim.x * PT) {
+    T b[PT], s0[PT], s1[PT];
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+      const int idx = base_idx + u;
+      b[u] = s0[u] = s1[u] = mk<T>(0, 0);
+      if (idx >= total) continue;
+      const int i = idx / ncols, col = idx % ncols;
+      const int s = op.s0 + col / C, c = col % C;
+      if (op.base) b[u] = op.base[((size_t)(op.base_j * m + i) * N + s) * C + c];
+      if (op.cpl != XC_NONE) {
+        const T* sp = op.src + ((size_t)op.src_j * m * N + (s + op.src_ds)) * C + c;
+        const size_t istride = (size_t)N * C;
+        s0[u] = __ldcg(sp + (size_t)i * istride);
+        const int nb = (op.cpl == XC_LOWER) ? i - 1 : i + 1;
+        if (op.cpl != XC_IDENT && nb >= 0 && nb < m) s1[u] = __ldcg(sp + (size_t)nb * istride);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+      const int idx = base_idx + u;
+      if (idx >= total) continue;
+      T v = b[u];
+      if (op.cpl != XC_NONE) {
+        T cp = s0[u];
+        if (op.cpl != XC_IDENT) {
+          const int i = idx / ncols;
+          cp = cmul((i == 0 || i == m - 1) ? vert_edge : vert_int, cp);
+          cp.x += dg * s1[u].x;
+          cp.y += dg * s1[u].y;
+        }
+        v = op.neg ? csub(v, cp) : cadd(v, cp);
+      }
+      xs[idx] = v;
     }
   }
   __syncthreads();
-  unsigned target = 0, lphase = 0;
-  for (int op = 0; op < p.nops; ++op) {
-    const SweepOp o = p.ops[op];
-    const int fb = (NBUF == 2) ? (op & 1) : 0;
-    const unsigned fpar = (NBUF == 2) ? ((op >> 1) & 1) : (op & 1);
-    if (NBUF == 2 && tid == 0 && nr > 0 && op + 1 < p.nops) {
-      fence_proxy_async();
-      mbar_expect_tx(&mb[(op + 1) & 1], fbytes);
-      bulk_g2s(Fbuf + (size_t)((op + 1) & 1) * rp * ldf, p.F + (size_t)p.ops[op + 1].f * m * ldf + (size_t)r0 * ldf,
-               fbytes, &mb[(op + 1) & 1]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = blockIdx.x * 8 + wid;
+  if (row >= m) return;
+  T acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = mk<T>(0, 0);
+  const T* Ar = A + (size_t)row * lda;
+  // lanes take pairs of consecutive node indices; four pairs in flight per lane
+  for (int k0 = 2 * lane; k0 < m; k0 += 64 * 4) {
+    T a[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 64 * u;
+      a[u][0] = k < m ? __ldg(Ar + k) : mk<T>(0, 0);
+      a[u][1] = k + 1 < m ? __ldg(Ar + k + 1) : mk<T>(0, 0);
     }
-    const T* src = (o.cpl_src == 0) ? p.V + (size_t)o.cpl_line * lstride : p.Zt + (size_t)(o.cpl_src - 1) * lstride;
-    const T* base = o.base_line >= 0 ? p.Rin + (size_t)o.base_line * lstride : nullptr;
-    T* out = p.V + (size_t)o.out_line * lstride;
-    T* zs = o.zsave >= 0 ? p.Zt + (size_t)o.zsave * lstride : nullptr;
-    const bool need_f = nr > 0;
-    for (int tile = 0; tile < p.ntile; ++tile) {
-      const unsigned nb = (o.cpl ? lbytes : 0u) + (base ? lbytes : 0u);
-      if (tid == 0) {
-        int ok = 1;
-        if (nb) {
-          fence_proxy_async();
-          mbar_expect_tx(&mb[2], nb);
-          if (o.cpl) bulk_g2s(Sbuf, src + (size_t)tile * lineT, lbytes, &mb[2]);
-          if (base) bulk_g2s(Bbuf, base + (size_t)tile * lineT, lbytes, &mb[2]);
-          ok = mbar_wait(&mb[2], lphase & 1, p.err, p.budget);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 64 * u;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (k + h < m) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < ncols) cfma(acc[c], a[u][h], xs[(k + h) * ncols + c]);
         }
-        if (ok && tile == 0 && need_f) ok = mbar_wait(&mb[fb], fpar, p.err, p.budget);
-        s_ok = ok;
-      }
-      if (nb) ++lphase;
-      __syncthreads();
-      if (!s_ok) return;
-      // x = base +- C(src), formed in place in Bbuf
-      for (int idx = tid; idx < lineT; idx += blockDim.x) {
-        const int i = idx / CT;
-        T v = base ? Bbuf[idx] : mk<T>(0, 0);
-        if (o.cpl) {
-          T cp = cmul(vert_s[i], Sbuf[idx]);
-          if (o.cpl == 1 && i >= 1) { const T y = Sbuf[idx - CT]; cp.x += dg * y.x; cp.y += dg * y.y; }
-          if (o.cpl == 2 && i + 1 < m) { const T y = Sbuf[idx + CT]; cp.x += dg * y.x; cp.y += dg * y.y; }
-          v = o.cpl_neg ? csub(v, cp) : cadd(v, cp);
-        }
-        Bbuf[idx] = v;
-      }
-      __syncthreads();
-      const T* Fr = Fbuf + (size_t)fb * rp * ldf;
-      for (int g0 = 0; g0 < nr; g0 += RP) {
-        const int ng = min(RP, nr - g0);
-        R acc[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] = 0;
-        for (int i = tid; i < m; i += blockDim.x) {
-          T xv[CT];
-#pragma unroll
-          for (int c = 0; c < CT; ++c) xv[c] = Bbuf[i * CT + c];
-#pragma unroll
-          for (int rr = 0; rr < RP; ++rr) {
-            if (rr < ng) {
-              const T f = Fr[(size_t)(g0 + rr) * ldf + i];
-#pragma unroll
-              for (int c = 0; c < CT; ++c) {
-                const int q = (rr * CT + c) * 2;
-                acc[q] = fma(f.x, xv[c].x, acc[q]);
-                acc[q] = fma(-f.y, xv[c].y, acc[q]);
-                acc[q + 1] = fma(f.x, xv[c].y, acc[q + 1]);
-                acc[q + 1] = fma(f.y, xv[c].x, acc[q + 1]);
-              }
-            }
-          }
-        }
-        // butterfly: after the offset-o round every lane keeps the half selected by (lane & o)
-#pragma unroll
-        for (int o2 = 16, half = NV / 2; o2 >= 1; o2 >>= 1, half >>= 1) {
-          const bool up = (lane & o2) != 0;
-#pragma unroll
-          for (int q = 0; q < half; ++q) {
-            const R send = up ? acc[q] : acc[q + half];
-            const R keep = up ? acc[q + half] : acc[q];
-            acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o2);
-          }
-        }
-        // lane holds values [lane * PER, lane * PER + PER)
-#pragma unroll
-        for (int q = 0; q < PER; ++q) red[wid * 64 + lane * PER + q] = acc[q];
-        __syncthreads();
-        if (tid < NV / 2) {
-          R re = 0, im = 0;
-          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            re += red[w * 64 + 2 * tid];
-            im += red[w * 64 + 2 * tid + 1];
-          }
-          const int rr = tid / CT, c = tid % CT;
-          if (rr < ng) {
-            const size_t g = (size_t)tile * lineT + (size_t)(r0 + g0 + rr) * CT + c;
-            T z;
-            z.x = re;
-            z.y = im;
-            if (o.out_sub) out[g] = csub(__ldcg(out + g), z);
-            else out[g] = z;
-            if (zs) zs[g] = z;
-          }
-        }
-        __syncthreads();
       }
     }
-    if (NBUF == 1 && tid == 0 && nr > 0 && op + 1 < p.nops) {
-      fence_proxy_async();
-      mbar_expect_tx(&mb[0], fbytes);
-      bulk_g2s(Fbuf, p.F + (size_t)p.ops[op + 1].f * m * ldf + (size_t)r0 * ldf, fbytes, &mb[0]);
-    }
-    if (op + 1 < p.nops) {
-      if (!grid_sync(p.bar, target, p.err, p.budget)) {
-        // let this CTA's outstanding factor copy land before leaving
-        if (tid == 0 && nr > 0) mbar_wait(&mb[(NBUF == 2) ? ((op + 1) & 1) : 0],
-                                          (NBUF == 2) ? (((op + 1) >> 1) & 1) : ((op + 1) & 1), p.err, p.budget);
-        return;
-      }
-      if (tid == 0) fence_proxy_async();
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc[c] = cadd(acc[c], shfl_xor(acc[c], o));
+  if (lane < ncols) {
+    T z = acc[0];
+#pragma unroll
+    for (int c = 1; c < 8; ++c)
+      if (lane == c) z = acc[c];
+    const int s = op.s0 + lane / C, c = lane % C;
+    T* o = op.out + ((size_t)(op.out_j * m + row) * N + s) * C + c;
+    apply_out(o, z, op.out_mode);
+    if (op.acc) {
+      T* a2 = op.acc + ((size_t)(op.acc_j * m + row) * N + s) * C + c;
+      apply_out(a2, op.out_mode == OUT_SET ? z : *o, op.acc_mode);
     }
   }
 }
+
+size_t Engine::sweep_ws_bytes(int C) const { return (size_t)(R + 1) * m * N * C * sweep_elem(); }
+
+size_t Engine::sweep_partial_bytes(int C) const { return (size_t)8 * m * N * C * sweep_elem(); }
 
 int Engine::ensure_sweep_ws(int C) {
-  const int ct = sweep_ct();
-  const int ntile = (C + ct - 1) / ct;
-  if ((size_t)ntile * ct <= w_cap_cols) return HH_OK;
-  dfree(w_rin); dfree(w_v); dfree(w_zt);
-  w_rin = w_v = w_zt = nullptr;
+  if ((size_t)C <= w_cap_cols) return HH_OK;
+  dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial);
+  w_rin = w_v = w_w = w_partial = nullptr;
   w_cap_cols = 0;
-  const size_t line = (size_t)m * ntile * ct * sweep_elem();
-  if (dmalloc(&w_rin, line * m) || dmalloc(&w_v, line * m) || dmalloc(&w_zt, line * 2)) return HH_ENOMEM;
-  w_cap_cols = (size_t)ntile * ct;
+  w_partial_bytes = 0;
+  const size_t b = sweep_ws_bytes(C);
+  if (dmalloc(&w_rin, b) || dmalloc(&w_v, b) || dmalloc(&w_w, b) || dmalloc(&w_partial, sweep_partial_bytes(C)))
+    return HH_ENOMEM;
+  w_partial_bytes = sweep_partial_bytes(C);
+  w_cap_cols = C;
   return HH_OK;
 }
 
-// Shared memory of the sweep kernel for NBUF factor buffers.
-size_t Engine::sweep_smem(int nbuf) const {
-  const size_t e = sweep_elem();
-  const int rp = sweep_rows_per_cta();
-  return (size_t)nbuf * rp * ldf * e + 2 * (size_t)m * sweep_ct() * e + (size_t)((m + 1) & ~1) * e +
-         8 * 64 * (e / 2) + 3 * sizeof(uint64_t);
-}
-int Engine::sweep_rows_per_cta() const { return (m + num_sms - 1) / num_sms; }
-int Engine::sweep_grid() const {
-  const int rp = sweep_rows_per_cta();
-  return (m + rp - 1) / rp;
-}
-
-template <typename R, int CT, int NBUF>
-static cudaError_t launch_sweep_t(Engine& E, const void* Rin, void* V, void* Zt, int ntile, bool single) {
+template <typename R>
+static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, int C, bool single, void* partial_buf,
+                                  size_t partial_bytes) {
   using T = typename Cx<R>::T;
-  SweepParams<R> p;
-  p.F = reinterpret_cast<const T*>(E.factors);
-  p.Rin = reinterpret_cast<const T*>(Rin);
-  p.V = reinterpret_cast<T*>(V);
-  p.Zt = reinterpret_cast<T*>(Zt);
-  p.ops = single ? E.d_ops_single : E.d_ops;
-  p.nops = single ? E.nops_single : E.nops_double;
-  p.cf = E.coef;
-  p.bar = E.bar;
-  p.err = E.err;
-  p.budget = E.opts.timeout_cycles;
-  p.ldf = E.ldf;
-  p.m = E.m;
-  p.ntile = ntile;
-  p.rp = E.sweep_rows_per_cta();
-  const size_t smem = E.sweep_smem(NBUF);
-  auto fn = sweep_tma_kernel<R, CT, 8, NBUF>;
-  cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  void* args[] = {(void*)&p};
-  cudaMemsetAsync(E.bar, 0, sizeof(unsigned), E.stream);
-  return E.launch_coop((const void*)fn, E.sweep_grid(), 256, smem, args);
+  const std::vector<SweepStep>& steps = single ? E.steps_single : E.steps_double;
+  const T* Fb = reinterpret_cast<const T*>(E.factors);
+  const size_t blk = (size_t)E.m * E.ldf;
+  auto buf = [&](int b) -> T* {
+    return b == SB_RIN ? (T*)Rin : (b == SB_V ? (T*)V : (b == SB_W ? (T*)W : nullptr));
+  };
+  const size_t gemv_cap = 200 * 1024;  // the narrow kernel keeps x (m x ncols) in shared memory
+  constexpr int BM = 64, BN = 64, BK = 16, STG = 3;
+  constexpr size_t gemm_smem = line_gemm_smem<R, BM, BN, BK, STG>();
+  auto gemm_fn = line_gemm_kernel<R, BM, BN, BK, 4, 4, STG>;
+  cudaFuncSetAttribute((const void*)gemm_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem);
+  cudaFuncSetAttribute((const void*)line_gemv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)std::min<size_t>((size_t)E.m * 8 * sizeof(T), gemv_cap));
+  for (const SweepStep& s : steps) {
+    LineOperand<T> op{};
+    op.base = buf(s.base); op.base_j = s.base_j;
+    op.src = buf(s.src); op.src_j = s.src_j; op.src_ds = s.src_ds; op.cpl = s.cpl; op.neg = s.neg;
+    op.out = buf(s.out); op.out_j = s.out_j; op.out_mode = s.out_mode;
+    op.acc = buf(s.acc); op.acc_j = s.acc_j; op.acc_mode = s.acc_mode;
+    op.s0 = s.s0; op.ns = s.ns; op.N = E.N; op.C = C;
+    const T* A = Fb + (size_t)s.f * blk;
+    const int ncols = s.ns * C;
+    if (ncols <= 8 && (size_t)E.m * ncols * sizeof(T) <= gemv_cap) {
+      line_gemv_kernel<R><<<(E.m + 7) / 8, 256, (size_t)E.m * ncols * sizeof(T), E.stream>>>(A, E.ldf, E.m, op,
+                                                                                          E.coef);
+      E.count_launch();
+    } else {
+      const int gx = (E.m + BM - 1) / BM, gy = (ncols + BN - 1) / BN;
+      // split K until about two CTAs per SM are busy (each slice at least two K tiles)
+      int nsplit = std::max(1, std::min(8, (2 * E.num_sms + gx * gy - 1) / (gx * gy)));
+      while (nsplit > 1 && (E.m + nsplit - 1) / nsplit < 2 * BK) --nsplit;
+      while (nsplit > 1 && (size_t)nsplit * E.m * ncols * sizeof(T) > partial_bytes) --nsplit;
+      const int kchunk = ((E.m + nsplit - 1) / nsplit + BK - 1) / BK * BK;
+      T* partial = nsplit > 1 ? reinterpret_cast<T*>(partial_buf) : nullptr;
+      gemm_fn<<<dim3(gx, gy, nsplit), 256, gemm_smem, E.stream>>>(A, E.ldf, E.m, op, E.coef, kchunk, partial);
+      E.count_launch();
+      if (nsplit > 1) {
+        split_reduce_kernel<R><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(partial, nsplit, E.m, op);
+        E.count_launch();
+      }
+    }
+  }
+  return cudaGetLastError();
 }
 
-int Engine::run_sweep(const void* Rin, void* V, void* Zt, int C, bool single) {
-  const int nops = single ? nops_single : nops_double;
-  const int ct = sweep_ct();
-  const int ntile = (C + ct - 1) / ct;
-  const double elem = (double)sweep_elem();
-  // algorithmic bytes: every block step streams one m x m factor block once for all columns,
-  // the right-hand-side lines are read once and the output lines written once
-  const double fbytes = (double)nops * m * m * elem + 2.0 * m * m * (double)ntile * ct * elem;
-  const int nbuf = sweep_smem(2) <= 220 * 1024 ? 2 : 1;
-  if (sweep_smem(nbuf) > 220 * 1024) {
-    set_error("grid too large for the sweep kernel's shared-memory tiles");
-    return HH_EINVAL;
+double Engine::sweep_flops(int C, bool single) const {
+  const std::vector<SweepStep>& steps = single ? steps_single : steps_double;
+  double f = 0;
+  for (const SweepStep& s : steps) f += 8.0 * m * m * (double)s.ns * C;
+  return f;
+}
+
+double Engine::sweep_bytes(int C, bool single) const {
+  // algorithmic bytes: each step reads one m x m block and its input lines once and writes its
+  // output (and accumulated) lines once; pack / unpack traffic excluded
+  const std::vector<SweepStep>& steps = single ? steps_single : steps_double;
+  const double e = (double)sweep_elem();
+  double b = 0;
+  for (const SweepStep& s : steps) {
+    const double line = (double)m * s.ns * C * e;
+    b += (double)m * m * e + line * ((s.base != SB_NONE) + (s.src != SB_NONE) + 1 + 2 * (s.acc != SB_NONE) +
+                                     (s.out_mode != OUT_SET));
   }
+  return b;
+}
+
+int Engine::run_sweep(const void* Rin, void* V, void* W, int C, bool single) {
   tick_begin(K_SWEEP);
-  cudaError_t ce;
-  if (precision == HH_PREC_FP32)
-    ce = nbuf == 2 ? launch_sweep_t<float, 4, 2>(*this, Rin, V, Zt, ntile, single)
-                   : launch_sweep_t<float, 4, 1>(*this, Rin, V, Zt, ntile, single);
-  else
-    ce = nbuf == 2 ? launch_sweep_t<double, 2, 2>(*this, Rin, V, Zt, ntile, single)
-                   : launch_sweep_t<double, 2, 1>(*this, Rin, V, Zt, ntile, single);
-  tick_end(K_SWEEP, fbytes, (double)nops * m * m * ntile * ct * 8.0);
+  const int rc = run_sweep_untimed(Rin, V, W, C, single, w_partial, w_partial_bytes);
+  tick_end(K_SWEEP, sweep_bytes(C, single), sweep_flops(C, single));
   last_columns = C;
+  return rc;
+}
+
+int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool single, void* partial,
+                              size_t partial_bytes) {
+  cudaError_t ce = precision == HH_PREC_FP32
+                       ? launch_steps_t<float>(*this, Rin, V, W, C, single, partial, partial_bytes)
+                       : launch_steps_t<double>(*this, Rin, V, W, C, single, partial, partial_bytes);
   if (ce != cudaSuccess) { set_cuda_error(ce, "sweep launch"); return HH_ECUDA; }
   return HH_OK;
 }
 
-// The same launch as run_sweep without the statistics events (the no-allocation entry
-// point creates no CUDA objects).
-int Engine::run_sweep_untimed(const void* Rin, void* V, void* Zt, int C, bool single) {
-  const int ct = sweep_ct();
-  const int ntile = (C + ct - 1) / ct;
-  const int nbuf = sweep_smem(2) <= 220 * 1024 ? 2 : 1;
-  if (sweep_smem(nbuf) > 220 * 1024) {
-    set_error("grid too large for the sweep kernel's shared-memory tiles");
-    return HH_EINVAL;
-  }
-  cudaError_t ce;
-  if (precision == HH_PREC_FP32)
-    ce = nbuf == 2 ? launch_sweep_t<float, 4, 2>(*this, Rin, V, Zt, ntile, single)
-                   : launch_sweep_t<float, 4, 1>(*this, Rin, V, Zt, ntile, single);
-  else
-    ce = nbuf == 2 ? launch_sweep_t<double, 2, 2>(*this, Rin, V, Zt, ntile, single)
-                   : launch_sweep_t<double, 2, 1>(*this, Rin, V, Zt, ntile, single);
-  if (ce != cudaSuccess) { set_cuda_error(ce, "sweep launch"); return HH_ECUDA; }
-  return HH_OK;
-}
-
-// launch helpers used by krylov.cu / api.cu
+// launch helpers used by krylov.cu / api.cu / noalloc.cu
 template <typename R>
 static void launch_pack_t(Engine& E, const double2* const* srcptr, const double* scale, int C, int t, int4 codes,
                           void* X) {
-  const int ct = E.sweep_ct(), ntile = (C + ct - 1) / ct;
-  pack_kernel<R><<<E.grid_for((size_t)E.m * E.m * ntile * ct), 256, 0, E.stream>>>(
-      srcptr, scale, C, t, codes, E.n, ct, ntile, reinterpret_cast<typename Cx<R>::T*>(X));
+  pack_kernel<R><<<E.grid_for(E.sweep_ws_bytes(C) / E.sweep_elem()), 256, 0, E.stream>>>(
+      srcptr, scale, C, t, codes, E.n, E.N, E.R, reinterpret_cast<typename Cx<R>::T*>(X));
   E.count_launch();
 }
 template <typename R>
 static void launch_unpack_t(Engine& E, const void* X, int C, int t, int4 codes, double2* dst, size_t stride) {
-  const int ct = E.sweep_ct(), ntile = (C + ct - 1) / ct;
-  unpack_kernel<R><<<E.grid_for((size_t)E.m * E.m * ntile * ct), 256, 0, E.stream>>>(
-      reinterpret_cast<const typename Cx<R>::T*>(X), C, t, codes, E.n, ct, ntile, dst, stride);
+  unpack_kernel<R><<<E.grid_for(E.sweep_ws_bytes(C) / E.sweep_elem()), 256, 0, E.stream>>>(
+      reinterpret_cast<const typename Cx<R>::T*>(X), C, t, codes, E.n, E.N, E.R, dst, stride);
   E.count_launch();
 }
 
