@@ -64,13 +64,16 @@ typedef struct {
   int scheme;             /* HH_SCHEME_AUTO: t=2 cross, t>2 sum */
   int single_sweep;       /* 1: forward sweeps only (LR, RL, BT, TB of Section 4) */
   int maxit;              /* iteration limit (default 200) */
-  double deflate_eta;     /* deflation threshold r_jj <= eta * ||w_j|| (default 1e-12) */
+  double deflate_eta;     /* deflation threshold r_jj <= eta * ||w_j|| (default 1e-10) */
   int bcr_depth;          /* reserved: 0 = block Thomas strip solves (the only value accepted) */
   int64_t timeout_cycles; /* SM clock budget of every device-side wait (default 4e9) */
   void* stream;           /* cudaStream_t to run on, or NULL for the handle's own stream */
   int use_graph;          /* 1 (default): the Arnoldi step is replayed as a CUDA graph */
   int profile;            /* 1: time every kernel class with CUDA events (hh_get_stats) */
-  int reserved[6];
+  int gs_passes;          /* Gram-Schmidt passes against the basis and within the new block:
+                             2 (default, CGS2) or 1 (the single pass whose inner products
+                             Section 3 counts, (k - 1/2) t^2 + 3t/2 at iteration k) */
+  int reserved[5];
 } hh_opts;
 
 typedef struct {

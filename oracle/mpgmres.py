@@ -34,7 +34,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-ETA = 1e-12
+ETA = 1e-10
 
 
 @dataclass
@@ -65,7 +65,7 @@ def _givens(a: complex, b: complex):
 
 
 def solve(A, precs, b: np.ndarray, tol: float = 1e-8, maxit: int = 200, scheme: str = "auto",
-          eta: float = ETA, single_pass: bool = False, keep_basis: bool = False) -> Result:
+          eta: float = ETA, single_pass: bool = False, keep_basis: bool = False, gs_passes: int | None = None) -> Result:
     """A: sparse matrix (or anything with @); precs: list of callables r -> M_i^{-1} r."""
     t = len(precs)
     b = np.asarray(b, dtype=np.complex128)
@@ -74,7 +74,7 @@ def solve(A, precs, b: np.ndarray, tol: float = 1e-8, maxit: int = 200, scheme: 
         return Result(np.zeros_like(b), 0, True, "ok", 0.0, 0.0)
     if scheme == "auto":
         scheme = "single" if t == 1 else ("cross" if t == 2 else "sum")
-    passes = 1 if single_pass else 2
+    passes = gs_passes if gs_passes is not None else (1 if single_pass else 2)
 
     V = [b / beta]
     Zs = []                 # accepted Z columns

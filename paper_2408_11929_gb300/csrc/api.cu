@@ -128,6 +128,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   if (opts.precision != HH_PREC_FP32 && opts.precision != HH_PREC_FP64) return (set_error("bad precision"), HH_EINVAL);
   if (opts.maxit < 1 || opts.maxit > 2000) return (set_error("maxit must be in [1, 2000]"), HH_EINVAL);
   if (opts.bcr_depth != 0) return (set_error("only bcr_depth = 0 (block Thomas strip solves) is implemented"), HH_EINVAL);
+  if (opts.gs_passes != 1 && opts.gs_passes != 2) return (set_error("gs_passes must be 1 or 2"), HH_EINVAL);
   if (opts.timeout_cycles <= 0) opts.timeout_cycles = 4000000000LL;
   k = k_; n = n_; N = strips; m = n + 1; R = n / N;
   precision = opts.precision;
@@ -295,12 +296,13 @@ void hh_default_opts(hh_opts* o) {
   o->scheme = HH_SCHEME_AUTO;
   o->single_sweep = 0;
   o->maxit = 200;
-  o->deflate_eta = 1e-12;
+  o->deflate_eta = 1e-10;
   o->bcr_depth = 0;
   o->timeout_cycles = 4000000000LL;
   o->stream = nullptr;
   o->use_graph = 1;
   o->profile = 0;
+  o->gs_passes = 2;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {

@@ -2,8 +2,8 @@
 // Section 4), FP64 complex.  Per iteration, for every active right-hand side r:
 //   Z_k = [M_d^{-1} s_d]   (sweep.cu, all directions and right-hand sides in one launch)
 //   W   = A Z_k            (matrix-free P1 stencil)
-//   CGS2: H = V^H W, W -= V H, twice, coefficients summed
-//   block QR of W in preconditioner order (again two passes against the new vectors),
+//   block CGS: H = V^H W, W -= V H, twice by default (opts.gs_passes), coefficients summed
+//   block QR of W in preconditioner order (the same number of passes against the new vectors),
 //     column j deflated when r_jj <= eta * ||w_j|| (norm after CGS2)
 //   Givens update of the scalar upper Hessenberg matrix, rho = |g_last|, converged when
 //     rho / ||b|| <= tol (tested once per iteration)
@@ -25,7 +25,7 @@ void launch_pack(Engine& E, const double2* const* srcptr, const double* scale, i
 void launch_unpack(Engine& E, const void* X, int C, int t, int4 codes, double2* dst, size_t stride);
 
 struct KState {
-  int nrhs, t, D, maxit, maxV, maxZ, GX, GQ, scheme;
+  int nrhs, t, D, maxit, maxV, maxZ, GX, GQ, scheme, passes;
   double tol, eta;
   double* beta;
   int *done, *status, *nV, *nZ, *iters, *nacc, *amap;
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
   int amap[TT];
   for (int j = 0; j < TT; ++j) {
     double2* w = Wr + j * D;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < S.passes; ++pass) {
       double v[2 * TT];
       for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
       if (active && acc > 0)
@@ -588,7 +588,7 @@ struct DevBuf {
 
 template <int TT>
 static void launch_iteration_gs(Engine& E, KState& S, double2* W, dim3 gsgrid) {
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < S.passes; ++pass) {
     gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(S, W);
     gs_reduce_kernel<<<S.nrhs, 256, 0, E.stream>>>(S, pass == 0);
     const size_t smem = (size_t)S.maxV * TT * sizeof(double2) + (size_t)S.maxV * sizeof(void*);
@@ -610,7 +610,7 @@ int Engine::solve_batch_dev(int nrhs, const double2* b, double2* x, double tol, 
   const size_t D = (size_t)m * m;
   KState S{};
   S.nrhs = nrhs; S.t = t; S.D = (int)D; S.maxit = maxit; S.maxV = 1 + maxit * t; S.maxZ = maxit * t;
-  S.tol = tol; S.eta = opts.deflate_eta;
+  S.tol = tol; S.eta = opts.deflate_eta; S.passes = opts.gs_passes;
   S.scheme = opts.scheme != HH_SCHEME_AUTO ? opts.scheme : (t == 2 ? HH_SCHEME_CROSS : (t > 2 ? HH_SCHEME_SUM : HH_SCHEME_CROSS));
   S.GX = std::max(1, std::min(num_sms * 2 / std::max(1, nrhs) + 1, (int)((D + 255) / 256)));
   S.GX = std::min(S.GX, num_sms * 2);
@@ -696,7 +696,7 @@ int Engine::solve_batch_dev(int nrhs, const double2* b, double2* x, double tol, 
       // algorithmic bytes of Gram-Schmidt this iteration: two passes of (read V + read W)
       // for the dot products and (read V + read/write W) for the update, plus the block QR
       const double nVmax = 1.0 + (double)(k - 1) * t;
-      tick_end(K_GS, nrhs * (2.0 * (2.0 * nVmax * D * 16 + 3.0 * t * D * 16) + 6.0 * t * D * 16), 0);
+      tick_end(K_GS, nrhs * (S.passes * (2.0 * nVmax * D * 16 + 3.0 * t * D * 16) + 6.0 * t * D * 16), 0);
     }
     if (ce != cudaSuccess) { set_cuda_error(ce, "qr launch"); rc = HH_ECUDA; break; }
     const size_t hsmem = (size_t)(S.maxZ + 2) * sizeof(double2);

@@ -55,81 +55,98 @@ __global__ void schur_kernel(const typename Cx<R>::T* __restrict__ X, int ldx, i
 
 // In-place Gauss-Jordan inversion with partial pivoting of one m x m complex matrix.
 // Ping-pong buffers A/B (step p reads the one of parity p, writes the other); row i of the
-// working matrix is owned by CTA i mod gridDim.x.  Column p of the source is kept
-// contiguous in col[p & 1] for the pivot search.  Pivot rows are recorded in piv.
+// working matrix is owned by CTA i mod gridDim.x, 1024 threads per CTA, one column per
+// thread per pass.  Column p of the source is kept contiguous in col[p & 1]; it gives the
+// pivot search and every row's elimination factor.  Each thread loads its owned rows
+// before the pivot search so the loads overlap it; only the pivot row is read after.
+constexpr int GJ_ROWS = 8;  // owned rows per CTA held in registers per pass
 template <typename R>
-__global__ void __launch_bounds__(256) gj_kernel(typename Cx<R>::T* A, typename Cx<R>::T* B,
-                                                 typename Cx<R>::T* col, int* piv, int m, int ld,
-                                                 unsigned* bar, int* err, long long budget) {
+__global__ void __launch_bounds__(1024) gj_kernel(typename Cx<R>::T* A, typename Cx<R>::T* B,
+                                                  typename Cx<R>::T* col, int* piv, int m, int ld,
+                                                  unsigned* bar, int* err, long long budget) {
   using T = typename Cx<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* prow = reinterpret_cast<T*>(smem_raw);
   __shared__ R s_val[32];
   __shared__ int s_idx[32];
   __shared__ int s_q;
   __shared__ T s_inv;
   unsigned target = 0;
   const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = gridDim.x;
+  const int nown = (m - (int)blockIdx.x + G - 1) / G;  // rows blockIdx.x, +G, +2G, ...
   for (int p = 0; p < m; ++p) {
     const T* src = (p & 1) ? B : A;
     T* dst = (p & 1) ? A : B;
     const T* colp = col + (size_t)(p & 1) * m;
     T* coln = col + (size_t)((p + 1) & 1) * m;
-    R best = (R)-1;
-    int bi = m;
-    for (int i = p + threadIdx.x; i < m; i += blockDim.x) {
-      const R v = cabs2(__ldcg(colp + i));
-      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-    }
-    for (int o = 16; o; o >>= 1) {
-      const R ov = __shfl_down_sync(0xffffffffu, best, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < nw; ++w)
-        if (s_val[w] > best || (s_val[w] == best && s_idx[w] < bi)) { best = s_val[w]; bi = s_idx[w]; }
-      s_q = bi;
-      if (!(best > (R)0) || !isfinite(best)) {
-        s_q = -1;
-        if (blockIdx.x == 0) atomicCAS(err, 0, (int)DEV_SINGULAR);
-      } else {
-        const T pv = __ldcg(colp + bi);
-        const R inv2 = (R)1 / cabs2(pv);
-        s_inv = mk<T>(pv.x * inv2, -pv.y * inv2);
-        if (blockIdx.x == 0) piv[p] = bi;
-      }
-    }
-    __syncthreads();
-    const int q = s_q;
-    if (q < 0) return;  // every CTA sees the same pivot column: all leave together
-    const T inv = s_inv;
-    const T* qrow = src + (size_t)q * ld;
-    for (int c = threadIdx.x; c < m; c += blockDim.x) prow[c] = (c == p) ? inv : cmul(__ldcg(qrow + c), inv);
-    __syncthreads();
-    for (int i = blockIdx.x; i < m; i += gridDim.x) {
-      T* drow = dst + (size_t)i * ld;
-      if (i == p) {
-        for (int c = threadIdx.x; c < m; c += blockDim.x) {
-          drow[c] = prow[c];
-          if (c == p + 1) coln[i] = prow[c];
+    for (int r0 = 0; r0 < nown; r0 += GJ_ROWS) {
+      // own rows of this pass at this thread's first column (loaded before the pivot search)
+      T own[GJ_ROWS];
+      {
+        const int c = threadIdx.x;
+#pragma unroll
+        for (int r = 0; r < GJ_ROWS; ++r) {
+          const int i = (int)blockIdx.x + (r0 + r) * G;
+          own[r] = (c < m && r0 + r < nown) ? __ldcg(src + (size_t)i * ld + c) : mk<T>(0, 0);
         }
-      } else {
-        const T* srow = src + (size_t)((i == q) ? p : i) * ld;
-        const T f = __ldcg(srow + p);
-        for (int c = threadIdx.x; c < m; c += blockDim.x) {
-          T v;
-          if (c == p) {
-            v = cmul(f, inv);
-            v.x = -v.x; v.y = -v.y;
+      }
+      if (r0 == 0) {
+        // pivot search over rows p..m-1 of column p
+        R best = (R)-1;
+        int bi = m;
+        for (int i = p + threadIdx.x; i < m; i += blockDim.x) {
+          const R v = cabs2(__ldcg(colp + i));
+          if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+        }
+        for (int o = 16; o; o >>= 1) {
+          const R ov = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          for (int w = 1; w < nw; ++w)
+            if (s_val[w] > best || (s_val[w] == best && s_idx[w] < bi)) { best = s_val[w]; bi = s_idx[w]; }
+          s_q = bi;
+          if (!(best > (R)0) || !isfinite(best)) {
+            s_q = -1;
+            if (blockIdx.x == 0) atomicCAS(err, 0, (int)DEV_SINGULAR);
           } else {
-            v = __ldcg(srow + c);
-            const T fp = cmul(f, prow[c]);
-            v = csub(v, fp);
+            const T pv = __ldcg(colp + bi);
+            const R inv2 = (R)1 / cabs2(pv);
+            s_inv = mk<T>(pv.x * inv2, -pv.y * inv2);
+            if (blockIdx.x == 0) piv[p] = bi;
           }
-          drow[c] = v;
+        }
+        __syncthreads();
+      }
+      const int q = s_q;
+      if (q < 0) return;  // every CTA sees the same pivot column: all leave together
+      const T inv = s_inv;
+      for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        const bool first = c == (int)threadIdx.x;
+        // scaled pivot row entry (old row q)
+        const T prow = (c == p) ? inv : cmul(__ldcg(src + (size_t)q * ld + c), inv);
+#pragma unroll
+        for (int r = 0; r < GJ_ROWS; ++r) {
+          if (r0 + r >= nown) continue;
+          const int i = (int)blockIdx.x + (r0 + r) * G;
+          T v;
+          if (i == p) {
+            v = prow;
+          } else {
+            // the working row at position i is old row i, except position q holds old row p
+            const int si = (i == q) ? p : i;
+            const T srow_c = (i != q && first) ? own[r] : __ldcg(src + (size_t)si * ld + c);
+            const T f = __ldcg(colp + si);
+            if (c == p) {
+              v = cmul(f, inv);
+              v.x = -v.x; v.y = -v.y;
+            } else {
+              v = csub(srow_c, cmul(f, prow));
+            }
+          }
+          dst[(size_t)i * ld + c] = v;
           if (c == p + 1) coln[i] = v;
         }
       }
@@ -247,7 +264,7 @@ int factor_impl(Engine& E) {
     return HH_ENOMEM;
   }
   int grid = E.num_sms < m ? E.num_sms : m;
-  const size_t smem = (size_t)m * sizeof(T);
+  const size_t smem = 0;
   int status = HH_OK;
   for (int j = 0; j <= Rr && status == HH_OK; ++j) {
     const int type = (j == 0) ? LINE_BOT : (j == Rr ? LINE_TOP : LINE_INT);
@@ -259,7 +276,7 @@ int factor_impl(Engine& E) {
     cudaMemsetAsync(piv, 0, m * sizeof(int), E.stream);
     void* args[] = {(void*)&bufA, (void*)&bufB, (void*)&col, (void*)&piv, (void*)&m, (void*)&ld,
                     (void*)&E.bar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
-    cudaError_t ce = E.launch_coop((const void*)gj_kernel<R>, grid, 256, smem, args);
+    cudaError_t ce = E.launch_coop((const void*)gj_kernel<R>, grid, 1024, smem, args);
     if (ce != cudaSuccess) { E.set_cuda_error(ce, "gj_kernel launch"); status = HH_ECUDA; break; }
     const T* W = ((m - 1) & 1) ? bufA : bufB;
     gj_perm_index<<<1, 1, 0, E.stream>>>(piv, srcidx, m);

@@ -42,8 +42,10 @@ def run(name: str, rhs_list=None, tight: float = 1e-10) -> dict:
     P = solver.Problem(w.k, w.n, w.strips, w.dirs)
     t_setup = time.time() - t0
     idx = sample_nodes(w.n)
+    from oracle import mpgmres
     out = {"workload": name, "k": w.k, "n": w.n, "strips": w.strips, "dirs": w.dirs, "tol": w.tol,
-           "tight_tol": tight, "sample_nodes": idx.tolist(), "oracle_setup_s": t_setup, "rhs": {}}
+           "tight_tol": tight, "sample_nodes": idx.tolist(), "oracle_setup_s": t_setup, "gs_passes": 2,
+           "deflate_eta": mpgmres.ETA, "rhs": {}}
     rhs_list = range(w.nrhs) if rhs_list is None else rhs_list
     for r in rhs_list:
         b = P.rhs(w.sources[r])

@@ -53,8 +53,8 @@ def test_struct_layout_matches_header(tmp_path):
 
 def test_default_opts(lib):
     o = hh.default_opts()
-    assert o.precision == hh.HH_PREC_FP64 and o.maxit == 200 and o.deflate_eta == 1e-12
-    assert o.use_graph == 1 and o.timeout_cycles > 0 and o.bcr_depth == 0
+    assert o.precision == hh.HH_PREC_FP64 and o.maxit == 200 and o.deflate_eta == 1e-10
+    assert o.use_graph == 1 and o.timeout_cycles > 0 and o.bcr_depth == 0 and o.gs_passes == 2
 
 
 @pytest.mark.parametrize("k,n,strips,dirs,kw", [
@@ -65,6 +65,7 @@ def test_default_opts(lib):
     (10.0, 32, 4, 16, {}),          # unknown direction bit
     (10.0, 32, 4, 15, {"maxit": 0}),
     (10.0, 32, 4, 15, {"bcr_depth": 2}),
+    (10.0, 32, 4, 15, {"gs_passes": 3}),
     (10.0, 1, 1, 15, {}),
 ])
 def test_setup_rejects_bad_arguments(lib, k, n, strips, dirs, kw):

@@ -224,3 +224,17 @@ def test_fp32_sweeps_solve():
     assert res.iterations <= ref.iterations + 2
     assert res.rel_res_explicit < 1.5e-6
     assert rel(x, tight.x) < 1e-5
+
+
+@pytest.mark.parametrize("dirs", ["LR+RL+BT+TB", "LR+BT"])
+def test_single_pass_gram_schmidt_matches_oracle(dirs):
+    """gs_passes = 1: one classical Gram-Schmidt pass (Section 3's inner-product count),
+    against the oracle run with the same single pass."""
+    k, n, N = 30.0, 48, 4
+    P = solver.Problem(k, n, N, dirs)
+    b = P.rhs(hh_inputs.centre_source())
+    ref = P.solve(b, tol=1e-8, gs_passes=1)
+    with hh.Handle(k, n, N, dirs, gs_passes=1) as h:
+        x, res = h.solve(b, tol=1e-8)
+    assert res.status == hh.HH_OK and res.iterations == ref.iterations
+    assert rel(x, ref.x) < 1e-10
