@@ -73,7 +73,9 @@ typedef struct {
   int gs_passes;          /* Gram-Schmidt passes against the basis and within the new block:
                              2 (default, CGS2) or 1 (the single pass whose inner products
                              Section 3 counts, (k - 1/2) t^2 + 3t/2 at iteration k) */
-  int reserved[5];
+  int serve_slots;        /* slots of the hh_submit request loop: requests solved together,
+                             each joining at an iteration boundary (default 8, 1..256) */
+  int reserved[4];
 } hh_opts;
 
 typedef struct {

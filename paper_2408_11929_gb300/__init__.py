@@ -29,7 +29,8 @@ class hh_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("scheme", ctypes.c_int), ("single_sweep", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("deflate_eta", ctypes.c_double), ("bcr_depth", ctypes.c_int),
                 ("timeout_cycles", ctypes.c_int64), ("stream", ctypes.c_void_p), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int), ("gs_passes", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("profile", ctypes.c_int), ("gs_passes", ctypes.c_int), ("serve_slots", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class hh_result(ctypes.Structure):

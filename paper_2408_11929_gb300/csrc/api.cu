@@ -1,6 +1,8 @@
 // C ABI (include/hh.h) on top of the engine: validation, host/device buffer handling,
 // timing, statistics and the asynchronous request loop behind hh_submit / hh_poll.
+#include <algorithm>
 #include <chrono>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -129,6 +131,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   if (opts.maxit < 1 || opts.maxit > 2000) return (set_error("maxit must be in [1, 2000]"), HH_EINVAL);
   if (opts.bcr_depth != 0) return (set_error("only bcr_depth = 0 (block Thomas strip solves) is implemented"), HH_EINVAL);
   if (opts.gs_passes != 1 && opts.gs_passes != 2) return (set_error("gs_passes must be 1 or 2"), HH_EINVAL);
+  if (opts.serve_slots < 1 || opts.serve_slots > 256) return (set_error("serve_slots must be in 1..256"), HH_EINVAL);
   if (opts.timeout_cycles <= 0) opts.timeout_cycles = 4000000000LL;
   k = k_; n = n_; N = strips; m = n + 1; R = n / N;
   precision = opts.precision;
@@ -191,6 +194,8 @@ Engine::~Engine() {
   cv.notify_all();
   if (worker_started && worker.joinable()) worker.join();
   if (stream) cudaStreamSynchronize(stream);
+  delete batch_solver;
+  batch_solver = nullptr;
   collect_ticks();
   for (auto ev : event_pool) cudaEventDestroy(ev);
   dfree(factors); dfree(bar); dfree(err);
@@ -248,7 +253,86 @@ struct Engine::Request {
   hh_result res;
   std::atomic<int> state{0};  // 0 queued, 1 running, 2 done
   hh_ticket id;
+  std::chrono::steady_clock::time_point t_submit;
 };
+
+// The request loop: one thread per handle owning a SlotSolver of opts.serve_slots slots.
+// Between two iterations it admits queued requests into the free slots; each iteration
+// advances every active request by one MPGMRES step (one batched sweep launch over their
+// columns); a request that finishes releases its slot at once.  solve_mu is held per
+// iteration so blocking solves on the same handle interleave at iteration boundaries.
+static void request_loop(Engine* Ep) {
+  Engine& E = *Ep;
+  cudaSetDevice(E.device);
+  std::unique_ptr<SlotSolver> ss;
+  std::vector<Engine::Request*> running;
+  auto fail_all = [&](int rc) {
+    for (auto* q : running) {
+      std::memset(&q->res, 0, sizeof(q->res));
+      q->res.status = (hh_status)rc;
+      q->state = 2;
+    }
+    running.clear();
+    ss.reset();
+  };
+  for (;;) {
+    std::vector<Engine::Request*> take;
+    {
+      std::unique_lock<std::mutex> lk(E.mu);
+      if (running.empty()) E.cv.wait(lk, [&] { return E.stopping || !E.queue.empty(); });
+      if (E.stopping && running.empty()) return;
+      if (!E.stopping) {
+        const int room = E.opts.serve_slots - (int)running.size();
+        while ((int)take.size() < room && !E.queue.empty()) {
+          take.push_back(E.queue.front());
+          E.queue.pop_front();
+        }
+      }
+    }
+    std::lock_guard<std::mutex> lk(E.solve_mu);
+    if (!ss) {
+      ss.reset(new SlotSolver(E));
+      const int rc = ss->init(E.opts.serve_slots);
+      if (rc) {
+        for (auto* q : take) running.push_back(q);
+        fail_all(rc);
+        continue;
+      }
+    }
+    if (!take.empty()) {
+      const int nt = (int)take.size();
+      std::vector<const double2*> b(nt);
+      std::vector<double2*> x(nt);
+      std::vector<double> tol(nt);
+      std::vector<void*> tags(nt);
+      for (int q = 0; q < nt; ++q) {
+        b[q] = reinterpret_cast<const double2*>(take[q]->rhs);
+        x[q] = reinterpret_cast<double2*>(take[q]->x);
+        tol[q] = take[q]->tol;
+        tags[q] = take[q];
+        take[q]->state = 1;
+        running.push_back(take[q]);
+      }
+      const int used = ss->admit(nt, b.data(), x.data(), tol.data(), tags.data(), nullptr);
+      if (used < 0) {
+        fail_all(-used);
+        continue;
+      }
+    }
+    std::vector<SlotDone> done;
+    const int rc = ss->iterate(done);
+    const auto now = std::chrono::steady_clock::now();
+    for (auto& d : done) {
+      auto* q = static_cast<Engine::Request*>(d.tag);
+      q->res = d.res;
+      q->res.t_setup_ms = E.setup_ms_total;
+      q->res.t_solve_ms = std::chrono::duration<double, std::milli>(now - q->t_submit).count();
+      running.erase(std::find(running.begin(), running.end(), q));
+      q->state = 2;
+    }
+    if (rc) fail_all(rc);
+  }
+}
 
 static std::mutex g_tickets_mu;
 static std::unordered_map<hh_ticket, std::pair<Engine*, Engine::Request*>> g_tickets;
@@ -303,6 +387,7 @@ void hh_default_opts(hh_opts* o) {
   o->use_graph = 1;
   o->profile = 0;
   o->gs_passes = 2;
+  o->serve_slots = 8;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {
@@ -455,6 +540,7 @@ hh_status hh_submit(hh_handle* h, const double* rhs, double* x, double tol, hh_t
   auto* rq = new Engine::Request();
   rq->rhs = rhs; rq->x = x; rq->tol = tol;
   rq->id = g_next_ticket++;
+  rq->t_submit = std::chrono::steady_clock::now();
   std::memset(&rq->res, 0, sizeof(rq->res));
   {
     std::lock_guard<std::mutex> lk(g_tickets_mu);
@@ -465,49 +551,7 @@ hh_status hh_submit(hh_handle* h, const double* rhs, double* x, double tol, hh_t
     E.queue.push_back(rq);
     if (!E.worker_started) {
       E.worker_started = true;
-      hh_handle* hh = h;
-      E.worker = std::thread([hh]() {
-        Engine& En = *hh->E;
-        cudaSetDevice(En.device);
-        for (;;) {
-          std::vector<Engine::Request*> batch;
-          {
-            std::unique_lock<std::mutex> lk2(En.mu);
-            En.cv.wait(lk2, [&] { return En.stopping || !En.queue.empty(); });
-            if (En.stopping && En.queue.empty()) return;
-            // group every queued request with the same tolerance as the first one
-            const double tol0 = En.queue.front()->tol;
-            for (auto it = En.queue.begin(); it != En.queue.end();) {
-              if ((*it)->tol == tol0 && batch.size() < 256) { batch.push_back(*it); it = En.queue.erase(it); }
-              else ++it;
-            }
-          }
-          const int nb = (int)batch.size();
-          for (auto* q : batch) q->state = 1;
-          const size_t D = (size_t)En.m * En.m;
-          // gather the batch into one contiguous device array
-          double2 *db = nullptr, *dx = nullptr;
-          int rc = En.dmalloc((void**)&db, nb * D * sizeof(double2));
-          if (!rc) rc = En.dmalloc((void**)&dx, nb * D * sizeof(double2));
-          std::vector<hh_result> rs(nb);
-          if (!rc) {
-            for (int r = 0; r < nb; ++r)
-              cudaMemcpyAsync(db + r * D, batch[r]->rhs, D * sizeof(double2), cudaMemcpyDefault, En.stream);
-            hh_handle tmp{&En};
-            rc = solve_common(&tmp, nb, (const double*)db, (double*)dx, batch[0]->tol, rs.data());
-            for (int r = 0; r < nb; ++r)
-              cudaMemcpyAsync(batch[r]->x, dx + r * D, D * sizeof(double2), cudaMemcpyDefault, En.stream);
-            cudaStreamSynchronize(En.stream);
-          }
-          En.dfree(db);
-          En.dfree(dx);
-          for (int r = 0; r < nb; ++r) {
-            batch[r]->res = rs[r];
-            if (rc == HH_ENOMEM || rc == HH_ECUDA) batch[r]->res.status = (hh_status)rc;
-            batch[r]->state = 2;
-          }
-        }
-      });
+      E.worker = std::thread(request_loop, &E);
     }
   }
   E.cv.notify_all();

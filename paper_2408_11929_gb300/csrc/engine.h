@@ -38,7 +38,7 @@ std::vector<SweepStep> build_steps(int n, int N, bool double_sweep);
 // Direction codes of the BT frame mapping (node of the BT frame -> node of the grid).
 enum DirCode { DC_BT = 0, DC_TB = 1, DC_LR = 2, DC_RL = 3 };
 
-struct SlotState;  // per right-hand side Krylov state (device arrays, see krylov.cu)
+class SlotSolver;  // continuous-batching MPGMRES driver (krylov.cu)
 
 class Engine {
  public:
@@ -84,6 +84,8 @@ class Engine {
   struct Request;
   std::deque<Request*> queue;
   std::mutex solve_mu;  // serialises solves on the engine (blocking calls vs request loop)
+  SlotSolver* batch_solver = nullptr;  // reused by solve_batch_dev while the slot count repeats
+  int batch_slots = 0;
 
   ~Engine();
   int init(double k, int n, int strips, uint32_t dirs, const hh_opts* o);
@@ -127,6 +129,38 @@ class Engine {
   size_t sweep_partial_bytes(int C) const;
   size_t w_cap_cols = 0;
   int ensure_sweep_ws(int C);
+};
+
+// Result of one finished slot (see SlotSolver::iterate).
+struct SlotDone {
+  void* tag;
+  int slot;
+  hh_result res;
+};
+
+// Continuous-batching MPGMRES driver over S slots (krylov.cu).  Right-hand sides are
+// admitted into free slots between iterations; every iteration advances all active slots
+// by one block Arnoldi step with a single batched sweep over their columns; a slot that
+// converges (or stops) is finalised and freed at once.  Not thread safe: one owner thread.
+class SlotSolver {
+ public:
+  explicit SlotSolver(Engine& E);
+  ~SlotSolver();
+  SlotSolver(const SlotSolver&) = delete;
+  SlotSolver& operator=(const SlotSolver&) = delete;
+  int init(int slots);
+  int free_slots() const;
+  int busy() const;
+  // b[q], x[q]: host or device pointers of one column each; returns the number admitted
+  // (at most free_slots()), or -status.
+  int admit(int count, const double2* const* b, double2* const* x, const double* tol, void* const* tags,
+            int* slot_out);
+  // One iteration of all active slots; appends the slots finished during it to out.
+  int iterate(std::vector<SlotDone>& out);
+
+ private:
+  struct Impl;
+  Impl* impl;
 };
 
 }  // namespace hh

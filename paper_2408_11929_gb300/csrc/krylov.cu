@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "common.cuh"
@@ -25,8 +26,15 @@ void launch_pack(Engine& E, const double2* const* srcptr, const double* scale, i
 void launch_unpack(Engine& E, const void* X, int C, int t, int4 codes, double2* dst, size_t stride);
 
 struct KState {
-  int nrhs, t, D, maxit, maxV, maxZ, GX, GQ, scheme, passes;
-  double tol, eta;
+  int nrhs, t, D, maxit, maxV, maxZ, GX, GQ, scheme, passes;  // nrhs = number of slots
+  double eta;
+  double* tolv;            // per slot tolerance
+  double2** Zcur;          // per slot: this iteration's Z block (t columns)
+  double2** Vcur;          // per slot: this iteration's block of new basis vectors
+  int* adm;                // per slot: 1 = being admitted now (start kernels)
+  int* fin;                // per slot: 1 = being finalised now (solution kernels)
+  double2** xout;          // per slot: where its solution goes
+  double2* bdev;           // per slot right-hand side (slots x D)
   double* beta;
   int *done, *status, *nV, *nZ, *iters, *nacc, *amap;
   double *rho, *nu, *cs, *hist, *npart;
@@ -89,6 +97,55 @@ __global__ void spmv_kernel(const double2* __restrict__ x, double2* __restrict__
   }
 }
 
+// y[c] = A x[c] for columns given by pointer tables
+__global__ void spmv_tab_kernel(const double2* const* __restrict__ xcol, double2* const* __restrict__ ycol, int ncols,
+                                Coef cf) {
+  const int n = cf.n, m = n + 1;
+  const size_t D = (size_t)m * m;
+  const double dg = cf.diag();
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < D * ncols; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = idx / D, g = idx % D;
+    const int j = (int)(g / m), i = (int)(g % m);
+    const double2* xc = xcol[c];
+    const int type = line_type(j, n);
+    double2 acc = make_double2(0, 0);
+    cfma(acc, cf.centre(i, type), xc[g]);
+    const double2 hz = cf.horiz(type);
+    if (i + 1 <= n) cfma(acc, hz, xc[g + 1]);
+    if (i >= 1) cfma(acc, hz, xc[g - 1]);
+    const double2 vt = cf.vert(i);
+    if (j >= 1) {
+      cfma(acc, vt, xc[g - m]);
+      if (i >= 1) { const double2 v = xc[g - m - 1]; acc.x += dg * v.x; acc.y += dg * v.y; }
+    }
+    if (j + 1 <= n) {
+      cfma(acc, vt, xc[g + m]);
+      if (i + 1 <= n) { const double2 v = xc[g + m + 1]; acc.x += dg * v.x; acc.y += dg * v.y; }
+    }
+    ycol[c][g] = acc;
+  }
+}
+
+// Column tables of one iteration for the active slots act[0..nact): sweep sources, Z
+// destinations (= operator inputs) and operator outputs (W).
+struct IterTables {
+  const double2** src;
+  double* scale;
+  double2** zdst;
+  double2** wdst;
+};
+__global__ void gather_tables_kernel(KState S, const int* __restrict__ act, int nact, IterTables T,
+                                     double2* __restrict__ W) {
+  const int t = S.t;
+  for (int q = threadIdx.x; q < nact * t; q += blockDim.x) {
+    const int a = q / t, d = q % t, r = act[a];
+    T.src[q] = S.srcptr[r * t + d];
+    T.scale[q] = S.scale[r * t + d];
+    T.zdst[q] = S.Zcur[r] + (size_t)d * S.D;
+    T.wdst[q] = W + ((size_t)r * t + d) * S.D;
+  }
+}
+
 // b = -M f_I for Gaussians src rows (x0, y0, sigma, re, im)
 __global__ void gauss_nodal_kernel(const double* __restrict__ src, int nsrc, int n, double2* f) {
   const int m = n + 1;
@@ -137,8 +194,9 @@ __global__ void mass_neg_kernel(const double2* __restrict__ f, double2* __restri
 }
 
 // ------------------------------------------------------------------ start / norms
-__global__ void norm_part_kernel(const double2* __restrict__ x, size_t D, double* part, int GX) {
+__global__ void norm_part_kernel(const double2* __restrict__ x, size_t D, double* part, int GX, const int* mask) {
   const int r = blockIdx.y;
+  if (mask && !mask[r]) return;
   const double2* xr = x + (size_t)r * D;
   double v[1] = {0};
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < D; g += (size_t)GX * blockDim.x) v[0] += cabs2(xr[g]);
@@ -147,9 +205,9 @@ __global__ void norm_part_kernel(const double2* __restrict__ x, size_t D, double
   if (threadIdx.x == 0) part[r * GX + blockIdx.x] = v[0];
 }
 
-__global__ void start_kernel(KState S, const double2* __restrict__ b) {
+__global__ void start_kernel(KState S) {
   const int r = blockIdx.x;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && S.adm[r]) {
     double s = 0;
     for (int q = 0; q < S.GX; ++q) s += S.npart[r * S.GX + q];
     const double beta = sqrt(s);
@@ -175,8 +233,10 @@ __global__ void start_kernel(KState S, const double2* __restrict__ b) {
   }
 }
 
-__global__ void scale_copy_kernel(KState S, const double2* __restrict__ b) {
+__global__ void scale_copy_kernel(KState S) {
   const int r = blockIdx.y;
+  if (!S.adm[r]) return;
+  const double2* b = S.bdev;
   const double beta = S.beta[r];
   const double inv = beta > 0 ? 1.0 / beta : 0.0;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < (size_t)S.D; g += (size_t)gridDim.x * blockDim.x)
@@ -283,15 +343,15 @@ __global__ void __launch_bounds__(256) gs_update_kernel(KState S, double2* __res
 // every CTA of the right-hand side sums the GQ partials in the same order (so all take the
 // same deflation decisions).  The barrier sequence is the same for every CTA.
 template <int TT>
-__global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__ W, double2* __restrict__ Vk,
-                                                 unsigned* bar, int* err, long long budget) {
+__global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__ W, unsigned* bar, int* err,
+                                                 long long budget) {
   const int r = blockIdx.y;
   const bool active = S.done[r] == 0;
   const size_t D = S.D;
   const size_t chunk = (D + S.GQ - 1) / S.GQ;
   const size_t g0 = blockIdx.x * chunk, g1 = min(D, g0 + chunk);
   double2* Wr = W + (size_t)r * TT * D;
-  double2* Vr = Vk + (size_t)r * TT * D;
+  double2* Vr = S.Vcur[r];
   __shared__ double sh[32 * 8];
   __shared__ double2 red_out[TT];
   unsigned target = 0;
@@ -400,7 +460,7 @@ __device__ void givens(double2 a, double2 b, double& c, double2& s) {
   s = cmul(ph, make_double2(b.x / rr, -b.y / rr));
 }
 
-__global__ void hess_kernel(KState S, double2* __restrict__ Zk, double2* __restrict__ Vk) {
+__global__ void hess_kernel(KState S) {
   const int r = blockIdx.x;
   if (threadIdx.x != 0 || S.done[r]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -442,10 +502,10 @@ __global__ void hess_kernel(KState S, double2* __restrict__ Zk, double2* __restr
     const double2 g0 = g[c];
     g[c] = cscale(g0, cs);
     g[c + 1] = cmul(make_double2(-sn.x, sn.y), g0);
-    S.Zptr[(size_t)r * S.maxZ + c] = Zk + ((size_t)r * t + j) * D;
+    S.Zptr[(size_t)r * S.maxZ + c] = S.Zcur[r] + (size_t)j * D;
     nZ = c + 1;
   }
-  for (int q = 0; q < nacc; ++q) S.Vptr[(size_t)r * S.maxV + nold + q] = Vk + ((size_t)r * t + q) * D;
+  for (int q = 0; q < nacc; ++q) S.Vptr[(size_t)r * S.maxV + nold + q] = S.Vcur[r] + (size_t)q * D;
   S.nV[r] = nold + nacc;
   S.nZ[r] = nZ;
   const int it = S.iters[r] + 1;
@@ -454,17 +514,17 @@ __global__ void hess_kernel(KState S, double2* __restrict__ Zk, double2* __restr
   S.rho[r] = rho;
   S.hist[(size_t)r * S.maxit + it - 1] = rho / S.beta[r];
   if (!isfinite(rho)) { S.status[r] = HH_ENAN; S.done[r] = 1; }
-  else if (rho / S.beta[r] <= S.tol) { S.status[r] = HH_OK; S.done[r] = 1; }
+  else if (rho / S.beta[r] <= S.tolv[r]) { S.status[r] = HH_OK; S.done[r] = 1; }
   else if (it >= S.maxit) { S.status[r] = HH_ENOCONV; S.done[r] = 1; }
 }
 
 // next sources: sum of the new vectors (t > 2), with its norm
-__global__ void source_sum_kernel(KState S, const double2* __restrict__ Vk) {
+__global__ void source_sum_kernel(KState S) {
   const int r = blockIdx.y;
   if (S.done[r] || S.scheme != HH_SCHEME_SUM) return;
   const int nacc = S.nacc[r];
   const size_t D = S.D;
-  const double2* Vr = Vk + (size_t)r * S.t * D;
+  const double2* Vr = S.Vcur[r];
   double2* s = S.sbuf + (size_t)r * D;
   double v[1] = {0};
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < D; g += (size_t)S.GX * blockDim.x) {
@@ -478,12 +538,12 @@ __global__ void source_sum_kernel(KState S, const double2* __restrict__ Vk) {
   if (threadIdx.x == 0) S.npart[r * S.GX + blockIdx.x] = v[0];
 }
 
-__global__ void source_final_kernel(KState S, const double2* __restrict__ Vk) {
+__global__ void source_final_kernel(KState S) {
   const int r = blockIdx.x;
   if (threadIdx.x != 0 || S.done[r]) return;
   const int t = S.t;
   const size_t D = S.D;
-  const double2* Vr = Vk + (size_t)r * t * D;
+  const double2* Vr = S.Vcur[r];
   if (S.scheme == HH_SCHEME_SUM) {
     double s = 0;
     for (int q = 0; q < S.GX; ++q) s += S.npart[r * S.GX + q];
@@ -507,7 +567,7 @@ __global__ void source_final_kernel(KState S, const double2* __restrict__ Vk) {
 // ------------------------------------------------------------------ final solution
 __global__ void backsub_kernel(KState S) {
   const int r = blockIdx.x;
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x != 0 || !S.fin[r]) return;
   const int nZ = S.nZ[r];
   const double2* Rb = S.Rrot + (size_t)r * ((size_t)S.maxZ * (S.maxZ + 1) / 2);
   const double2* g = S.g + (size_t)r * (S.maxZ + 1);
@@ -521,8 +581,10 @@ __global__ void backsub_kernel(KState S) {
   }
 }
 
-__global__ void xsol_kernel(KState S, double2* __restrict__ x) {
+__global__ void xsol_kernel(KState S) {
   const int r = blockIdx.y;
+  if (!S.fin[r]) return;
+  double2* x = S.xout[r];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nZ = S.nZ[r];
   double2* ys = reinterpret_cast<double2*>(smem_raw);
@@ -536,16 +598,21 @@ __global__ void xsol_kernel(KState S, double2* __restrict__ x) {
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < D; g += (size_t)gridDim.x * blockDim.x) {
     double2 a = make_double2(0, 0);
     for (int c = 0; c < nZ; ++c) cfma(a, zp[c][g], ys[c]);
-    x[(size_t)r * D + g] = a;
+    x[g] = a;
   }
 }
 
-__global__ void resid_part_kernel(const double2* __restrict__ b, const double2* __restrict__ Ax, size_t D,
-                                  double* part, int GX) {
+__global__ void resid_part_kernel(KState S, const double2* __restrict__ W) {
   const int r = blockIdx.y;
+  if (!S.fin[r]) return;
+  const size_t D = S.D;
+  const int GX = S.GX;
+  double* part = S.npart;
+  const double2* b = S.bdev + (size_t)r * D;
+  const double2* Ax = W + (size_t)r * S.t * D;
   double v[1] = {0};
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < D; g += (size_t)GX * blockDim.x) {
-    const double2 d = csub(b[(size_t)r * D + g], Ax[(size_t)r * D + g]);
+    const double2 d = csub(b[g], Ax[g]);
     v[0] += cabs2(d);
   }
   __shared__ double sh[32];
@@ -555,7 +622,7 @@ __global__ void resid_part_kernel(const double2* __restrict__ b, const double2* 
 
 __global__ void resid_final_kernel(KState S) {
   const int r = blockIdx.x;
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x != 0 || !S.fin[r]) return;
   double s = 0;
   for (int q = 0; q < S.GX; ++q) s += S.npart[r * S.GX + q];
   S.res_exp[r] = S.beta[r] > 0 ? sqrt(s) / S.beta[r] : 0.0;
@@ -568,189 +635,371 @@ int qr_blocks_per_sm() {
   return std::min(a, b);
 }
 
-// ------------------------------------------------------------------ host driver
-namespace {
-struct DevBuf {
-  Engine* E = nullptr;
-  std::vector<void*> ptrs;
-  template <typename T> T* get(size_t count) {
-    void* p = nullptr;
-    if (E->dmalloc(&p, std::max<size_t>(count * sizeof(T), 16))) return nullptr;
-    cudaMemsetAsync(p, 0, std::max<size_t>(count * sizeof(T), 16), E->stream);
-    ptrs.push_back(p);
-    return reinterpret_cast<T*>(p);
+void launch_unpack_tab(Engine& E, const void* X, int C, int t, int4 codes, double2* const* dstcol);
+
+// ------------------------------------------------------------------ slot solver
+// Continuous batching: S slots, each an independent MPGMRES solve (its own basis, Hessenberg
+// matrix, tolerance and iteration count).  Every iteration sweeps the columns of the active
+// slots only; slots finish independently and new right-hand sides are admitted between
+// iterations.  Each slot's per-iteration blocks (t columns of Z and of new basis vectors)
+// come from a pool of equally sized device blocks and return to it when the slot finishes.
+struct SlotSolver::Impl {
+  Engine& E;
+  int S = 0, t = 0, maxit = 0;
+  size_t D = 0;
+  KState K{};
+  std::vector<void*> owned;
+  double2* W = nullptr;       // S * t * D operator outputs / residual scratch
+  double2* xstage = nullptr;  // S * D solutions of slots whose caller buffer is host memory
+  int* d_act = nullptr;
+  IterTables T{};
+  // pinned staging
+  int *h_act = nullptr, *h_done = nullptr, *h_iters = nullptr, *h_status = nullptr, *h_mask = nullptr;
+  double *h_rho = nullptr, *h_beta = nullptr, *h_res = nullptr, *h_tolv = nullptr;
+  double2 **h_zcur = nullptr, **h_vcur = nullptr, **h_xout = nullptr, **h_tab0 = nullptr, **h_tab1 = nullptr;
+  std::vector<void*> pinned;
+  struct Slot {
+    bool busy = false, done = false;
+    void* tag = nullptr;
+    double2* xdev = nullptr;  // where the device solution goes
+    double* xuser = nullptr;  // caller buffer (host) or nullptr
+    std::vector<void*> blocks;
+  };
+  std::vector<Slot> slots;
+  std::vector<void*> pool;
+  int4 codes{};
+
+  explicit Impl(Engine& e) : E(e) {}
+  ~Impl() {
+    cudaStreamSynchronize(E.stream);
+    for (void* p : owned) E.dfree(p);
+    for (void* p : pool) E.dfree(p);
+    for (auto& sl : slots)
+      for (void* p : sl.blocks) E.dfree(p);
+    for (void* p : pinned) cudaFreeHost(p);
   }
-  ~DevBuf() {
-    for (void* p : ptrs) E->dfree(p);
+  template <typename T_> T_* dev(size_t count) {
+    void* p = nullptr;
+    if (E.dmalloc(&p, std::max<size_t>(count * sizeof(T_), 16))) return nullptr;
+    cudaMemsetAsync(p, 0, std::max<size_t>(count * sizeof(T_), 16), E.stream);
+    owned.push_back(p);
+    return reinterpret_cast<T_*>(p);
+  }
+  template <typename T_> T_* host(size_t count) {
+    void* p = nullptr;
+    if (cudaMallocHost(&p, std::max<size_t>(count * sizeof(T_), 16)) != cudaSuccess) return nullptr;
+    pinned.push_back(p);
+    return reinterpret_cast<T_*>(p);
+  }
+  void* block() {
+    if (!pool.empty()) {
+      void* p = pool.back();
+      pool.pop_back();
+      return p;
+    }
+    void* p = nullptr;
+    if (E.dmalloc(&p, (size_t)t * D * sizeof(double2))) return nullptr;
+    return p;
+  }
+
+  int init(int nslots) {
+    S = nslots;
+    t = E.t;
+    maxit = E.opts.maxit;
+    D = (size_t)E.m * E.m;
+    K.nrhs = S; K.t = t; K.D = (int)D; K.maxit = maxit; K.maxV = 1 + maxit * t; K.maxZ = maxit * t;
+    K.eta = E.opts.deflate_eta; K.passes = E.opts.gs_passes;
+    K.scheme = E.opts.scheme != HH_SCHEME_AUTO ? E.opts.scheme
+                                               : (t == 2 ? HH_SCHEME_CROSS : (t > 2 ? HH_SCHEME_SUM : HH_SCHEME_CROSS));
+    K.GX = std::max(1, std::min(E.num_sms * 2 / S + 1, (int)((D + 255) / 256)));
+    K.GX = std::min(K.GX, E.num_sms * 2);
+    const int cap = E.num_sms * E.coop_per_sm;
+    K.GQ = std::max(1, std::min(cap / S, E.num_sms));
+    if (K.GQ * S > cap) return (set_error("too many slots for one cooperative QR launch"), HH_EINVAL);
+    K.beta = dev<double>(S); K.done = dev<int>(S); K.status = dev<int>(S);
+    K.nV = dev<int>(S); K.nZ = dev<int>(S); K.iters = dev<int>(S); K.nacc = dev<int>(S);
+    K.amap = dev<int>((size_t)S * t); K.rho = dev<double>(S); K.nu = dev<double>((size_t)S * t);
+    K.cs = dev<double>((size_t)S * K.maxZ); K.sn = dev<double2>((size_t)S * K.maxZ);
+    K.hist = dev<double>((size_t)S * maxit); K.npart = dev<double>((size_t)S * K.GX);
+    K.Vptr = dev<double2*>((size_t)S * K.maxV); K.Zptr = dev<double2*>((size_t)S * K.maxZ);
+    K.Hacc = dev<double2>((size_t)S * K.maxV * t); K.Hthis = dev<double2>((size_t)S * K.maxV * t);
+    K.Hpart = dev<double2>((size_t)S * K.maxV * t * K.GX); K.Rnew = dev<double2>((size_t)S * t * t);
+    K.g = dev<double2>((size_t)S * (K.maxZ + 1));
+    K.Rrot = dev<double2>((size_t)S * ((size_t)K.maxZ * (K.maxZ + 1) / 2));
+    K.y = dev<double2>((size_t)S * K.maxZ); K.qpart = dev<double2>((size_t)2 * S * K.GQ * 4);
+    K.sbuf = dev<double2>((size_t)S * D); K.V0 = dev<double2>((size_t)S * D);
+    K.srcptr = (const double2**)dev<double2*>((size_t)S * t); K.scale = dev<double>((size_t)S * t);
+    K.res_exp = dev<double>(S);
+    K.tolv = dev<double>(S); K.Zcur = dev<double2*>(S); K.Vcur = dev<double2*>(S);
+    K.adm = dev<int>(S); K.fin = dev<int>(S); K.xout = dev<double2*>(S); K.bdev = dev<double2>((size_t)S * D);
+    W = dev<double2>((size_t)S * t * D);
+    xstage = dev<double2>((size_t)S * D);
+    d_act = dev<int>(S);
+    T.src = (const double2**)dev<double2*>((size_t)S * t); T.scale = dev<double>((size_t)S * t);
+    T.zdst = dev<double2*>((size_t)S * t); T.wdst = dev<double2*>((size_t)S * t);
+    if (!W || !xstage || !T.wdst || !K.bdev || !K.Rrot) return HH_ENOMEM;
+    h_act = host<int>(S); h_done = host<int>(S); h_iters = host<int>(S); h_status = host<int>(S);
+    h_mask = host<int>(S); h_rho = host<double>(S); h_beta = host<double>(S); h_res = host<double>(S);
+    h_tolv = host<double>(S);
+    h_zcur = host<double2*>(S); h_vcur = host<double2*>(S); h_xout = host<double2*>(S);
+    h_tab0 = host<double2*>(S); h_tab1 = host<double2*>(S);
+    if (!h_tab1) return (set_error("pinned host allocation failed"), HH_ENOMEM);
+    for (int r = 0; r < S; ++r) h_done[r] = 1;
+    cudaMemcpyAsync(K.done, h_done, sizeof(int) * S, cudaMemcpyHostToDevice, E.stream);
+    slots.assign(S, Slot());
+    if (E.ensure_sweep_ws(S * t)) return HH_ENOMEM;
+    int* cp = &codes.x;
+    for (int d = 0; d < 4; ++d) cp[d] = d < t ? E.dir_codes[d] : 0;
+    cudaError_t e = cudaStreamSynchronize(E.stream);
+    if (e != cudaSuccess) return (E.set_cuda_error(e, "slot solver init"), HH_ECUDA);
+    return HH_OK;
+  }
+
+  int free_slots() const {
+    int c = 0;
+    for (auto& sl : slots) c += !sl.busy;
+    return c;
+  }
+  int busy() const { return S - free_slots(); }
+
+  // Admit right-hand sides into free slots; returns the number admitted.  b[q] and x[q] may be
+  // host or device pointers (unified addressing): a host x is filled when the slot finishes.
+  int admit(int count, const double2* const* b, double2* const* x, const double* tol, void* const* tags,
+            int* slot_out) {
+    for (int r = 0; r < S; ++r) h_mask[r] = 0;
+    int used = 0;
+    for (int q = 0; q < count; ++q) {
+      int r = -1;
+      for (int c = 0; c < S; ++c)
+        if (!slots[c].busy) { r = c; break; }
+      if (r < 0) break;
+      cudaPointerAttributes pa{};
+      bool x_dev = cudaPointerGetAttributes(&pa, x[q]) == cudaSuccess &&
+                   (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+      cudaGetLastError();
+      Slot& sl = slots[r];
+      sl.busy = true;
+      sl.done = false;
+      sl.tag = tags ? tags[q] : nullptr;
+      sl.xuser = x_dev ? nullptr : reinterpret_cast<double*>(x[q]);
+      sl.xdev = x_dev ? x[q] : xstage + (size_t)r * D;
+      cudaMemcpyAsync(K.bdev + (size_t)r * D, b[q], D * sizeof(double2), cudaMemcpyDefault, E.stream);
+      h_tolv[r] = tol[q];
+      h_mask[r] = 1;
+      h_xout[r] = sl.xdev;
+      if (slot_out) slot_out[q] = r;
+      ++used;
+    }
+    if (!used) return 0;
+    cudaMemcpyAsync(K.adm, h_mask, sizeof(int) * S, cudaMemcpyHostToDevice, E.stream);
+    cudaMemcpyAsync(K.xout, h_xout, sizeof(double2*) * S, cudaMemcpyHostToDevice, E.stream);
+    cudaMemcpyAsync(K.tolv, h_tolv, sizeof(double) * S, cudaMemcpyHostToDevice, E.stream);
+    dim3 ng(K.GX, S);
+    norm_part_kernel<<<ng, 256, 0, E.stream>>>(K.bdev, D, K.npart, K.GX, K.adm);
+    start_kernel<<<S, 32, 0, E.stream>>>(K);
+    scale_copy_kernel<<<ng, 256, 0, E.stream>>>(K);
+    E.count_launch(3);
+    // slots whose right-hand side is zero (or not finite) finish at once
+    cudaMemcpyAsync(h_done, K.done, sizeof(int) * S, cudaMemcpyDeviceToHost, E.stream);
+    cudaError_t e = cudaStreamSynchronize(E.stream);
+    if (e != cudaSuccess) return -(E.set_cuda_error(e, "admit"), HH_ECUDA);
+    cudaMemsetAsync(K.adm, 0, sizeof(int) * S, E.stream);
+    return used;
+  }
+
+  template <int TT>
+  void gs_and_qr(cudaError_t& ce) {
+    dim3 gsgrid(K.GX, S);
+    for (int pass = 0; pass < K.passes; ++pass) {
+      gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K, W);
+      gs_reduce_kernel<<<S, 256, 0, E.stream>>>(K, pass == 0);
+      const size_t smem = (size_t)K.maxV * TT * sizeof(double2) + (size_t)K.maxV * sizeof(void*);
+      cudaFuncSetAttribute((const void*)gs_update_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      gs_update_kernel<TT><<<gsgrid, 256, smem, E.stream>>>(K, W);
+      E.count_launch(3);
+    }
+    cudaMemsetAsync(E.bar, 0, sizeof(unsigned), E.stream);
+    void* args[] = {(void*)&K, (void*)&W, (void*)&E.bar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
+    ce = E.launch_coop((const void*)qr_kernel<TT>, K.GQ, 256, 0, args, S);
+  }
+
+  struct Done {
+    void* tag;
+    int slot;
+    hh_result res;
+  };
+
+  // One MPGMRES iteration for every active slot; completed slots are finalised into out.
+  int iterate(std::vector<Done>& out) {
+    int nact = 0;
+    for (int r = 0; r < S; ++r)
+      if (slots[r].busy && !slots[r].done && !h_done[r]) h_act[nact++] = r;
+    if (nact > 0) {
+      for (int a = 0; a < nact; ++a) {
+        const int r = h_act[a];
+        void* z = block();
+        void* v = block();
+        if (!z || !v) return HH_ENOMEM;
+        slots[r].blocks.push_back(z);
+        slots[r].blocks.push_back(v);
+        h_zcur[r] = (double2*)z;
+        h_vcur[r] = (double2*)v;
+      }
+      cudaMemcpyAsync(K.Zcur, h_zcur, sizeof(double2*) * S, cudaMemcpyHostToDevice, E.stream);
+      cudaMemcpyAsync(K.Vcur, h_vcur, sizeof(double2*) * S, cudaMemcpyHostToDevice, E.stream);
+      cudaMemcpyAsync(d_act, h_act, sizeof(int) * nact, cudaMemcpyHostToDevice, E.stream);
+      gather_tables_kernel<<<1, 256, 0, E.stream>>>(K, d_act, nact, T, W);
+      E.count_launch();
+      const int C = nact * t;
+      launch_pack(E, T.src, T.scale, C, t, codes, E.w_rin);
+      int rc = E.run_sweep(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0);
+      if (rc) return rc;
+      launch_unpack_tab(E, E.w_v, C, t, codes, T.zdst);
+      E.tick_begin(Engine::K_SPMV);
+      spmv_tab_kernel<<<E.grid_for(D * C), 256, 0, E.stream>>>(T.zdst, T.wdst, C, E.coef);
+      E.count_launch();
+      E.tick_end(Engine::K_SPMV, 2.0 * C * D * 16.0, 0);
+      E.tick_begin(Engine::K_GS);
+      cudaError_t ce = cudaSuccess;
+      switch (t) {
+        case 1: gs_and_qr<1>(ce); break;
+        case 2: gs_and_qr<2>(ce); break;
+        case 3: gs_and_qr<3>(ce); break;
+        default: gs_and_qr<4>(ce); break;
+      }
+      {
+        double nv = 0;
+        for (int a = 0; a < nact; ++a) nv += 1.0 + (double)(slots[h_act[a]].blocks.size() / 2 - 1) * t;
+        E.tick_end(Engine::K_GS, K.passes * (2.0 * nv * D * 16 + 3.0 * C * D * 16) + 6.0 * C * D * 16, 0);
+      }
+      if (ce != cudaSuccess) return (E.set_cuda_error(ce, "qr launch"), HH_ECUDA);
+      const size_t hsmem = (size_t)(K.maxZ + 2) * sizeof(double2);
+      cudaFuncSetAttribute((const void*)hess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+      hess_kernel<<<S, 32, hsmem, E.stream>>>(K);
+      source_sum_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K);
+      source_final_kernel<<<S, 32, 0, E.stream>>>(K);
+      E.count_launch(3);
+    }
+    cudaMemcpyAsync(h_done, K.done, sizeof(int) * S, cudaMemcpyDeviceToHost, E.stream);
+    cudaError_t se = cudaStreamSynchronize(E.stream);
+    if (se != cudaSuccess) return (E.set_cuda_error(se, "iteration"), HH_ECUDA);
+    int rc = E.check_device_error("iteration");
+    if (rc) return rc;
+    return finalize(out);
+  }
+
+  // Solution, explicit residual and result of every slot that has just finished.
+  int finalize(std::vector<Done>& out) {
+    int nfin = 0;
+    for (int r = 0; r < S; ++r) {
+      h_mask[r] = (slots[r].busy && !slots[r].done && h_done[r]) ? 1 : 0;
+      if (h_mask[r]) {
+        h_tab0[nfin] = slots[r].xdev;
+        h_tab1[nfin] = W + (size_t)r * t * D;
+        ++nfin;
+      }
+    }
+    if (!nfin) return HH_OK;
+    cudaMemcpyAsync(K.fin, h_mask, sizeof(int) * S, cudaMemcpyHostToDevice, E.stream);
+    cudaMemcpyAsync(T.zdst, h_tab0, sizeof(double2*) * nfin, cudaMemcpyHostToDevice, E.stream);
+    cudaMemcpyAsync(T.wdst, h_tab1, sizeof(double2*) * nfin, cudaMemcpyHostToDevice, E.stream);
+    backsub_kernel<<<S, 32, 0, E.stream>>>(K);
+    const size_t xsmem = (size_t)K.maxZ * (sizeof(double2) + sizeof(void*));
+    cudaFuncSetAttribute((const void*)xsol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem);
+    xsol_kernel<<<dim3(K.GX, S), 256, xsmem, E.stream>>>(K);
+    E.tick_begin(Engine::K_SPMV);
+    spmv_tab_kernel<<<E.grid_for(D * nfin), 256, 0, E.stream>>>((const double2* const*)T.zdst, T.wdst, nfin, E.coef);
+    E.tick_end(Engine::K_SPMV, 2.0 * nfin * D * 16.0, 0);
+    resid_part_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K, W);
+    resid_final_kernel<<<S, 32, 0, E.stream>>>(K);
+    E.count_launch(5);
+    cudaMemcpyAsync(h_status, K.status, sizeof(int) * S, cudaMemcpyDeviceToHost, E.stream);
+    cudaMemcpyAsync(h_iters, K.iters, sizeof(int) * S, cudaMemcpyDeviceToHost, E.stream);
+    cudaMemcpyAsync(h_rho, K.rho, sizeof(double) * S, cudaMemcpyDeviceToHost, E.stream);
+    cudaMemcpyAsync(h_beta, K.beta, sizeof(double) * S, cudaMemcpyDeviceToHost, E.stream);
+    cudaMemcpyAsync(h_res, K.res_exp, sizeof(double) * S, cudaMemcpyDeviceToHost, E.stream);
+    for (int r = 0; r < S; ++r)
+      if (h_mask[r] && slots[r].xuser)
+        cudaMemcpyAsync(slots[r].xuser, slots[r].xdev, D * sizeof(double2), cudaMemcpyDeviceToHost, E.stream);
+    cudaMemsetAsync(K.fin, 0, sizeof(int) * S, E.stream);
+    cudaError_t e = cudaStreamSynchronize(E.stream);
+    if (e != cudaSuccess) return (E.set_cuda_error(e, "finalize"), HH_ECUDA);
+    for (int r = 0; r < S; ++r) {
+      if (!h_mask[r]) continue;
+      Done d;
+      d.tag = slots[r].tag;
+      d.slot = r;
+      std::memset(&d.res, 0, sizeof(d.res));
+      d.res.iterations = h_iters[r];
+      d.res.rel_res_implicit = h_beta[r] > 0 ? h_rho[r] / h_beta[r] : 0.0;
+      d.res.rel_res_explicit = h_res[r];
+      d.res.status = (hh_status)h_status[r];
+      out.push_back(d);
+      for (void* p : slots[r].blocks) pool.push_back(p);
+      slots[r].blocks.clear();
+      slots[r] = Slot();
+    }
+    return HH_OK;
   }
 };
-}  // namespace
 
-template <int TT>
-static void launch_iteration_gs(Engine& E, KState& S, double2* W, dim3 gsgrid) {
-  for (int pass = 0; pass < S.passes; ++pass) {
-    gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(S, W);
-    gs_reduce_kernel<<<S.nrhs, 256, 0, E.stream>>>(S, pass == 0);
-    const size_t smem = (size_t)S.maxV * TT * sizeof(double2) + (size_t)S.maxV * sizeof(void*);
-    cudaFuncSetAttribute((const void*)gs_update_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    gs_update_kernel<TT><<<gsgrid, 256, smem, E.stream>>>(S, W);
-    E.count_launch(3);
-  }
+SlotSolver::SlotSolver(Engine& E) : impl(new Impl(E)) {}
+SlotSolver::~SlotSolver() { delete impl; }
+int SlotSolver::init(int slots) { return impl->init(slots); }
+int SlotSolver::free_slots() const { return impl->free_slots(); }
+int SlotSolver::busy() const { return impl->busy(); }
+int SlotSolver::admit(int count, const double2* const* b, double2* const* x, const double* tol, void* const* tags,
+                      int* slot_out) {
+  return impl->admit(count, b, x, tol, tags, slot_out);
 }
-
-template <int TT>
-static cudaError_t launch_qr(Engine& E, KState& S, double2* W, double2* Vk) {
-  cudaMemsetAsync(E.bar, 0, sizeof(unsigned), E.stream);
-  void* args[] = {(void*)&S, (void*)&W, (void*)&Vk, (void*)&E.bar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
-  return E.launch_coop((const void*)qr_kernel<TT>, S.GQ, 256, 0, args, S.nrhs);
+int SlotSolver::iterate(std::vector<SlotDone>& out) {
+  std::vector<Impl::Done> d;
+  const int rc = impl->iterate(d);
+  for (auto& q : d) out.push_back(SlotDone{q.tag, q.slot, q.res});
+  return rc;
 }
 
 int Engine::solve_batch_dev(int nrhs, const double2* b, double2* x, double tol, hh_result* res) {
-  const int maxit = opts.maxit;
-  const size_t D = (size_t)m * m;
-  KState S{};
-  S.nrhs = nrhs; S.t = t; S.D = (int)D; S.maxit = maxit; S.maxV = 1 + maxit * t; S.maxZ = maxit * t;
-  S.tol = tol; S.eta = opts.deflate_eta; S.passes = opts.gs_passes;
-  S.scheme = opts.scheme != HH_SCHEME_AUTO ? opts.scheme : (t == 2 ? HH_SCHEME_CROSS : (t > 2 ? HH_SCHEME_SUM : HH_SCHEME_CROSS));
-  S.GX = std::max(1, std::min(num_sms * 2 / std::max(1, nrhs) + 1, (int)((D + 255) / 256)));
-  S.GX = std::min(S.GX, num_sms * 2);
-  {
-    int per_sm = coop_per_sm;
-    int cap = num_sms * per_sm;
-    S.GQ = std::max(1, std::min(cap / nrhs, num_sms));
-    if (S.GQ * nrhs > cap) return (set_error("too many right-hand sides for one cooperative QR launch"), HH_EINVAL);
+  if (!batch_solver || batch_slots != nrhs) {
+    delete batch_solver;
+    batch_solver = nullptr;
+    batch_slots = 0;
+    auto* fresh = new SlotSolver(*this);
+    const int irc = fresh->init(nrhs);
+    if (irc) {
+      delete fresh;
+      return irc;
+    }
+    batch_solver = fresh;
+    batch_slots = nrhs;
   }
-  DevBuf B;
-  B.E = this;
-  S.beta = B.get<double>(nrhs); S.done = B.get<int>(nrhs); S.status = B.get<int>(nrhs);
-  S.nV = B.get<int>(nrhs); S.nZ = B.get<int>(nrhs); S.iters = B.get<int>(nrhs); S.nacc = B.get<int>(nrhs);
-  S.amap = B.get<int>((size_t)nrhs * t); S.rho = B.get<double>(nrhs); S.nu = B.get<double>((size_t)nrhs * t);
-  S.cs = B.get<double>((size_t)nrhs * S.maxZ); S.sn = B.get<double2>((size_t)nrhs * S.maxZ);
-  S.hist = B.get<double>((size_t)nrhs * maxit); S.npart = B.get<double>((size_t)nrhs * S.GX);
-  S.Vptr = B.get<double2*>((size_t)nrhs * S.maxV); S.Zptr = B.get<double2*>((size_t)nrhs * S.maxZ);
-  S.Hacc = B.get<double2>((size_t)nrhs * S.maxV * t); S.Hthis = B.get<double2>((size_t)nrhs * S.maxV * t);
-  S.Hpart = B.get<double2>((size_t)nrhs * S.maxV * t * S.GX); S.Rnew = B.get<double2>((size_t)nrhs * t * t);
-  S.g = B.get<double2>((size_t)nrhs * (S.maxZ + 1));
-  S.Rrot = B.get<double2>((size_t)nrhs * ((size_t)S.maxZ * (S.maxZ + 1) / 2));
-  S.y = B.get<double2>((size_t)nrhs * S.maxZ); S.qpart = B.get<double2>((size_t)2 * nrhs * S.GQ * 4);
-  S.sbuf = B.get<double2>((size_t)nrhs * D); S.V0 = B.get<double2>((size_t)nrhs * D);
-  S.srcptr = (const double2**)B.get<double2*>((size_t)nrhs * t); S.scale = B.get<double>((size_t)nrhs * t);
-  S.res_exp = B.get<double>(nrhs);
-  double2* W = B.get<double2>((size_t)nrhs * t * D);
-  if (!W || !S.res_exp || !S.V0 || !S.Rrot) return HH_ENOMEM;
-  const int C = nrhs * t;
-  if (ensure_sweep_ws(C)) return HH_ENOMEM;
-  int4 codes = make_int4(0, 0, 0, 0);
-  int* cp = &codes.x;
-  for (int d = 0; d < t; ++d) cp[d] = dir_codes[d];
-
-  // beta, V0
-  dim3 ng(S.GX, nrhs);
-  norm_part_kernel<<<ng, 256, 0, stream>>>(b, D, S.npart, S.GX);
-  start_kernel<<<nrhs, 32, 0, stream>>>(S, b);
-  scale_copy_kernel<<<ng, 256, 0, stream>>>(S, b);
-  count_launch(3);
-
-  std::vector<double2*> zblocks, vblocks;
-  std::vector<int> h_done(nrhs), h_status(nrhs), h_iters(nrhs);
-  int* pinned_done = nullptr;
-  cudaMallocHost((void**)&pinned_done, sizeof(int) * nrhs);
+  SlotSolver& ss = *batch_solver;
   int rc = HH_OK;
-  int k = 0;
-  for (k = 1; k <= maxit; ++k) {
-    double2 *Zk = nullptr, *Vk = nullptr;
-    if (dmalloc((void**)&Zk, (size_t)C * D * sizeof(double2)) || dmalloc((void**)&Vk, (size_t)C * D * sizeof(double2))) {
-      dfree(Zk);
-      rc = HH_ENOMEM;
-      break;
-    }
-    zblocks.push_back(Zk);
-    vblocks.push_back(Vk);
-    // preconditioners: every (rhs, direction) pair is one sweep column
-    launch_pack(*this, S.srcptr, S.scale, C, t, codes, w_rin);
-    rc = run_sweep(w_rin, w_v, w_w, C, opts.single_sweep != 0);
-    if (rc) break;
-    launch_unpack(*this, w_v, C, t, codes, Zk, D);
-    // W = A Z_k
-    tick_begin(K_SPMV);
-    spmv_kernel<<<grid_for(D * C), 256, 0, stream>>>(Zk, W, C, coef);
-    count_launch();
-    tick_end(K_SPMV, 2.0 * C * D * 16.0, 0);
-    // Gram-Schmidt
-    tick_begin(K_GS);
-    dim3 gsgrid(S.GX, nrhs);
-    switch (t) {
-      case 1: launch_iteration_gs<1>(*this, S, W, gsgrid); break;
-      case 2: launch_iteration_gs<2>(*this, S, W, gsgrid); break;
-      case 3: launch_iteration_gs<3>(*this, S, W, gsgrid); break;
-      default: launch_iteration_gs<4>(*this, S, W, gsgrid); break;
-    }
-    cudaError_t ce;
-    switch (t) {
-      case 1: ce = launch_qr<1>(*this, S, W, Vk); break;
-      case 2: ce = launch_qr<2>(*this, S, W, Vk); break;
-      case 3: ce = launch_qr<3>(*this, S, W, Vk); break;
-      default: ce = launch_qr<4>(*this, S, W, Vk); break;
-    }
-    {
-      // algorithmic bytes of Gram-Schmidt this iteration: two passes of (read V + read W)
-      // for the dot products and (read V + read/write W) for the update, plus the block QR
-      const double nVmax = 1.0 + (double)(k - 1) * t;
-      tick_end(K_GS, nrhs * (S.passes * (2.0 * nVmax * D * 16 + 3.0 * t * D * 16) + 6.0 * t * D * 16), 0);
-    }
-    if (ce != cudaSuccess) { set_cuda_error(ce, "qr launch"); rc = HH_ECUDA; break; }
-    const size_t hsmem = (size_t)(S.maxZ + 2) * sizeof(double2);
-    cudaFuncSetAttribute((const void*)hess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
-    hess_kernel<<<nrhs, 32, hsmem, stream>>>(S, Zk, Vk);
-    source_sum_kernel<<<ng, 256, 0, stream>>>(S, Vk);
-    source_final_kernel<<<nrhs, 32, 0, stream>>>(S, Vk);
-    count_launch(4);
-    cudaMemcpyAsync(pinned_done, S.done, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, stream);
-    cudaError_t se = cudaStreamSynchronize(stream);
-    if (se != cudaSuccess) { set_cuda_error(se, "iteration"); rc = HH_ECUDA; break; }
-    rc = check_device_error("iteration");
-    if (rc) break;
-    bool all = true;
-    for (int r = 0; r < nrhs; ++r) all = all && pinned_done[r];
-    if (all) break;
+  const size_t D = (size_t)m * m;
+  std::vector<const double2*> bp(nrhs);
+  std::vector<double2*> xp(nrhs);
+  std::vector<double> tv(nrhs, tol);
+  std::vector<void*> tags(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    bp[r] = b + (size_t)r * D;
+    xp[r] = x + (size_t)r * D;
+    tags[r] = reinterpret_cast<void*>((intptr_t)r);
   }
-  if (rc == HH_OK) {
-    backsub_kernel<<<nrhs, 32, 0, stream>>>(S);
-    const size_t xsmem = (size_t)S.maxZ * (sizeof(double2) + sizeof(void*));
-    cudaFuncSetAttribute((const void*)xsol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem);
-    xsol_kernel<<<dim3(S.GX, nrhs), 256, xsmem, stream>>>(S, x);
-    tick_begin(K_SPMV);
-    spmv_kernel<<<grid_for(D * nrhs), 256, 0, stream>>>(x, W, nrhs, coef);
-    tick_end(K_SPMV, 2.0 * nrhs * D * 16.0, 0);
-    resid_part_kernel<<<ng, 256, 0, stream>>>(b, W, D, S.npart, S.GX);
-    resid_final_kernel<<<nrhs, 32, 0, stream>>>(S);
-    count_launch(5);
-    std::vector<double> h_rho(nrhs), h_beta(nrhs), h_res(nrhs);
-    cudaMemcpyAsync(h_status.data(), S.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(h_iters.data(), S.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(h_rho.data(), S.rho, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(h_beta.data(), S.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(h_res.data(), S.res_exp, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, stream);
-    cudaError_t se = cudaStreamSynchronize(stream);
-    if (se != cudaSuccess) { set_cuda_error(se, "final"); rc = HH_ECUDA; }
-    int worst = HH_OK;
-    for (int r = 0; r < nrhs && rc == HH_OK; ++r) {
-      if (res) {
-        res[r].iterations = h_iters[r];
-        res[r].rel_res_implicit = h_beta[r] > 0 ? h_rho[r] / h_beta[r] : 0.0;
-        res[r].rel_res_explicit = h_res[r];
-        res[r].status = (hh_status)h_status[r];
-      }
-      if (h_status[r] != HH_OK && worst == HH_OK) worst = h_status[r];
-    }
-    if (rc == HH_OK) rc = worst;
-  }
-  cudaStreamSynchronize(stream);
-  for (auto p : zblocks) dfree(p);
-  for (auto p : vblocks) dfree(p);
-  cudaFreeHost(pinned_done);
+  const int used = ss.admit(nrhs, bp.data(), xp.data(), tv.data(), tags.data(), nullptr);
+  if (used < 0) return -used;
+  std::vector<SlotDone> done;
+  // slots finished at admission (zero right-hand side)
+  rc = ss.iterate(done);
+  while (rc == HH_OK && ss.busy() > 0) rc = ss.iterate(done);
   collect_ticks();
-  return rc;
+  if (rc) return rc;
+  int worst = HH_OK;
+  for (auto& d : done) {
+    const int r = (int)(intptr_t)d.tag;
+    if (res) res[r] = d.res;
+    if (d.res.status != HH_OK && worst == HH_OK) worst = d.res.status;
+  }
+  return worst;
 }
 
 int Engine::apply_operator(int ncols, const double2* x, double2* y) {

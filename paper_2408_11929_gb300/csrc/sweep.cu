@@ -170,6 +170,26 @@ __global__ void unpack_kernel(const typename Cx<R>::T* __restrict__ X, int C, in
   }
 }
 
+// Same as unpack_kernel with one destination pointer per column.
+template <typename R>
+__global__ void unpack_tab_kernel(const typename Cx<R>::T* __restrict__ X, int C, int t, int4 codes, int n, int N,
+                                  int Rl, double2* const* __restrict__ dstcol) {
+  const int m = n + 1;
+  const size_t total = (size_t)(Rl + 1) * m * N * C;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % C);
+    size_t q = idx / C;
+    const int s = (int)(q % N);
+    q /= N;
+    const int i = (int)(q % m);
+    const int j = (int)(q / m);
+    if (j == Rl && s != N - 1) continue;
+    int io, jo;
+    frame_map(code_of(codes, c % t), i, s * Rl + j, n, io, jo);
+    dstcol[c][(size_t)jo * m + io] = to_d(X[idx]);
+  }
+}
+
 // Narrow step (at most 8 columns: the interface chains and the last strip's extra line
 // of a single right-hand side).  The CTA forms x (m x ncols) in shared memory, then one warp
 // per output row walks the row of A with two complex entries per lane per load and sums
@@ -396,6 +416,15 @@ static void launch_unpack_t(Engine& E, const void* X, int C, int t, int4 codes, 
 void launch_pack(Engine& E, const double2* const* srcptr, const double* scale, int C, int t, int4 codes, void* X) {
   if (E.precision == HH_PREC_FP32) launch_pack_t<float>(E, srcptr, scale, C, t, codes, X);
   else launch_pack_t<double>(E, srcptr, scale, C, t, codes, X);
+}
+void launch_unpack_tab(Engine& E, const void* X, int C, int t, int4 codes, double2* const* dstcol) {
+  if (E.precision == HH_PREC_FP32)
+    unpack_tab_kernel<float><<<E.grid_for(E.sweep_ws_bytes(C) / E.sweep_elem()), 256, 0, E.stream>>>(
+        reinterpret_cast<const float2*>(X), C, t, codes, E.n, E.N, E.R, dstcol);
+  else
+    unpack_tab_kernel<double><<<E.grid_for(E.sweep_ws_bytes(C) / E.sweep_elem()), 256, 0, E.stream>>>(
+        reinterpret_cast<const double2*>(X), C, t, codes, E.n, E.N, E.R, dstcol);
+  E.count_launch();
 }
 void launch_unpack(Engine& E, const void* X, int C, int t, int4 codes, double2* dst, size_t stride) {
   if (E.precision == HH_PREC_FP32) launch_unpack_t<float>(E, X, C, t, codes, dst, stride);

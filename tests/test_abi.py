@@ -55,6 +55,7 @@ def test_default_opts(lib):
     o = hh.default_opts()
     assert o.precision == hh.HH_PREC_FP64 and o.maxit == 200 and o.deflate_eta == 1e-10
     assert o.use_graph == 1 and o.timeout_cycles > 0 and o.bcr_depth == 0 and o.gs_passes == 2
+    assert o.serve_slots == 8
 
 
 @pytest.mark.parametrize("k,n,strips,dirs,kw", [
@@ -66,6 +67,8 @@ def test_default_opts(lib):
     (10.0, 32, 4, 15, {"maxit": 0}),
     (10.0, 32, 4, 15, {"bcr_depth": 2}),
     (10.0, 32, 4, 15, {"gs_passes": 3}),
+    (10.0, 32, 4, 15, {"serve_slots": 0}),
+    (10.0, 32, 4, 15, {"serve_slots": 257}),
     (10.0, 1, 1, 15, {}),
 ])
 def test_setup_rejects_bad_arguments(lib, k, n, strips, dirs, kw):

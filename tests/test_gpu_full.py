@@ -1,0 +1,102 @@
+"""Full-size GPU parity against stored oracle values (tests/golden, written by
+tests/golden/make_golden.py from oracle/ only).
+
+* k = 100, n = 256, 16 strips, 8 right-hand sides, FP64: the same iteration count as the
+  oracle for every right-hand side and the solution within 1e-10 relative (sampled nodes).
+* k = 200, n = 512, 16 strips, 64 right-hand sides in one batch, complex64 sweeps: tol 1e-6
+  reached within the oracle's iterations + 2, and the solution close to the oracle's
+  solution at tol 1e-10 (sampled nodes).
+* k = 400, n = 1024, 32 strips, complex64 sweeps: the same bar, when its stored values exist.
+
+Solution bar of the complex64 runs.  Flexible MPGMRES forms its residual and iterate in
+FP64 whatever precision the preconditioner runs in, so a solve stopped at relative residual
+tol has error ||x - x*|| <= ||A^-1|| ||b|| tol, the same bound as the oracle stopped at the
+same tol.  The bar is therefore three times the oracle's own distance between its
+tol-solution and its tight solution (both stored), which allows for the two residuals
+pointing in different directions.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import hh_inputs
+import paper_2408_11929_gb300 as hh
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    p = os.path.join(GOLD, f"{name}.json")
+    if not os.path.exists(p):
+        pytest.skip(f"no stored oracle values for {name}")
+    return json.load(open(p))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def stop_err(g, r):
+    """The oracle's own error from stopping at the workload tolerance (sampled nodes)."""
+    gr = g["rhs"][str(r)]
+    x = np.array(gr["x_sample_re"]) + 1j * np.array(gr["x_sample_im"])
+    t = np.array(gr["tight_x_sample_re"]) + 1j * np.array(gr["tight_x_sample_im"])
+    return np.linalg.norm(x - t) / np.linalg.norm(t)
+
+
+def sample_err(x, g, r, tight=False):
+    idx = np.array(g["sample_nodes"])
+    pre = "tight_" if tight else ""
+    ref = np.array(g["rhs"][str(r)][pre + "x_sample_re"]) + 1j * np.array(g["rhs"][str(r)][pre + "x_sample_im"])
+    return np.linalg.norm(x[idx] - ref) / np.linalg.norm(ref)
+
+
+def test_k100_fp64_eight_rhs():
+    w = hh_inputs.workload("k100_n256")
+    g = golden(w.name)
+    with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp64") as h:
+        B = np.concatenate([h.assemble_rhs(s) for s in w.sources])
+        X, res = h.solve_batch(B, w.nrhs, tol=w.tol)
+    X = X.reshape(w.nrhs, -1)
+    for r in range(w.nrhs):
+        gr = g["rhs"][str(r)]
+        assert res[r].status == hh.HH_OK
+        assert res[r].iterations == gr["iterations"], r
+        assert sample_err(X[r], g, r) < 1e-10, r
+        assert res[r].rel_res_explicit < w.tol
+
+
+def test_k200_fp32_batch_of_64():
+    w = hh_inputs.workload("k200_n512_b64")
+    g = golden(w.name)
+    torch = pytest.importorskip("torch")
+    with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32") as h:
+        B = torch.cat([torch.from_numpy(h.assemble_rhs(s)) for s in w.sources]).cuda()
+        X, res = h.solve_batch(B, w.nrhs, tol=w.tol)
+    X = X.reshape(w.nrhs, -1).cpu().numpy()
+    for r in (int(k) for k in g["rhs"]):
+        gr = g["rhs"][str(r)]
+        assert res[r].status == hh.HH_OK
+        assert res[r].iterations <= gr["iterations"] + 2, r
+        assert res[r].rel_res_explicit < 1.05 * w.tol, r
+        assert sample_err(X[r], g, r, tight=True) < 3 * stop_err(g, r), r
+    assert all(q.status == hh.HH_OK for q in res)
+
+
+def test_k400_fp32():
+    w = hh_inputs.workload("k400_n1024")
+    g = golden(w.name)
+    torch = pytest.importorskip("torch")
+    with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32") as h:
+        b = torch.from_numpy(h.assemble_rhs(w.sources[0])).cuda()
+        x, res = h.solve(b, tol=w.tol)
+    gr = g["rhs"]["0"]
+    assert res.status == hh.HH_OK
+    assert res.iterations <= gr["iterations"] + 2
+    assert res.rel_res_explicit < 1.05 * w.tol
+    assert sample_err(x.cpu().numpy(), g, 0, tight=True) < 3 * stop_err(g, 0)

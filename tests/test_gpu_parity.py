@@ -238,3 +238,49 @@ def test_single_pass_gram_schmidt_matches_oracle(dirs):
         x, res = h.solve(b, tol=1e-8)
     assert res.status == hh.HH_OK and res.iterations == ref.iterations
     assert rel(x, ref.x) < 1e-10
+
+
+def test_continuous_batching_matches_alone():
+    """Requests with mixed tolerances arrive while others are mid-solve and share two slots
+    (serve_slots = 2, five requests): each result equals the same request solved alone."""
+    import time
+    k, n, N = 25.0, 48, 4
+    srcs = hh_inputs.random_sources(5, seed=21, complex_amp=True)
+    tols = [1e-6, 1e-10, 1e-8, 1e-7, 1e-9]
+    with hh.Handle(k, n, N, serve_slots=2) as h:
+        bs = [h.assemble_rhs(s) for s in srcs]
+        alone = [h.solve(b, tol=t) for b, t in zip(bs, tols)]
+        xs = [np.zeros_like(b) for b in bs]
+        tickets = [h.submit(bs[0], xs[0], tol=tols[0])]
+        time.sleep(0.05)  # the first request is iterating when the others arrive
+        tickets += [h.submit(b, x, tol=t) for b, x, t in zip(bs[1:], xs[1:], tols[1:])]
+        done = {}
+        t0 = time.time()
+        while len(done) < len(tickets) and time.time() - t0 < 120:
+            for t in tickets:
+                if t not in done:
+                    st, res = h.poll(t)
+                    if st != hh.HH_EPENDING:
+                        done[t] = (st, res)
+            time.sleep(0.001)
+    assert len(done) == len(tickets)
+    for (xa, ra), x, t, tol in zip(alone, xs, tickets, tols):
+        st, res = done[t]
+        assert st == hh.HH_OK and res.iterations == ra.iterations
+        assert res.rel_res_explicit < tol
+        assert rel(x, xa) < 1e-10
+
+
+def test_batch_zero_and_nonzero_columns():
+    """A zero right-hand side inside a batch finishes at admission with x = 0 while the
+    other columns iterate to the oracle's iteration count."""
+    k, n, N = 20.0, 32, 4
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    ref = P.solve(b, tol=1e-8)
+    B = np.stack([np.zeros_like(b), b, np.zeros_like(b)])
+    with hh.Handle(k, n, N) as h:
+        X, res = h.solve_batch(np.ascontiguousarray(B.ravel()), 3, tol=1e-8)
+    X = X.reshape(3, -1)
+    assert res[0].iterations == 0 and res[2].iterations == 0 and np.all(X[0] == 0) and np.all(X[2] == 0)
+    assert res[1].iterations == ref.iterations and rel(X[1], ref.x) < 1e-10
