@@ -119,31 +119,47 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------- peaks / traffic
 def measured_peaks() -> dict:
+    """HBM copy bandwidth and SM clock from MEASURED_PEAKS.json (else the fallback figures),
+    plus the FP32 and FP64 ALU peaks derived from the unit counts at the maximum SM clock:
+    152 SMs x 128 FP32 FMA lanes x 2 flops per clock, and the measured FP64 FMA rate."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
-    return {"hbm_gbs": 6800.0, "src": "fallback"}
+        out = {"hbm_gbs": float(d["hbm_gbs"]), "sm_mhz": float(d.get("sm_max_mhz", 2070.0)), "src": "measured"}
+    else:
+        out = {"hbm_gbs": 6800.0, "sm_mhz": 2070.0, "src": "fallback"}
+    out["fp32_alu_tflops"] = 152 * 128 * 2 * out["sm_mhz"] * 1e6 / 1e12
+    return out
 
 
-def sweep_source_hash() -> str:
+def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sweep.cu", "common.cuh"):
+    for f in ("gemm.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2408_11929_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(workload: str):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on the
-    current sweep kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    """DRAM bytes per launch of the wide sweep GEMM step from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "line_gemm_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_hash") != sweep_source_hash():
+    if d.get("source_hash") != kernel_source_hash():
         return None
     e = d.get("workloads", {}).get(workload)
     return None if e is None else float(e["dram_bytes_per_launch"])
+
+
+def percentile(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    pos = (len(v) - 1) * q
+    lo = int(pos)
+    hi = min(lo + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (pos - lo)
 
 
 # ---------------------------------------------------------------------- oracle (CPU) baseline
@@ -226,15 +242,16 @@ def run_gpu(args, ws, rank, local):
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
         iters = []
-        for _ in range(args.steps):
+        for i in range(args.steps):
             _, res = h.solve(b, x, tol=w.tol)
+            ev[i + 1].record(stream)
             iters.append(res.iterations)
-        e1.record(stream)
         torch.cuda.synchronize()
+        step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+        e0, e1 = ev[0], ev[-1]
         if ws > 1:
             dist.barrier()
         clocks = clk.stop()
@@ -259,9 +276,12 @@ def run_gpu(args, ws, rank, local):
     out = None
     if rank == 0:
         nsw = max(1, st["sweep_launches"])
-        sweep_bytes = st["sweep_bytes"] / nsw
         sweep_ms = st["sweep_ms"] / nsw if st["sweep_ms"] > 0 else None
-        achieved = sweep_bytes / (sweep_ms / 1e3) / 1e9 if sweep_ms else None
+        ngm = max(1, st["gemm_launches"])
+        gemm_ms = st["gemm_ms"] / ngm if st["gemm_ms"] > 0 else None
+        gemm_flops = st["gemm_flops"] / ngm
+        achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms else None
+        step_total_ms = sum(step_ms)
         traffic = ncu_traffic(WORKLOAD)
         g = golden(w)
         err = None
@@ -280,11 +300,25 @@ def run_gpu(args, ws, rank, local):
             "time_to_tol_ms": tmax / args.steps * 1e3, "iterations": iters[-1], "iterations_oracle": iters_oracle,
             "status": hh.STATUS_NAMES[status], "rel_res_explicit": rel_exp, "setup_ms": setup_ms,
             "error_vs_oracle_tight": err,
-            "roofline": {"bound": "hbm", "kernel": "sweep_kernel<float,4>",
-                         "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": sweep_ms,
-                         "launches": st["sweep_launches"], "peak_src": peaks["src"] + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "roofline": {"bound": "alu", "kernel": "line_gemm_kernel<float> (+ split_reduce_kernel): wide sweep GEMM step",
+                         "achieved": achieved, "peak": peaks["fp32_alu_tflops"], "unit": "TFLOP/s",
+                         "frac": (achieved / peaks["fp32_alu_tflops"]) if achieved else None, "traffic": traffic,
+                         "algorithmic_flops_per_launch": gemm_flops, "avg_launch_ms": gemm_ms,
+                         "launches": st["gemm_launches"],
+                         "share_of_step": st["gemm_ms"] / step_total_ms if step_total_ms > 0 else None,
+                         "peak_src": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x %.0f MHz (max SM clock, %s)"
+                                     % (peaks["sm_mhz"], peaks["src"] + " MEASURED_PEAKS.json" if peaks["src"] == "measured" else "fallback")},
+            "phase_roofline": {
+                "sweep": {"ms_per_launch": sweep_ms, "bytes_per_launch": st["sweep_bytes"] / nsw,
+                          "gbs": (st["sweep_bytes"] / nsw) / (sweep_ms / 1e3) / 1e9 if sweep_ms else None,
+                          "hbm_frac": ((st["sweep_bytes"] / nsw) / (sweep_ms / 1e3) / 1e9 / peaks["hbm_gbs"]) if sweep_ms else None},
+                "spmv": {"gbs": st["spmv_bytes"] / (st["spmv_ms"] / 1e3) / 1e9 if st["spmv_ms"] > 0 else None,
+                         "hbm_frac": (st["spmv_bytes"] / (st["spmv_ms"] / 1e3) / 1e9 / peaks["hbm_gbs"]) if st["spmv_ms"] > 0 else None},
+                "gram_schmidt": {"gbs": st["gs_bytes"] / (st["gs_ms"] / 1e3) / 1e9 if st["gs_ms"] > 0 else None,
+                                 "hbm_frac": (st["gs_bytes"] / (st["gs_ms"] / 1e3) / 1e9 / peaks["hbm_gbs"]) if st["gs_ms"] > 0 else None},
+                "hbm_peak_gbs": peaks["hbm_gbs"]},
+            "latency_ms": {"p50": percentile(step_ms, 0.5), "p99": percentile(step_ms, 0.99),
+                           "samples": len(step_ms), "kind": "closed loop, one solve at a time"},
             "e2e": {"value": e2e_units / e2e_max, "unit": "solves/s", "h2d_bytes_per_step": int(b_host.nbytes),
                     "d2h_bytes_per_step": int(xh.nbytes)},
             "gpu_launches": int(st["kernel_launches"]),
@@ -351,7 +385,12 @@ def run_sweep_only(args):
                       "sweep_ms": ms, "steps_per_launch": st["sweep_steps"],
                       "us_per_step": ms * 1e3 / st["sweep_steps"],
                       "GBps": st["sweep_bytes"] / max(1, st["sweep_launches"]) / (ms / 1e3) / 1e9,
-                      "total_ms": e0.elapsed_time(e1)}), flush=True)
+                      "total_ms": e0.elapsed_time(e1),
+                      "gemm_launches_per_sweep": st["gemm_launches"] / max(1, st["sweep_launches"]),
+                      "gemm_us_per_launch": st["gemm_ms"] * 1e3 / max(1, st["gemm_launches"]),
+                      "gemm_tflops": (st["gemm_flops"] / (st["gemm_ms"] / 1e3) / 1e12) if st["gemm_ms"] > 0 else None,
+                      "gemm_share_of_sweep": st["gemm_ms"] / st["sweep_ms"] if st["sweep_ms"] > 0 else None}),
+          flush=True)
 
 
 def main():

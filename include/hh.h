@@ -98,6 +98,10 @@ typedef struct {
   int factor_blocks;       /* distinct m x m blocks stored (R + 1) */
   int m, ldf, columns;     /* nodes per line, padded leading dimension, sweep columns of last solve */
   int64_t sweep_steps;     /* dependent block steps of one sweep launch */
+  /* the wide GEMM steps of the sweeps, timed one by one in every 4th sweep when
+     opts.profile is set: sampled launches, their device time (ms) and their complex
+     multiply-add flops (8 m^2 per column) */
+  int64_t gemm_launches;   double gemm_ms;   double gemm_flops;
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

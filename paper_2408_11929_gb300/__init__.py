@@ -48,7 +48,8 @@ class hh_stats(ctypes.Structure):
                 ("gs_launches", ctypes.c_int64), ("gs_ms", ctypes.c_double), ("gs_bytes", ctypes.c_double),
                 ("setup_launches", ctypes.c_int64), ("setup_ms", ctypes.c_double), ("setup_flops", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("factor_bytes", ctypes.c_int64), ("factor_blocks", ctypes.c_int),
-                ("m", ctypes.c_int), ("ldf", ctypes.c_int), ("columns", ctypes.c_int), ("sweep_steps", ctypes.c_int64)]
+                ("m", ctypes.c_int), ("ldf", ctypes.c_int), ("columns", ctypes.c_int), ("sweep_steps", ctypes.c_int64),
+                ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

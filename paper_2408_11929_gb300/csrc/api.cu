@@ -520,6 +520,9 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->ldf = E.ldf;
   st->columns = E.last_columns;
   st->sweep_steps = (int64_t)(E.opts.single_sweep ? E.steps_single.size() : E.steps_double.size());
+  st->gemm_launches = E.launches[Engine::K_GEMM];
+  st->gemm_ms = E.ms[Engine::K_GEMM];
+  st->gemm_flops = E.flops[Engine::K_GEMM];
   return HH_OK;
 }
 

@@ -311,6 +311,15 @@ int Engine::ensure_sweep_ws(int C) {
   return HH_OK;
 }
 
+// Algorithmic bytes of one step: it reads its m x m block and its input lines once and
+// writes its output (and accumulated) lines once.
+static double step_bytes(const Engine& E, const SweepStep& s, int C) {
+  const double e = (double)E.sweep_elem();
+  const double line = (double)E.m * s.ns * C * e;
+  return (double)E.m * E.m * e + line * ((s.base != SB_NONE) + (s.src != SB_NONE) + 1 + 2 * (s.acc != SB_NONE) +
+                                         (s.out_mode != OUT_SET));
+}
+
 template <typename R>
 static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, int C, bool single, void* partial_buf,
                                   size_t partial_bytes) {
@@ -328,6 +337,9 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
   cudaFuncSetAttribute((const void*)gemm_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem);
   cudaFuncSetAttribute((const void*)line_gemv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)std::min<size_t>((size_t)E.m * 8 * sizeof(T), gemv_cap));
+  // the wide GEMM steps are timed one by one in every 4th sweep (events between launches
+  // cost a little, so they are sampled)
+  const bool tick_gemm = E.opts.profile && (E.sweep_calls++ % 4 == 0);
   for (const SweepStep& s : steps) {
     LineOperand<T> op{};
     op.base = buf(s.base); op.base_j = s.base_j;
@@ -349,12 +361,14 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
       while (nsplit > 1 && (size_t)nsplit * E.m * ncols * sizeof(T) > partial_bytes) --nsplit;
       const int kchunk = ((E.m + nsplit - 1) / nsplit + BK - 1) / BK * BK;
       T* partial = nsplit > 1 ? reinterpret_cast<T*>(partial_buf) : nullptr;
+      if (tick_gemm) E.tick_begin(Engine::K_GEMM);
       gemm_fn<<<dim3(gx, gy, nsplit), 256, gemm_smem, E.stream>>>(A, E.ldf, E.m, op, E.coef, kchunk, partial);
       E.count_launch();
       if (nsplit > 1) {
         split_reduce_kernel<R><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(partial, nsplit, E.m, op);
         E.count_launch();
       }
+      if (tick_gemm) E.tick_end(Engine::K_GEMM, step_bytes(E, s, C), 8.0 * E.m * E.m * (double)ncols);
     }
   }
   return cudaGetLastError();
@@ -368,16 +382,9 @@ double Engine::sweep_flops(int C, bool single) const {
 }
 
 double Engine::sweep_bytes(int C, bool single) const {
-  // algorithmic bytes: each step reads one m x m block and its input lines once and writes its
-  // output (and accumulated) lines once; pack / unpack traffic excluded
   const std::vector<SweepStep>& steps = single ? steps_single : steps_double;
-  const double e = (double)sweep_elem();
   double b = 0;
-  for (const SweepStep& s : steps) {
-    const double line = (double)m * s.ns * C * e;
-    b += (double)m * m * e + line * ((s.base != SB_NONE) + (s.src != SB_NONE) + 1 + 2 * (s.acc != SB_NONE) +
-                                     (s.out_mode != OUT_SET));
-  }
+  for (const SweepStep& s : steps) b += step_bytes(*this, s, C);
   return b;
 }
 
