@@ -367,13 +367,21 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
     if (threadIdx.x == 0)
       for (int q = 0; q < TT; ++q) part[(size_t)blockIdx.x * TT + q] = make_double2(v[2 * q], v[2 * q + 1]);
     if (!grid_sync(bar, target, err, budget)) return false;
-    if (threadIdx.x == 0) {
+    // every CTA sums the GQ partials with all its threads, in one fixed order, so all CTAs
+    // hold bit-identical sums
+    double w[2 * TT];
+#pragma unroll
+    for (int q = 0; q < 2 * TT; ++q) w[q] = 0;
+    for (int b = threadIdx.x; b < S.GQ; b += blockDim.x)
+#pragma unroll
       for (int q = 0; q < TT; ++q) {
-        double2 s = make_double2(0, 0);
-        for (int b = 0; b < S.GQ; ++b) s = cadd(s, __ldcg(part + (size_t)b * TT + q));
-        red_out[q] = s;
+        const double2 p = __ldcg(part + (size_t)b * TT + q);
+        w[2 * q] += p.x;
+        w[2 * q + 1] += p.y;
       }
-    }
+    block_sum<2 * TT>(w, sh);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < TT; ++q) red_out[q] = make_double2(w[2 * q], w[2 * q + 1]);
     __syncthreads();
     parity ^= 1;
     return true;
@@ -714,7 +722,7 @@ struct SlotSolver::Impl {
     K.GX = std::max(1, std::min(E.num_sms * 2 / S + 1, (int)((D + 255) / 256)));
     K.GX = std::min(K.GX, E.num_sms * 2);
     const int cap = E.num_sms * E.coop_per_sm;
-    K.GQ = std::max(1, std::min(cap / S, E.num_sms));
+    K.GQ = std::max(1, cap / S);
     if (K.GQ * S > cap) return (set_error("too many slots for one cooperative QR launch"), HH_EINVAL);
     K.beta = dev<double>(S); K.done = dev<int>(S); K.status = dev<int>(S);
     K.nV = dev<int>(S); K.nZ = dev<int>(S); K.iters = dev<int>(S); K.nacc = dev<int>(S);

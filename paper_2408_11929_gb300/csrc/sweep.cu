@@ -191,9 +191,10 @@ __global__ void unpack_tab_kernel(const typename Cx<R>::T* __restrict__ X, int C
 }
 
 // Narrow step (at most 8 columns: the interface chains and the last strip's extra line
-// of a single right-hand side).  The CTA forms x (m x ncols) in shared memory, then one warp
-// per output row walks the row of A with two complex entries per lane per load and sums
-// across the warp with shuffles.
+// of a single right-hand side).  The CTA forms x (m x ncols) in shared memory, column-major
+// so that the 32 lanes of a warp read 32 consecutive node indices of one column without bank
+// conflicts; then one warp per output row walks the row of A (consecutive entries per lane,
+// eight loads in flight) and sums across the warp with shuffles.
 template <typename R>
 __global__ void __launch_bounds__(256) line_gemv_kernel(const typename Cx<R>::T* __restrict__ A, int lda, int m,
                                                         LineOperand<typename Cx<R>::T> op, Coef cf) {
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(256) line_gemv_kernel(const typename Cx<R>::T*
         }
         v = op.neg ? csub(v, cp) : cadd(v, cp);
       }
-      xs[idx] = v;
+      xs[(idx % ncols) * m + idx / ncols] = v;
     }
   }
   __syncthreads();
@@ -252,25 +253,21 @@ __global__ void __launch_bounds__(256) line_gemv_kernel(const typename Cx<R>::T*
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = mk<T>(0, 0);
   const T* Ar = A + (size_t)row * lda;
-  // lanes take pairs of consecutive node indices; four pairs in flight per lane
-  for (int k0 = 2 * lane; k0 < m; k0 += 64 * 4) {
-    T a[4][2];
+  constexpr int U = 8;  // loads in flight per lane
+  for (int k0 = lane; k0 < m; k0 += 32 * U) {
+    T a[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int k = k0 + 64 * u;
-      a[u][0] = k < m ? __ldg(Ar + k) : mk<T>(0, 0);
-      a[u][1] = k + 1 < m ? __ldg(Ar + k + 1) : mk<T>(0, 0);
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + 32 * u;
+      a[u] = k < m ? __ldg(Ar + k) : mk<T>(0, 0);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int k = k0 + 64 * u;
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + 32 * u;
+      if (k < m) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (k + h < m) {
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (c < ncols) cfma(acc[c], a[u][h], xs[(k + h) * ncols + c]);
-        }
+        for (int c = 0; c < 8; ++c)
+          if (c < ncols) cfma(acc[c], a[u], xs[c * m + k]);
       }
     }
   }
