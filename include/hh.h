@@ -68,14 +68,18 @@ typedef struct {
   int bcr_depth;          /* reserved: 0 = block Thomas strip solves (the only value accepted) */
   int64_t timeout_cycles; /* SM clock budget of every device-side wait (default 4e9) */
   void* stream;           /* cudaStream_t to run on, or NULL for the handle's own stream */
-  int use_graph;          /* 1 (default): the Arnoldi step is replayed as a CUDA graph */
+  int use_graph;          /* 1 (default): each sweep (its 200-odd dependent launches) is captured
+                             once per array set and column count and replayed as a CUDA graph */
   int profile;            /* 1: time every kernel class with CUDA events (hh_get_stats) */
   int gs_passes;          /* Gram-Schmidt passes against the basis and within the new block:
                              2 (default, CGS2) or 1 (the single pass whose inner products
                              Section 3 counts, (k - 1/2) t^2 + 3t/2 at iteration k) */
   int serve_slots;        /* slots of the hh_submit request loop: requests solved together,
                              each joining at an iteration boundary (default 8, 1..256) */
-  int reserved[4];
+  int tensor_cores;       /* HH_PREC_FP32 only.  1 (default): the wide sweep steps run on the
+                             tensor cores (tcgen05, TF32 operands split hi + lo, three products,
+                             FP32 accumulation); 0: FP32 FMA on the CUDA cores */
+  int reserved[3];
 } hh_opts;
 
 typedef struct {
@@ -98,10 +102,11 @@ typedef struct {
   int factor_blocks;       /* distinct m x m blocks stored (R + 1) */
   int m, ldf, columns;     /* nodes per line, padded leading dimension, sweep columns of last solve */
   int64_t sweep_steps;     /* dependent block steps of one sweep launch */
-  /* the wide GEMM steps of the sweeps, timed one by one in every 4th sweep when
+  /* the wide GEMM steps of the sweeps, timed one by one in every 8th sweep when
      opts.profile is set: sampled launches, their device time (ms) and their complex
      multiply-add flops (8 m^2 per column) */
   int64_t gemm_launches;   double gemm_ms;   double gemm_flops;
+  int tensor_cores;        /* 1 when the wide sweep steps run on the tensor cores */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -30,7 +30,7 @@ class hh_opts(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("deflate_eta", ctypes.c_double), ("bcr_depth", ctypes.c_int),
                 ("timeout_cycles", ctypes.c_int64), ("stream", ctypes.c_void_p), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("gs_passes", ctypes.c_int), ("serve_slots", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("tensor_cores", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class hh_result(ctypes.Structure):
@@ -49,7 +49,8 @@ class hh_stats(ctypes.Structure):
                 ("setup_launches", ctypes.c_int64), ("setup_ms", ctypes.c_double), ("setup_flops", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("factor_bytes", ctypes.c_int64), ("factor_blocks", ctypes.c_int),
                 ("m", ctypes.c_int), ("ldf", ctypes.c_int), ("columns", ctypes.c_int), ("sweep_steps", ctypes.c_int64),
-                ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double)]
+                ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double),
+                ("tensor_cores", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

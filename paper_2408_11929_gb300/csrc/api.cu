@@ -136,7 +136,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   k = k_; n = n_; N = strips; m = n + 1; R = n / N;
   precision = opts.precision;
   ldf = (m + 3) & ~3;
-  coef.k = k; coef.h = 1.0 / n; coef.n = n;
+  coef.init(k, n);
   static const int bitcode[4] = {DC_LR, DC_RL, DC_BT, DC_TB};
   dir_codes.clear();
   for (int b = 0; b < 4; ++b)
@@ -162,7 +162,10 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   const size_t fbytes = (size_t)factor_blocks() * m * ldf * sweep_elem();
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  if (fbytes + (64ull << 20) > free_b) return (set_error("strip factors do not fit in free device memory"), HH_ENOMEM);
+  // the tensor-core form keeps two more copies of the complex64 factor store (hi and lo)
+  const size_t fcopies = (precision == HH_PREC_FP32 && opts.tensor_cores) ? 3 : 1;
+  if (fcopies * fbytes + (64ull << 20) > free_b)
+    return (set_error("strip factors do not fit in free device memory"), HH_ENOMEM);
   if (dmalloc(&factors, fbytes) || dmalloc((void**)&bar, 64) || dmalloc((void**)&err, 64)) return HH_ENOMEM;
   cudaMemsetAsync(bar, 0, 64, stream);
   cudaMemsetAsync(err, 0, 64, stream);
@@ -175,6 +178,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   cudaEventCreate(&b);
   cudaEventRecord(a, stream);
   int rc = factor();
+  if (rc == HH_OK) rc = prepare_tensor_cores();
   cudaEventRecord(b, stream);
   cudaEventSynchronize(b);
   float t_ms = 0;
@@ -196,10 +200,13 @@ Engine::~Engine() {
   if (stream) cudaStreamSynchronize(stream);
   delete batch_solver;
   batch_solver = nullptr;
+  for (auto& g : sweep_graphs) cudaGraphExecDestroy(g.exec);
+  sweep_graphs.clear();
   collect_ticks();
   for (auto ev : event_pool) cudaEventDestroy(ev);
   dfree(factors); dfree(bar); dfree(err);
   dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial);
+  dfree(factors_hi); dfree(factors_lo);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
@@ -388,6 +395,7 @@ void hh_default_opts(hh_opts* o) {
   o->profile = 0;
   o->gs_passes = 2;
   o->serve_slots = 8;
+  o->tensor_cores = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {
@@ -523,6 +531,7 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->gemm_launches = E.launches[Engine::K_GEMM];
   st->gemm_ms = E.ms[Engine::K_GEMM];
   st->gemm_flops = E.flops[Engine::K_GEMM];
+  st->tensor_cores = E.tc_ready ? 1 : 0;
   return HH_OK;
 }
 

@@ -92,6 +92,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+// one plain arrival (release at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile(
@@ -126,6 +130,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* e
 }
 // orders this thread's generic-proxy accesses with its later async-proxy (TMA) accesses
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// the same for shared memory only (does not wait for this thread's global loads)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 // ---------------------------------------------------------------- P1 stencil coefficients
 // Matrix A = K - k^2 M - i k M_Gamma on the (n+1)^2 grid, cells cut along SW-NE diagonals.
@@ -140,36 +148,49 @@ enum LineType { LINE_BOT = 0, LINE_INT = 1, LINE_TOP = 2 };
 struct Coef {
   double k, h;
   int n;
-  // coupling of node (i, l) to (i, l-1): vertical edge shared by up to two triangles,
-  // plus the boundary edge mass on the sides x = 0, x = 1
-  __host__ __device__ double2 vert(int i) const {
-    int cnt = (i < n) + (i >= 1);
-    double re = cnt * (-0.5 - k * k * h * h / 24.0);
-    double im = (i == 0 || i == n) ? -k * h / 6.0 : 0.0;
-    return make_double2(re, im);
+  // The distinct coefficient values, filled once on the host by init(): kernels only select
+  // from these tables (GB300's FP64 divide is far too slow to evaluate per thread).
+  double2 vert_t[2];      // [edge node i = 0 or n, interior node]
+  double diag_t;
+  double2 horiz_t[3];     // by line type
+  double2 centre_t[3][3]; // [line type][node class: i = 0, interior, i = n]
+
+  __host__ void init(double k_, int n_) {
+    k = k_;
+    n = n_;
+    h = 1.0 / n_;
+    const double kkh = k * k * h * h, kh = k * h;
+    // coupling of node (i, l) to (i, l-1): vertical edge shared by up to two triangles,
+    // plus the boundary edge mass on the sides x = 0, x = 1
+    vert_t[0] = make_double2(1 * (-0.5 - kkh / 24.0), -kh / 6.0);
+    vert_t[1] = make_double2(2 * (-0.5 - kkh / 24.0), 0.0);
+    // coupling of node (i, l) to (i-1, l-1): the diagonal of one cell (hypotenuse of both halves)
+    diag_t = -kkh / 12.0;
+    for (int type = 0; type < 3; ++type) {
+      // coupling along a line between (i, l) and (i+1, l)
+      const int cnt = (type != LINE_TOP) + (type != LINE_BOT);
+      horiz_t[type] = make_double2(cnt * (-0.5 - kkh / 24.0), (type != LINE_INT) ? -kh / 6.0 : 0.0);
+      // diagonal entry of node i on a line of the given type
+      for (int cls = 0; cls < 3; ++cls) {
+        const bool top = type == LINE_TOP, bot = type == LINE_BOT;
+        const bool lo_end = cls == 0, hi_end = cls == 2;  // i = 0, i = n
+        const bool lt_n = !hi_end, ge_1 = !lo_end;
+        int kc = 0, ntri = 0, nbe = 0;
+        if (!top && lt_n) { kc += 1; ntri += 2; }  // cell NE of the node: two acute corners
+        if (!top && ge_1) { kc += 1; ntri += 1; }  // cell NW: one right-angle corner
+        if (!bot && ge_1) { kc += 1; ntri += 2; }  // cell SW: two acute corners
+        if (!bot && lt_n) { kc += 1; ntri += 1; }  // cell SE: one right-angle corner
+        if (bot || top) nbe += ge_1 + lt_n;
+        if (lo_end || hi_end) nbe += (!bot) + (!top);
+        centre_t[type][cls] = make_double2(kc - kkh / 12.0 * ntri, -kh / 3.0 * nbe);
+      }
+    }
   }
-  // coupling of node (i, l) to (i-1, l-1): the diagonal of one cell (hypotenuse of both halves)
-  __host__ __device__ double diag() const { return -k * k * h * h / 12.0; }
-  // coupling along a line between (i, l) and (i+1, l)
-  __host__ __device__ double2 horiz(int type) const {
-    int cnt = (type != LINE_TOP) + (type != LINE_BOT);
-    double re = cnt * (-0.5 - k * k * h * h / 24.0);
-    double im = (type != LINE_INT) ? -k * h / 6.0 : 0.0;
-    return make_double2(re, im);
-  }
-  // diagonal entry of node i on a line of the given type
+  __host__ __device__ double2 vert(int i) const { return vert_t[(i == 0 || i == n) ? 0 : 1]; }
+  __host__ __device__ double diag() const { return diag_t; }
+  __host__ __device__ double2 horiz(int type) const { return horiz_t[type]; }
   __host__ __device__ double2 centre(int i, int type) const {
-    bool top = type == LINE_TOP, bot = type == LINE_BOT;
-    int kc = 0, ntri = 0, nbe = 0;
-    if (!top && i < n) { kc += 1; ntri += 2; }   // cell NE of the node: two acute corners
-    if (!top && i >= 1) { kc += 1; ntri += 1; }  // cell NW: one right-angle corner
-    if (!bot && i >= 1) { kc += 1; ntri += 2; }  // cell SW: two acute corners
-    if (!bot && i < n) { kc += 1; ntri += 1; }   // cell SE: one right-angle corner
-    if (bot || top) nbe += (i >= 1) + (i < n);
-    if (i == 0 || i == n) nbe += (!bot) + (!top);
-    double re = kc - k * k * h * h / 12.0 * ntri;
-    double im = -k * h / 3.0 * nbe;
-    return make_double2(re, im);
+    return centre_t[type][i == 0 ? 0 : (i == n ? 2 : 1)];
   }
 };
 

@@ -1,6 +1,7 @@
 // Host-side engine: one per hh_handle.  Owns the device, stream, strip factors and the
 // Krylov slots; the kernels live in setup.cu, sweep.cu and krylov.cu.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -56,6 +57,33 @@ class Engine {
 
   // device buffers
   void* factors = nullptr;  // R+3 blocks of m x ldf complex: F_0..F_R, G, K (setup.cu)
+  // tensor-core operands (complex64 only): the factor store split into TF32 hi and lo
+  // parts, and one 3-D tensor map over each (floats along a row, rows, blocks)
+  void* factors_hi = nullptr;
+  void* factors_lo = nullptr;
+  CUtensorMap tmap_hi{}, tmap_lo{};
+  bool tc_ready = false;
+  int prepare_tensor_cores();  // sweep.cu
+  // 3-D views of a sweep array (floats of a node row, node rows, lines) with the raw-row
+  // boxes of the tensor-core step (16 and 18 rows), cached per (array, columns per strip)
+  struct LineMaps {
+    const void* ptr = nullptr;
+    int C = -1;
+    CUtensorMap base{}, src{};
+  };
+  LineMaps line_maps[6];
+  int line_maps_next = 0;
+  void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
+  const LineMaps* line_maps_for(const void* buf, int C);
+  // sweeps replayed as CUDA graphs (opts.use_graph), one per (arrays, columns, kind)
+  struct SweepGraph {
+    const void *rin, *v, *w, *partial;
+    int C;
+    bool single;
+    cudaGraphExec_t exec;
+    int64_t kernels;  // launches per replay
+  };
+  std::vector<SweepGraph> sweep_graphs;
   unsigned* bar = nullptr;  // grid barrier counter
   int* err = nullptr;       // device error word
   std::vector<SweepStep> steps_double, steps_single;  // sweep schedules
@@ -114,8 +142,10 @@ class Engine {
 
   // sweep on packed columns (strip-interleaved layout, C columns): Rin -> V, W = corrections
   int run_sweep(const void* Rin, void* V, void* W, int C, bool single);
+  // partial: split-K slices (or nullptr); allow_graph = false keeps the sweep eager (graph
+  // instantiation may allocate, which the no-allocation entry point must not)
   int run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool single, void* partial,
-                        size_t partial_bytes);  // partial: split-K slices (or nullptr)
+                        size_t partial_bytes, bool allow_graph = true);
   int apply_preconditioner_noalloc(int dcode, int ncols, const double2* r, double2* z, bool single);
   size_t sweep_elem() const { return precision == HH_PREC_FP32 ? 8 : 16; }
   size_t sweep_ws_bytes(int C) const;          // bytes of one packed sweep array

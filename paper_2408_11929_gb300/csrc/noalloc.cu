@@ -107,7 +107,7 @@ int Engine::apply_preconditioner_noalloc(int dcode, int ncols, const double2* r,
   int4 codes = make_int4(dcode, dcode, dcode, dcode);
   launch_pack(*this, tab, scale, ncols, 1, codes, rin);
   const size_t part_bytes = kNoAllocScratchBytes > off_part ? kNoAllocScratchBytes - off_part : 0;
-  rc = run_sweep_untimed(rin, v, w, ncols, single, part_bytes ? s + off_part : nullptr, part_bytes);
+  rc = run_sweep_untimed(rin, v, w, ncols, single, part_bytes ? s + off_part : nullptr, part_bytes, false);
   if (rc == HH_OK) launch_unpack(*this, v, ncols, 1, codes, z, D);
   cudaError_t e = cudaStreamSynchronize(stream);
   if (rc) return rc;

@@ -32,9 +32,15 @@
 #include <cstdio>
 #include <vector>
 
+#include <cudaTypedefs.h>
+#include <cstring>
+#include <string>
+#include <type_traits>
+
 #include "common.cuh"
 #include "engine.h"
 #include "gemm.cuh"
+#include "tc_gemm.cuh"
 
 namespace hh {
 
@@ -319,7 +325,7 @@ static double step_bytes(const Engine& E, const SweepStep& s, int C) {
 
 template <typename R>
 static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, int C, bool single, void* partial_buf,
-                                  size_t partial_bytes) {
+                                  size_t partial_bytes, bool allow_tick) {
   using T = typename Cx<R>::T;
   const std::vector<SweepStep>& steps = single ? E.steps_single : E.steps_double;
   const T* Fb = reinterpret_cast<const T*>(E.factors);
@@ -332,11 +338,13 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
   constexpr size_t gemm_smem = line_gemm_smem<R, BM, BN, BK, STG>();
   auto gemm_fn = line_gemm_kernel<R, BM, BN, BK, 4, 4, STG>;
   cudaFuncSetAttribute((const void*)gemm_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem);
+  if (E.tc_ready)
+    cudaFuncSetAttribute((const void*)tc_line_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc::SMEM);
   cudaFuncSetAttribute((const void*)line_gemv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)std::min<size_t>((size_t)E.m * 8 * sizeof(T), gemv_cap));
-  // the wide GEMM steps are timed one by one in every 4th sweep (events between launches
-  // cost a little, so they are sampled)
-  const bool tick_gemm = E.opts.profile && (E.sweep_calls++ % 4 == 0);
+  // allow_tick: time the wide GEMM steps one by one (a sampled, eager sweep)
+  const bool tick_gemm = allow_tick && E.opts.profile;
   for (const SweepStep& s : steps) {
     LineOperand<T> op{};
     op.base = buf(s.base); op.base_j = s.base_j;
@@ -350,6 +358,29 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
       line_gemv_kernel<R><<<(E.m + 7) / 8, 256, (size_t)E.m * ncols * sizeof(T), E.stream>>>(A, E.ldf, E.m, op,
                                                                                           E.coef);
       E.count_launch();
+    } else if (std::is_same<R, float>::value && E.tc_ready && C % 2 == 0) {
+      // tensor-core step: 128 rows x 64 complex columns per CTA, K split to fill the SMs
+      const int gx = (E.m + tc::BM - 1) / tc::BM, gy = (ncols + tc::BNC - 1) / tc::BNC;
+      int nsplit = std::max(1, std::min(8, (E.num_sms - 4 + gx * gy - 1) / (gx * gy)));
+      while (nsplit > 1 && (size_t)nsplit * E.m * ncols * sizeof(T) > partial_bytes) --nsplit;
+      const int kchunk = ((E.m + nsplit - 1) / nsplit + tc::BKC - 1) / tc::BKC * tc::BKC;
+      nsplit = (E.m + kchunk - 1) / kchunk;  // no empty split
+      float2* partial = nsplit > 1 ? reinterpret_cast<float2*>(partial_buf) : nullptr;
+      LineOperand<float2> opf;
+      std::memcpy(&opf, &op, sizeof(opf));
+      const Engine::LineMaps* mb = E.line_maps_for(op.base ? op.base : Rin, C);
+      const Engine::LineMaps* ms = E.line_maps_for(op.src ? op.src : Rin, C);
+      if (!mb || !ms) return cudaErrorInvalidValue;
+      if (tick_gemm) E.tick_begin(Engine::K_GEMM);
+      tc_line_gemm_kernel<<<dim3(gx, gy, nsplit), tc::THREADS, tc::SMEM, E.stream>>>(
+          E.tmap_hi, E.tmap_lo, mb->base, ms->src, s.f, E.m, opf, E.coef, kchunk, partial, E.err,
+          E.opts.timeout_cycles);
+      E.count_launch();
+      if (nsplit > 1) {
+        split_reduce_kernel<float><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(partial, nsplit, E.m, opf);
+        E.count_launch();
+      }
+      if (tick_gemm) E.tick_end(Engine::K_GEMM, step_bytes(E, s, C), 8.0 * E.m * E.m * (double)ncols);
     } else {
       const int gx = (E.m + BM - 1) / BM, gy = (ncols + BN - 1) / BN;
       // split K until about two CTAs per SM are busy (each slice at least two K tiles)
@@ -394,11 +425,50 @@ int Engine::run_sweep(const void* Rin, void* V, void* W, int C, bool single) {
 }
 
 int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool single, void* partial,
-                              size_t partial_bytes) {
-  cudaError_t ce = precision == HH_PREC_FP32
-                       ? launch_steps_t<float>(*this, Rin, V, W, C, single, partial, partial_bytes)
-                       : launch_steps_t<double>(*this, Rin, V, W, C, single, partial, partial_bytes);
-  if (ce != cudaSuccess) { set_cuda_error(ce, "sweep launch"); return HH_ECUDA; }
+                              size_t partial_bytes, bool allow_graph) {
+  // Every 8th sweep of a profiled handle times its GEMM steps one by one and so runs
+  // eagerly; all other sweeps replay a captured graph of their launches.
+  const bool sampled = opts.profile && (sweep_calls++ % 8 == 0);
+  auto launch = [&](bool tick) {
+    return precision == HH_PREC_FP32
+               ? launch_steps_t<float>(*this, Rin, V, W, C, single, partial, partial_bytes, tick)
+               : launch_steps_t<double>(*this, Rin, V, W, C, single, partial, partial_bytes, tick);
+  };
+  if (!opts.use_graph || !allow_graph || sampled) {
+    cudaError_t ce = launch(sampled);
+    if (ce != cudaSuccess) { set_cuda_error(ce, "sweep launch"); return HH_ECUDA; }
+    return HH_OK;
+  }
+  cudaGraphExec_t exec = nullptr;
+  int64_t per_replay = 0;
+  for (const SweepGraph& g : sweep_graphs)
+    if (g.rin == Rin && g.v == V && g.w == W && g.partial == partial && g.C == C && g.single == single) {
+      exec = g.exec;
+      per_replay = g.kernels;
+    }
+  if (!exec) {
+    cudaGraph_t graph = nullptr;
+    const int64_t before = kernel_launches;
+    cudaError_t ce = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      const cudaError_t le = launch(false);
+      ce = cudaStreamEndCapture(stream, &graph);
+      if (ce == cudaSuccess) ce = le;
+    }
+    per_replay = kernel_launches - before;
+    kernel_launches = before;  // counted at every replay instead
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      set_cuda_error(ce, "sweep graph capture");
+      return HH_ECUDA;
+    }
+    sweep_graphs.push_back(SweepGraph{Rin, V, W, partial, C, single, exec, per_replay});
+  }
+  cudaError_t ce = cudaGraphLaunch(exec, stream);
+  if (ce != cudaSuccess) { set_cuda_error(ce, "sweep graph launch"); return HH_ECUDA; }
+  count_launch((int)per_replay);
   return HH_OK;
 }
 
@@ -430,6 +500,81 @@ void launch_unpack_tab(Engine& E, const void* X, int C, int t, int4 codes, doubl
         reinterpret_cast<const double2*>(X), C, t, codes, E.n, E.N, E.R, dstcol);
   E.count_launch();
 }
+// hi = F rounded to TF32, lo = F - hi, elementwise over the whole complex64 factor store
+__global__ void tf32_split_kernel(const float* __restrict__ F, float* __restrict__ hi, float* __restrict__ lo,
+                                  size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    float h, l;
+    tc::split_tf32(F[i], h, l);
+    hi[i] = h;
+    lo[i] = l;
+  }
+}
+
+int Engine::prepare_tensor_cores() {
+  if (precision != HH_PREC_FP32 || !opts.tensor_cores) return HH_OK;
+  const size_t nfloat = (size_t)factor_blocks() * m * ldf * 2;
+  if (dmalloc(&factors_hi, nfloat * sizeof(float)) || dmalloc(&factors_lo, nfloat * sizeof(float))) return HH_ENOMEM;
+  tf32_split_kernel<<<grid_for(nfloat), 256, 0, stream>>>(reinterpret_cast<const float*>(factors),
+                                                         reinterpret_cast<float*>(factors_hi),
+                                                         reinterpret_cast<float*>(factors_lo), nfloat);
+  count_launch();
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return HH_ECUDA;
+  }
+  encode_fn = fn;
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  // rows of 2m floats (interleaved complex), m rows per block, factor_blocks() blocks
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * m, (cuuint64_t)m, (cuuint64_t)factor_blocks()};
+  const cuuint64_t strides[2] = {(cuuint64_t)ldf * 2 * sizeof(float), (cuuint64_t)m * ldf * 2 * sizeof(float)};
+  const cuuint32_t box[3] = {32, (cuuint32_t)tc::BM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int h = 0; h < 2; ++h) {
+    CUresult r = encode(h ? &tmap_lo : &tmap_hi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h ? factors_lo : factors_hi, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+      return HH_ECUDA;
+    }
+  }
+  tc_ready = true;
+  return HH_OK;
+}
+
+const Engine::LineMaps* Engine::line_maps_for(const void* buf, int C) {
+  for (const LineMaps& lm : line_maps)
+    if (lm.ptr == buf && lm.C == C) return &lm;
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(encode_fn);
+  if (!encode || C % 2) return nullptr;
+  LineMaps& lm = line_maps[line_maps_next];
+  line_maps_next = (line_maps_next + 1) % 6;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * N * C, (cuuint64_t)m, (cuuint64_t)(R + 1)};
+  const cuuint64_t strides[2] = {(cuuint64_t)2 * N * C * sizeof(float), (cuuint64_t)m * 2 * N * C * sizeof(float)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint32_t box_b[3] = {(cuuint32_t)(2 * tc::BNC), (cuuint32_t)tc::RAW_BASE_ROWS, 1};
+  const cuuint32_t box_s[3] = {(cuuint32_t)(2 * tc::BNC), (cuuint32_t)tc::RAW_SRC_ROWS, 1};
+  void* p = const_cast<void*>(buf);
+  if (encode(&lm.base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p, dims, strides, box_b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      encode(&lm.src, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p, dims, strides, box_s, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    lm.ptr = nullptr;
+    set_error("cuTensorMapEncodeTiled failed for a sweep array");
+    return nullptr;
+  }
+  lm.ptr = buf;
+  lm.C = C;
+  return &lm;
+}
+
 void launch_unpack(Engine& E, const void* X, int C, int t, int4 codes, double2* dst, size_t stride) {
   if (E.precision == HH_PREC_FP32) launch_unpack_t<float>(E, X, C, t, codes, dst, stride);
   else launch_unpack_t<double>(E, X, C, t, codes, dst, stride);

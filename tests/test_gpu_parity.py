@@ -284,3 +284,27 @@ def test_batch_zero_and_nonzero_columns():
     X = X.reshape(3, -1)
     assert res[0].iterations == 0 and res[2].iterations == 0 and np.all(X[0] == 0) and np.all(X[2] == 0)
     assert res[1].iterations == ref.iterations and rel(X[1], ref.x) < 1e-10
+
+
+@pytest.mark.parametrize("k,n,N", [(20.0, 32, 4), (15.0, 40, 5), (60.0, 256, 8)])
+def test_tensor_core_sweeps(k, n, N):
+    """complex64 sweeps on the tensor cores (TF32 operands split hi + lo, three products, FP32
+    accumulation) against the CUDA-core complex64 sweeps and the FP64 oracle sweep."""
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], 4, seed=5)
+    errs = {}
+    with hh.Handle(k, n, N, precision="fp32", tensor_cores=1) as ht, \
+            hh.Handle(k, n, N, precision="fp32", tensor_cores=0) as hc:
+        assert ht.stats()["tensor_cores"] == 1 and hc.stats()["tensor_cores"] == 0
+        for d in sweep.DIRECTIONS:
+            sw = sweep.Sweeper(A, k, n, N, d)
+            zt = ht.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
+            zc = hc.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
+            for c in range(4):
+                ref = sw.apply(r[c])
+                errs[(d, c)] = (rel(zt[c], ref), rel(zc[c], ref))
+    worst_t = max(e[0] for e in errs.values())
+    worst_c = max(e[1] for e in errs.values())
+    print(f"tensor-core vs oracle {worst_t:.2e}, CUDA-core vs oracle {worst_c:.2e}")
+    assert worst_c < 2e-4
+    assert worst_t < 2e-4
