@@ -63,10 +63,11 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // launch and only grows; `target` is the caller's running arrival target.  Every wait is
 // bounded by `budget` SM cycles: on expiry the device error word is set and false is
 // returned, so that every CTA leaves the kernel instead of spinning.
-__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned& target, int* err, long long budget) {
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned& target, int* err, long long budget,
+                                          unsigned participants) {
   __shared__ int s_ok;
   __syncthreads();
-  target += gridDim.x * gridDim.y;
+  target += participants;
   if (threadIdx.x == 0) {
     __threadfence();
     red_release_add(count, 1u);
@@ -80,6 +81,10 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned& target, int
   }
   __syncthreads();
   return s_ok != 0;
+}
+// the whole grid
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned& target, int* err, long long budget) {
+  return grid_sync(count, target, err, budget, gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------- TMA bulk copies + mbarriers

@@ -338,10 +338,45 @@ __global__ void __launch_bounds__(256) gs_update_kernel(KState S, double2* __res
   }
 }
 
+// Sum TT complex values (v[2q], v[2q+1]) over the CTAs of one right-hand side of qr_kernel:
+// per-CTA partials into qpart[parity], grid barrier, then every CTA adds the GQ partials with
+// all its threads in one fixed order, so that all CTAs hold bit-identical sums (red_out).
+template <int TT>
+__device__ __forceinline__ bool qr_reduce(double (&v)[2 * TT], const KState& S, int r, int& parity, unsigned* bar,
+                                          unsigned& target, int* err, long long budget, double* sh,
+                                          double2* red_out) {
+  block_sum<2 * TT>(v, sh);
+  double2* part = S.qpart + ((size_t)parity * S.nrhs + r) * S.GQ * TT;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < TT; ++q) part[(size_t)blockIdx.x * TT + q] = make_double2(v[2 * q], v[2 * q + 1]);
+  // the CTAs of one right-hand side meet on its own counter: right-hand sides take different
+  // numbers of reductions (their deflation decisions differ)
+  if (!grid_sync(bar + r, target, err, budget, gridDim.x)) return false;
+  double w[2 * TT];
+#pragma unroll
+  for (int q = 0; q < 2 * TT; ++q) w[q] = 0;
+  for (int b = threadIdx.x; b < S.GQ; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < TT; ++q) {
+      const double2 p = __ldcg(part + (size_t)b * TT + q);
+      w[2 * q] += p.x;
+      w[2 * q + 1] += p.y;
+    }
+  block_sum<2 * TT>(w, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < TT; ++q) red_out[q] = make_double2(w[2 * q], w[2 * q + 1]);
+  __syncthreads();
+  parity ^= 1;
+  return true;
+}
+
 // ------------------------------------------------------------------ block QR (cooperative)
-// Grid (GQ, nrhs).  Every reduction: per-CTA partials into qpart[parity], grid barrier,
-// every CTA of the right-hand side sums the GQ partials in the same order (so all take the
-// same deflation decisions).  The barrier sequence is the same for every CTA.
+// Grid (GQ, nrhs).  Every reduction: per-CTA partials into qpart[parity], a barrier among the
+// GQ CTAs of the right-hand side (bar[r]), then every CTA of the right-hand side sums the GQ
+// partials in the same order, so all of them take the same deflation decisions and run the
+// same sequence of reductions.
 template <int TT>
 __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__ W, unsigned* bar, int* err,
                                                  long long budget) {
@@ -360,81 +395,77 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
   if (writer && active)
     for (int q = 0; q < TT * TT; ++q) S.Rnew[(size_t)r * TT * TT + q] = make_double2(0, 0);
 
-  // reduce TT complex values (in v[2*TT]) across the CTAs of this right-hand side
   auto reduce = [&](double (&v)[2 * TT]) -> bool {
-    block_sum<2 * TT>(v, sh);
-    double2* part = S.qpart + ((size_t)parity * S.nrhs + r) * S.GQ * TT;
-    if (threadIdx.x == 0)
-      for (int q = 0; q < TT; ++q) part[(size_t)blockIdx.x * TT + q] = make_double2(v[2 * q], v[2 * q + 1]);
-    if (!grid_sync(bar, target, err, budget)) return false;
-    // every CTA sums the GQ partials with all its threads, in one fixed order, so all CTAs
-    // hold bit-identical sums
-    double w[2 * TT];
-#pragma unroll
-    for (int q = 0; q < 2 * TT; ++q) w[q] = 0;
-    for (int b = threadIdx.x; b < S.GQ; b += blockDim.x)
-#pragma unroll
-      for (int q = 0; q < TT; ++q) {
-        const double2 p = __ldcg(part + (size_t)b * TT + q);
-        w[2 * q] += p.x;
-        w[2 * q + 1] += p.y;
-      }
-    block_sum<2 * TT>(w, sh);
-    if (threadIdx.x == 0)
-      for (int q = 0; q < TT; ++q) red_out[q] = make_double2(w[2 * q], w[2 * q + 1]);
-    __syncthreads();
-    parity ^= 1;
-    return true;
+    return qr_reduce<TT>(v, S, r, parity, bar, target, err, budget, sh, red_out);
   };
 
+  // Every thread owns the same elements (g0 + threadIdx.x + k * blockDim.x) in every phase,
+  // so phases need no block synchronisation besides the reductions.
   double nu[TT];
   {
     double v[2 * TT];
+#pragma unroll
     for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
     if (active)
       for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x)
 #pragma unroll
         for (int j = 0; j < TT; ++j) v[2 * j] += cabs2(Wr[j * D + g]);
     if (!reduce(v)) return;
+#pragma unroll
     for (int j = 0; j < TT; ++j) nu[j] = sqrt(red_out[j].x);
   }
-  int acc = 0;
+  int acc = 0;  // accepted new vectors so far (the same in every CTA)
   int amap[TT];
+#pragma unroll
   for (int j = 0; j < TT; ++j) {
     double2* w = Wr + j * D;
-    for (int pass = 0; pass < S.passes; ++pass) {
-      double v[2 * TT];
-      for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
-      if (active && acc > 0)
-        for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-          const double2 wv = w[g];
-          for (int q = 0; q < acc; ++q) {
-            const double2 vq = Vr[q * D + g];
-            v[2 * q] = fma(vq.x, wv.x, v[2 * q]); v[2 * q] = fma(vq.y, wv.y, v[2 * q]);
-            v[2 * q + 1] = fma(vq.x, wv.y, v[2 * q + 1]); v[2 * q + 1] = fma(-vq.y, wv.x, v[2 * q + 1]);
+    double nrm = 0;  // |w_j|^2 of this thread's elements after the last pass
+    if (acc > 0) {
+      for (int pass = 0; pass < S.passes; ++pass) {
+        double v[2 * TT];
+#pragma unroll
+        for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
+        if (active)
+          for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+            const double2 wv = w[g];
+#pragma unroll
+            for (int q = 0; q < TT - 1; ++q)
+              if (q < acc) {
+                const double2 vq = Vr[q * D + g];
+                v[2 * q] = fma(vq.x, wv.x, v[2 * q]); v[2 * q] = fma(vq.y, wv.y, v[2 * q]);
+                v[2 * q + 1] = fma(vq.x, wv.y, v[2 * q + 1]); v[2 * q + 1] = fma(-vq.y, wv.x, v[2 * q + 1]);
+              }
           }
-        }
-      if (!reduce(v)) return;
-      if (active && acc > 0) {
+        if (!reduce(v)) return;
         double2 c[TT];
+#pragma unroll
         for (int q = 0; q < TT; ++q) c[q] = red_out[q];
-        for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-          double2 wv = w[g];
-          for (int q = 0; q < acc; ++q) wv = csub(wv, cmul(c[q], Vr[q * D + g]));
-          w[g] = wv;
-        }
-        if (writer)
-          for (int q = 0; q < acc; ++q) {
-            double2* p = S.Rnew + (size_t)r * TT * TT + q * TT + j;
-            *p = cadd(*p, c[q]);
+        const bool last = pass == S.passes - 1;
+        nrm = 0;
+        if (active)
+          for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+            double2 wv = w[g];
+#pragma unroll
+            for (int q = 0; q < TT - 1; ++q)
+              if (q < acc) wv = csub(wv, cmul(c[q], Vr[q * D + g]));
+            w[g] = wv;
+            if (last) nrm += cabs2(wv);
           }
+        if (writer && active)
+#pragma unroll
+          for (int q = 0; q < TT - 1; ++q)
+            if (q < acc) {
+              double2* p = S.Rnew + (size_t)r * TT * TT + q * TT + j;
+              *p = cadd(*p, c[q]);
+            }
       }
-      __syncthreads();
+    } else if (active) {
+      for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) nrm += cabs2(w[g]);
     }
     double v[2 * TT];
+#pragma unroll
     for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
-    if (active)
-      for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) v[0] += cabs2(w[g]);
+    v[0] = nrm;
     if (!reduce(v)) return;
     const double rjj = sqrt(red_out[0].x);
     amap[j] = -1;
@@ -446,10 +477,10 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
       amap[j] = acc;
       ++acc;
     }
-    __syncthreads();
   }
   if (writer && active) {
     S.nacc[r] = acc;
+#pragma unroll
     for (int j = 0; j < TT; ++j) {
       S.amap[r * TT + j] = amap[j];
       S.nu[r * TT + j] = nu[j];
@@ -658,6 +689,7 @@ struct SlotSolver::Impl {
   KState K{};
   std::vector<void*> owned;
   double2* W = nullptr;       // S * t * D operator outputs / residual scratch
+  unsigned* qbar = nullptr;   // per-slot barrier counters of the block QR
   double2* xstage = nullptr;  // S * D solutions of slots whose caller buffer is host memory
   int* d_act = nullptr;
   IterTables T{};
@@ -741,6 +773,7 @@ struct SlotSolver::Impl {
     K.tolv = dev<double>(S); K.Zcur = dev<double2*>(S); K.Vcur = dev<double2*>(S);
     K.adm = dev<int>(S); K.fin = dev<int>(S); K.xout = dev<double2*>(S); K.bdev = dev<double2>((size_t)S * D);
     W = dev<double2>((size_t)S * t * D);
+    qbar = dev<unsigned>(S);
     xstage = dev<double2>((size_t)S * D);
     d_act = dev<int>(S);
     T.src = (const double2**)dev<double2*>((size_t)S * t); T.scale = dev<double>((size_t)S * t);
@@ -826,8 +859,8 @@ struct SlotSolver::Impl {
       gs_update_kernel<TT><<<gsgrid, 256, smem, E.stream>>>(K, W);
       E.count_launch(3);
     }
-    cudaMemsetAsync(E.bar, 0, sizeof(unsigned), E.stream);
-    void* args[] = {(void*)&K, (void*)&W, (void*)&E.bar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
+    cudaMemsetAsync(qbar, 0, sizeof(unsigned) * S, E.stream);
+    void* args[] = {(void*)&K, (void*)&W, (void*)&qbar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
     ce = E.launch_coop((const void*)qr_kernel<TT>, K.GQ, 256, 0, args, S);
   }
 

@@ -296,6 +296,101 @@ __global__ void __launch_bounds__(256) line_gemv_kernel(const typename Cx<R>::T*
   }
 }
 
+// Narrow steps, second form: x (m x ncols, ncols <= 8) is formed once into a column-major
+// scratch array xout[c * m + k] by line_xbuild_kernel; line_gemv_split_kernel then gives
+// each CTA RPC rows of the factor block and splits the node index across its 8 warps, so that
+// every lane issues its loads of A and x together; the warps' partial sums meet in shared
+// memory before the step's output modes.
+template <typename R>
+__global__ void line_xbuild_kernel(int m, LineOperand<typename Cx<R>::T> op, Coef cf, typename Cx<R>::T* __restrict__ xout) {
+  using T = typename Cx<R>::T;
+  const int ncols = op.ns * op.C, N = op.N, C = op.C;
+  const size_t istride = (size_t)N * C;
+  const double2 ve = cf.vert(0), vi = cf.vert(1);
+  const T vert_edge = mk<T>(ve.x, ve.y), vert_int = mk<T>(vi.x, vi.y);
+  const R dg = (R)cf.diag();
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * ncols; idx += gridDim.x * blockDim.x) {
+    const int k = idx / ncols, col = idx % ncols;
+    const int s = op.s0 + col / C, c = col % C;
+    T v = op.base ? __ldcg(op.base + ((size_t)(op.base_j * m + k) * N + s) * C + c) : mk<T>(0, 0);
+    if (op.cpl != XC_NONE) {
+      const T* sp = op.src + ((size_t)op.src_j * m * N + (s + op.src_ds)) * C + c;
+      T cp = __ldcg(sp + (size_t)k * istride);
+      if (op.cpl != XC_IDENT) {
+        const int nb = op.cpl == XC_LOWER ? k - 1 : k + 1;
+        const T y = (nb >= 0 && nb < m) ? __ldcg(sp + (size_t)nb * istride) : mk<T>(0, 0);
+        cp = cmul((k == 0 || k == m - 1) ? vert_edge : vert_int, cp);
+        cp.x += dg * y.x;
+        cp.y += dg * y.y;
+      }
+      v = op.neg ? csub(v, cp) : cadd(v, cp);
+    }
+    xout[(size_t)col * m + k] = v;
+  }
+}
+
+template <typename R, int RPC>
+__global__ void __launch_bounds__(256) line_gemv_split_kernel(const typename Cx<R>::T* __restrict__ A, int lda, int m,
+                                                              LineOperand<typename Cx<R>::T> op,
+                                                              const typename Cx<R>::T* __restrict__ x) {
+  using T = typename Cx<R>::T;
+  __shared__ T red[8][RPC][8];
+  const int ncols = op.ns * op.C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * RPC;
+  const int kw = ((m + 7) / 8 + 31) / 32 * 32;  // node indices per warp, a multiple of 32
+  const int kb = warp * kw, ke = min(m, kb + kw);
+  T acc[RPC][8];
+#pragma unroll
+  for (int r = 0; r < RPC; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = mk<T>(0, 0);
+#pragma unroll 2
+  for (int k = kb + lane; k < ke; k += 32) {
+    T a[RPC];
+#pragma unroll
+    for (int r = 0; r < RPC; ++r) a[r] = row0 + r < m ? __ldg(A + (size_t)(row0 + r) * lda + k) : mk<T>(0, 0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c < ncols) {
+        const T xv = __ldcg(x + (size_t)c * m + k);
+#pragma unroll
+        for (int r = 0; r < RPC; ++r) cfma(acc[r][c], a[r], xv);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RPC; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c < ncols) {
+        T v = acc[r][c];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v = cadd(v, shfl_xor(v, o));
+        if (lane == 0) red[warp][r][c] = v;
+      }
+    }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < RPC * ncols) {
+    const int r = t / ncols, col = t % ncols;
+    const int gr = row0 + r;
+    if (gr < m) {
+      T z = red[0][r][col];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) z = cadd(z, red[w][r][col]);
+      const int N = op.N, C = op.C;
+      const int s = op.s0 + col / C, c = col % C;
+      T* o = op.out + ((size_t)(op.out_j * m + gr) * N + s) * C + c;
+      apply_out(o, z, op.out_mode);
+      if (op.acc) {
+        T* a2 = op.acc + ((size_t)(op.acc_j * m + gr) * N + s) * C + c;
+        apply_out(a2, op.out_mode == OUT_SET ? z : *o, op.acc_mode);
+      }
+    }
+  }
+}
+
 size_t Engine::sweep_ws_bytes(int C) const { return (size_t)(R + 1) * m * N * C * sweep_elem(); }
 
 size_t Engine::sweep_partial_bytes(int C) const { return (size_t)8 * m * N * C * sweep_elem(); }
@@ -354,7 +449,13 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
     op.s0 = s.s0; op.ns = s.ns; op.N = E.N; op.C = C;
     const T* A = Fb + (size_t)s.f * blk;
     const int ncols = s.ns * C;
-    if (ncols <= 8 && (size_t)E.m * ncols * sizeof(T) <= gemv_cap) {
+    if (ncols <= 8 && partial_buf && partial_bytes >= (size_t)E.m * ncols * sizeof(T)) {
+      T* xs = reinterpret_cast<T*>(partial_buf);  // narrow steps leave the split-K buffer free
+      line_xbuild_kernel<R><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(E.m, op, E.coef, xs);
+      constexpr int RPC = 4;
+      line_gemv_split_kernel<R, RPC><<<(E.m + RPC - 1) / RPC, 256, 0, E.stream>>>(A, E.ldf, E.m, op, xs);
+      E.count_launch(2);
+    } else if (ncols <= 8 && (size_t)E.m * ncols * sizeof(T) <= gemv_cap) {
       line_gemv_kernel<R><<<(E.m + 7) / 8, 256, (size_t)E.m * ncols * sizeof(T), E.stream>>>(A, E.ldf, E.m, op,
                                                                                           E.coef);
       E.count_launch();
