@@ -129,20 +129,27 @@ def measured_peaks() -> dict:
     else:
         out = {"hbm_gbs": 6800.0, "sm_mhz": 2070.0, "src": "fallback"}
     out["fp32_alu_tflops"] = 152 * 128 * 2 * out["sm_mhz"] * 1e6 / 1e12
+    # FP64: the nominal GB300 rate of the profiling recipe (FP64 FMA measured at 1.2 TFLOP/s)
+    out["fp64_tflops"] = 1.25
+    # TF32 dense tensor rate: the measured bf16 burst rate x the nominal TF32 / bf16 ratio
+    bf16 = float(json.load(open(p))["bf16_tflops"]) if os.path.exists(p) else 1900.0
+    out["tf32_tflops"] = bf16 * 1.1 / 2.25
+    out["tf32_src"] = ("measured bf16 %.0f TFLOP/s (MEASURED_PEAKS.json) x nominal TF32/bf16 1.1/2.25" % bf16
+                       if os.path.exists(p) else "fallback bf16 1900 TFLOP/s x 1.1/2.25")
     return out
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("gemm.cuh", "common.cuh"):
+    for f in ("gemm.cuh", "tc_gemm.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2408_11929_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str):
+def ncu_traffic(workload: str, kind: str = "simt"):
     """DRAM bytes per launch of the wide sweep GEMM step from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "line_gemm_traffic.json")
+    p = os.path.join(ROOT, "profiles", "line_gemm_traffic.json" if kind == "simt" else "tc_line_gemm_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -282,6 +289,42 @@ def run_gpu(args, ws, rank, local):
         gemm_flops = st["gemm_flops"] / ngm
         achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms else None
         step_total_ms = sum(step_ms)
+        # the two heaviest kernels: the wide sweep GEMM step (tensor cores; timed in sampled
+        # sweeps) and the FP64 Gram-Schmidt inner products (every launch timed)
+        gemm_total_ms = (gemm_ms or 0.0) * st["wide_steps"] * st["sweep_launches"]
+        ngd = max(1, st["gsdot_launches"])
+        gsdot_ms = st["gsdot_ms"] / ngd if st["gsdot_ms"] > 0 else None
+        gsdot_flops = st["gsdot_flops"] / ngd
+        gsdot_ach = gsdot_flops / (gsdot_ms / 1e3) / 1e12 if gsdot_ms else None
+        tc_on = bool(st["tensor_cores"])
+        gemm_peak = peaks["tf32_tflops"] if tc_on else peaks["fp32_alu_tflops"]
+        gemm_line = {
+            "bound": "tensor" if tc_on else "alu",
+            "kernel": ("tc_line_gemm_kernel (tcgen05 kind::tf32, 3 products per K step) + split_reduce_kernel"
+                       if tc_on else "line_gemm_kernel<float> + split_reduce_kernel") + ": wide sweep GEMM step",
+            "achieved": achieved, "peak": gemm_peak, "unit": "TFLOP/s",
+            "frac": (achieved / gemm_peak) if achieved else None,
+            "traffic": traffic if not tc_on else ncu_traffic(WORKLOAD, "tc"),
+            "algorithmic_flops_per_launch": gemm_flops, "avg_launch_ms": gemm_ms,
+            "launches_timed": st["gemm_launches"],
+            "share_of_step": gemm_total_ms / step_total_ms if step_total_ms > 0 else None,
+            "peak_src": peaks["tf32_src"] if tc_on else
+            "derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x %.0f MHz" % peaks["sm_mhz"],
+            "note": "algorithmic flops = 8 m^2 per complex column (complex multiply-adds); the tensor "
+                    "cores execute three TF32 products per K step (hi*hi + hi*lo + lo*hi), so the "
+                    "attainable fraction of the TF32 peak is at most 1/3"}
+        gsdot_line = {
+            "bound": "alu", "kernel": "gs_dot_kernel<4,4>: FP64 block Gram-Schmidt inner products",
+            "achieved": gsdot_ach, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": (gsdot_ach / peaks["fp64_tflops"]) if gsdot_ach else None, "traffic": None,
+            "algorithmic_flops_per_launch": gsdot_flops, "avg_launch_ms": gsdot_ms,
+            "launches_timed": st["gsdot_launches"],
+            "share_of_step": st["gsdot_ms"] / step_total_ms if step_total_ms > 0 else None,
+            "peak_src": "nominal GB300 FP64 rate 1.25 TFLOP/s (profiling recipe); FP64 FMA measured 1.2 TFLOP/s",
+            "note": "FP64 complex multiply-adds at 8 flops each; bound by the FP64 pipe, not HBM "
+                    "(it reads 16 bytes per 32 flops)"}
+        ranked = sorted([gemm_line, gsdot_line], key=lambda r: -(r["share_of_step"] or 0))
+        dominant, others = ranked[0], ranked[1:]
         traffic = ncu_traffic(WORKLOAD)
         g = golden(w)
         err = None
@@ -300,14 +343,8 @@ def run_gpu(args, ws, rank, local):
             "time_to_tol_ms": tmax / args.steps * 1e3, "iterations": iters[-1], "iterations_oracle": iters_oracle,
             "status": hh.STATUS_NAMES[status], "rel_res_explicit": rel_exp, "setup_ms": setup_ms,
             "error_vs_oracle_tight": err,
-            "roofline": {"bound": "alu", "kernel": "line_gemm_kernel<float> (+ split_reduce_kernel): wide sweep GEMM step",
-                         "achieved": achieved, "peak": peaks["fp32_alu_tflops"], "unit": "TFLOP/s",
-                         "frac": (achieved / peaks["fp32_alu_tflops"]) if achieved else None, "traffic": traffic,
-                         "algorithmic_flops_per_launch": gemm_flops, "avg_launch_ms": gemm_ms,
-                         "launches": st["gemm_launches"],
-                         "share_of_step": st["gemm_ms"] / step_total_ms if step_total_ms > 0 else None,
-                         "peak_src": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x %.0f MHz (max SM clock, %s)"
-                                     % (peaks["sm_mhz"], peaks["src"] + " MEASURED_PEAKS.json" if peaks["src"] == "measured" else "fallback")},
+            "roofline": dominant,
+            "roofline_others": others,
             "phase_roofline": {
                 "sweep": {"ms_per_launch": sweep_ms, "bytes_per_launch": st["sweep_bytes"] / nsw,
                           "gbs": (st["sweep_bytes"] / nsw) / (sweep_ms / 1e3) / 1e9 if sweep_ms else None,

@@ -107,6 +107,11 @@ typedef struct {
      multiply-add flops (8 m^2 per column) */
   int64_t gemm_launches;   double gemm_ms;   double gemm_flops;
   int tensor_cores;        /* 1 when the wide sweep steps run on the tensor cores */
+  /* the Gram-Schmidt inner-product kernel (every launch, within the gs class): launches,
+     device time (ms, with opts.profile) and FP64 flops (8 per basis element and new column) */
+  int64_t gsdot_launches;  double gsdot_ms;  double gsdot_flops;
+  double gs_flops;         /* FP64 flops of the whole gs class (both passes, dot + update) */
+  int64_t wide_steps;      /* wide GEMM steps in one sweep of the last column count */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

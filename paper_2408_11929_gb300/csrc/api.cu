@@ -532,6 +532,12 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->gemm_ms = E.ms[Engine::K_GEMM];
   st->gemm_flops = E.flops[Engine::K_GEMM];
   st->tensor_cores = E.tc_ready ? 1 : 0;
+  st->gsdot_launches = E.launches[Engine::K_GSDOT];
+  st->gsdot_ms = E.ms[Engine::K_GSDOT];
+  st->gsdot_flops = E.flops[Engine::K_GSDOT];
+  st->gs_flops = E.flops[Engine::K_GS];
+  for (const SweepStep& sp : E.opts.single_sweep ? E.steps_single : E.steps_double)
+    st->wide_steps += (int64_t)(sp.ns * E.last_columns > 8);
   return HH_OK;
 }
 

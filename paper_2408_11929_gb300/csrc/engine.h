@@ -92,20 +92,21 @@ class Engine {
   // statistics
   // K_GEMM: the wide GEMM steps inside a sweep (GEMM launch + its split-K reduction), a subset
   // of K_SWEEP timed on their own
-  enum KClass { K_SWEEP = 0, K_SPMV = 1, K_GS = 2, K_SETUP = 3, K_GEMM = 4, K_NCLASS = 5 };
+  // K_GSDOT: the Gram-Schmidt inner-product kernel alone (every launch), within K_GS
+  enum KClass { K_SWEEP = 0, K_SPMV = 1, K_GS = 2, K_SETUP = 3, K_GEMM = 4, K_GSDOT = 5, K_NCLASS = 6 };
   struct Tick { cudaEvent_t a, b; int cls; double bytes, flops; };
   std::vector<Tick> pending_ticks;
   std::vector<cudaEvent_t> event_pool;
-  int64_t launches[K_NCLASS] = {0, 0, 0, 0, 0};
-  double ms[K_NCLASS] = {0, 0, 0, 0, 0};
-  double bytes[K_NCLASS] = {0, 0, 0, 0, 0};
-  double flops[K_NCLASS] = {0, 0, 0, 0, 0};
+  int64_t launches[K_NCLASS] = {0, 0, 0, 0, 0, 0};
+  double ms[K_NCLASS] = {0, 0, 0, 0, 0, 0};
+  double bytes[K_NCLASS] = {0, 0, 0, 0, 0, 0};
+  double flops[K_NCLASS] = {0, 0, 0, 0, 0, 0};
   int64_t kernel_launches = 0;
   double setup_ms_total = 0;
   int last_columns = 0;
   int64_t sweep_calls = 0;
   Tick cur_tick[K_NCLASS];
-  bool tick_open[K_NCLASS] = {false, false, false, false, false};
+  bool tick_open[K_NCLASS] = {false, false, false, false, false, false};
 
   // request loop (hh_submit / hh_poll)
   std::mutex mu;

@@ -849,10 +849,14 @@ struct SlotSolver::Impl {
   }
 
   template <int TT>
-  void gs_and_qr(cudaError_t& ce) {
+  // nv: basis vectors of all active slots (each projected against its t new columns)
+  void gs_and_qr(cudaError_t& ce, double nv) {
     dim3 gsgrid(K.GX, S);
     for (int pass = 0; pass < K.passes; ++pass) {
+      E.tick_begin(Engine::K_GSDOT);
       gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K, W);
+      // one complex multiply-add (8 real flops) per basis element and new column
+      E.tick_end(Engine::K_GSDOT, nv * D * 16.0 + (double)t * D * 16.0 * nv / 4.0, 8.0 * nv * t * D);
       gs_reduce_kernel<<<S, 256, 0, E.stream>>>(K, pass == 0);
       const size_t smem = (size_t)K.maxV * TT * sizeof(double2) + (size_t)K.maxV * sizeof(void*);
       cudaFuncSetAttribute((const void*)gs_update_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -900,19 +904,18 @@ struct SlotSolver::Impl {
       spmv_tab_kernel<<<E.grid_for(D * C), 256, 0, E.stream>>>(T.zdst, T.wdst, C, E.coef);
       E.count_launch();
       E.tick_end(Engine::K_SPMV, 2.0 * C * D * 16.0, 0);
+      double nv = 0;  // basis vectors of the active slots before this iteration's block
+      for (int a = 0; a < nact; ++a) nv += 1.0 + (double)(slots[h_act[a]].blocks.size() / 2 - 1) * t;
       E.tick_begin(Engine::K_GS);
       cudaError_t ce = cudaSuccess;
       switch (t) {
-        case 1: gs_and_qr<1>(ce); break;
-        case 2: gs_and_qr<2>(ce); break;
-        case 3: gs_and_qr<3>(ce); break;
-        default: gs_and_qr<4>(ce); break;
+        case 1: gs_and_qr<1>(ce, nv); break;
+        case 2: gs_and_qr<2>(ce, nv); break;
+        case 3: gs_and_qr<3>(ce, nv); break;
+        default: gs_and_qr<4>(ce, nv); break;
       }
-      {
-        double nv = 0;
-        for (int a = 0; a < nact; ++a) nv += 1.0 + (double)(slots[h_act[a]].blocks.size() / 2 - 1) * t;
-        E.tick_end(Engine::K_GS, K.passes * (2.0 * nv * D * 16 + 3.0 * C * D * 16) + 6.0 * C * D * 16, 0);
-      }
+      E.tick_end(Engine::K_GS, K.passes * (2.0 * nv * D * 16 + 3.0 * C * D * 16) + 6.0 * C * D * 16,
+                 K.passes * 16.0 * nv * t * D);
       if (ce != cudaSuccess) return (E.set_cuda_error(ce, "qr launch"), HH_ECUDA);
       const size_t hsmem = (size_t)(K.maxZ + 2) * sizeof(double2);
       cudaFuncSetAttribute((const void*)hess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);

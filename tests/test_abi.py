@@ -41,15 +41,15 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "hh.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hh_opts), sizeof(hh_result),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hh_opts), sizeof(hh_result),'
                     ' sizeof(hh_stats), offsetof(hh_opts, stream), offsetof(hh_stats, sweep_steps),'
-                    ' offsetof(hh_result, status), offsetof(hh_stats, gemm_flops));return 0;}\n')
+                    ' offsetof(hh_result, status), offsetof(hh_stats, gemm_flops), offsetof(hh_stats, gs_flops));return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(hh.hh_opts), ctypes.sizeof(hh.hh_result), ctypes.sizeof(hh.hh_stats),
                     hh.hh_opts.stream.offset, hh.hh_stats.sweep_steps.offset, hh.hh_result.status.offset,
-                    hh.hh_stats.gemm_flops.offset]
+                    hh.hh_stats.gemm_flops.offset, hh.hh_stats.gs_flops.offset]
 
 
 def test_default_opts(lib):
