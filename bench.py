@@ -390,6 +390,46 @@ def run_fp64(w, local):
             "rel_res_explicit": res.rel_res_explicit}
 
 
+def run_serving(nreq: int, rate_hz: float, seed: int = 0) -> dict:
+    """The mixed-k request stream: nreq requests (k uniform in [50, 400], n = ceil(2.5k/32)*32,
+    strips of 32 node lines, one Gaussian each, tol 1e-6) arriving as a Poisson stream of
+    rate_hz, through one hh_server (complex64 sweeps on the tensor cores, 2 slots per
+    problem).  Latency = submission to completion (queueing, setup of an uncached problem and
+    the solve); throughput = requests / (last completion - first arrival)."""
+    import paper_2408_11929_gb300 as hh
+    reqs = hh_inputs.serving_stream(nreq, seed=seed, rate_hz=rate_hz)
+    xs = [np.zeros((q["n"] + 1) ** 2, dtype=np.complex128) for q in reqs]
+    done, tickets = {}, []
+    with hh.Server(precision="fp32", serve_slots=2) as srv:
+        t0 = time.perf_counter()
+        i = 0
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i]["t_arrive"] <= now:
+                q = reqs[i]
+                tickets.append(srv.submit(q["k"], q["n"], q["strips"], q["sources"], xs[i], tol=1e-6))
+                i += 1
+            for j, t in enumerate(tickets):
+                if j not in done:
+                    st, res = srv.poll(t)
+                    if st != hh.HH_EPENDING:
+                        done[j] = (st, res, time.perf_counter() - t0)
+            time.sleep(0.0005)
+        stats = srv.stats()
+    lat = [done[j][1].t_solve_ms for j in range(len(reqs))]
+    t_end = max(done[j][2] for j in range(len(reqs)))
+    return {
+        "nreq": nreq, "rate_hz": rate_hz, "seed": seed,
+        "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99), "mean_ms": float(np.mean(lat)),
+        "solves_per_s": nreq / (t_end - reqs[0]["t_arrive"]),
+        "all_ok": all(done[j][0] == hh.HH_OK for j in range(len(reqs))),
+        "max_rel_res_explicit": max(done[j][1].rel_res_explicit for j in range(len(reqs))),
+        "iterations_mean": float(np.mean([done[j][1].iterations for j in range(len(reqs))])),
+        "setups": stats["setups"], "cache_hits": stats["cache_hits"], "evictions": stats["evictions"],
+        "setup_ms_total": stats["setup_ms"], "k_range": [50, 400], "n_range": [128, 1024],
+        "kind": "open loop, Poisson arrivals, mixed k; latency includes queueing and the setup of uncached problems"}
+
+
 def run_sweep_only(args):
     """One direction's double sweep on 4 columns (the column count of one 4-direction solve
     iteration), k = 0.39 n, timed with CUDA events on the launching stream."""
@@ -438,7 +478,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep"],
+    ap.add_argument("--serve-nreq", type=int, default=40, help="requests of the mixed-k serving stream (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving stream (1/s)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve"],
                     help="sweep: time hh_apply_preconditioner alone (4 columns) -- the profiling case")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--strips", type=int, default=32)
@@ -446,6 +488,11 @@ def main():
     args = ap.parse_args()
     if args.mode == "sweep":
         run_sweep_only(args)
+        return
+    if args.mode == "serve":
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"mode": "serve", **run_serving(args.serve_nreq, args.serve_rate)}), flush=True)
         return
     ws, rank, local = dist_env()
     w = hh_inputs.workload(WORKLOAD)
@@ -483,6 +530,10 @@ def main():
         dist.init_process_group("nccl")
     out = run_gpu(args, ws, rank, local)
     if rank == 0:
+        if args.serve_nreq > 0:
+            out["serving"] = run_serving(args.serve_nreq, args.serve_rate)
+            out["latency_ms"]["serving_p50"] = out["serving"]["p50_ms"]
+            out["latency_ms"]["serving_p99"] = out["serving"]["p99_ms"]
         if not args.no_fp64:
             out["fp64"] = run_fp64(w, local)
             out["fp32_speedup_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["ms_per_step"]

@@ -189,6 +189,54 @@ void hh_destroy(hh_handle* h);
 /* Message of the last failure in this thread ("" if none).  Valid until the next call. */
 const char* hh_last_error(void);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving: requests for many problems (k, n) behind one submit / poll interface.
+ *
+ * The server keeps one handle per (k, n, strips, dirs) resident on the device (strip
+ * factors, sweep workspaces, Krylov state) and reuses it for later requests of the same
+ * problem.  A request for an uncached problem is admitted by device memory: the new
+ * handle's bytes are estimated and, if the budget is exceeded, idle handles are evicted least
+ * recently used first; if that is not enough the request waits until running requests
+ * finish.  Each handle has its own stream and request loop (continuous batching, hh_submit),
+ * so solves of different problems and the setup of a new one overlap on the device.
+ * ------------------------------------------------------------------------------------- */
+typedef struct hh_server hh_server;
+
+typedef struct {
+  int64_t handles;          /* problems resident */
+  int64_t bytes_reserved;   /* estimated device bytes of the resident handles */
+  int64_t budget;           /* device-memory budget */
+  int64_t setups;           /* handles built */
+  int64_t cache_hits;       /* requests served by a resident handle */
+  int64_t evictions;        /* handles destroyed to make room */
+  int64_t completed;        /* requests finished */
+  int64_t queued, running;  /* requests waiting for admission / being solved */
+  double setup_ms;          /* summed host time of the setups */
+} hh_server_stats;
+
+/* opts: the options of every handle the server builds (NULL = defaults; the stream field
+ * is ignored: every handle gets its own).  mem_budget: device bytes the resident handles
+ * may hold (0 = 85 % of the free device memory at creation).  Errors: HH_EINVAL, HH_ECUDA. */
+hh_status hh_server_create(const hh_opts* opts, size_t mem_budget, hh_server** out);
+
+/* Queue one solve of the problem (k, n, strips, dirs) with the load vector of nsrc Gaussian
+ * sources (rows x0, y0, sigma, re, im; copied) to relative residual tol.  x: host or device
+ * pointer of 2 (n+1)^2 doubles (complex128, node order), written when the request finishes;
+ * it must stay valid until hh_server_poll returns something other than HH_EPENDING.
+ * Errors: HH_EINVAL (bad problem or arguments). */
+hh_status hh_server_submit(hh_server* s, double k, int n, int strips, uint32_t dirs, int nsrc, const double* src,
+                           double* x, double tol, hh_ticket* ticket);
+
+/* HH_EPENDING while the request is queued or running; otherwise its final status, with
+ * res->t_solve_ms = time from submission to completion (queueing, setup and solve) and
+ * res->t_setup_ms the problem's setup time. */
+hh_status hh_server_poll(hh_server* s, hh_ticket ticket, hh_result* res);
+
+hh_status hh_server_get_stats(hh_server* s, hh_server_stats* st);
+
+/* Fails the queued requests (HH_EINVAL), waits for the running ones, frees everything. */
+void hh_server_destroy(hh_server* s);
+
 #ifdef __cplusplus
 }
 #endif

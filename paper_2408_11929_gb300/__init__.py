@@ -57,9 +57,20 @@ class hh_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class hh_server_stats(ctypes.Structure):
+    _fields_ = [("handles", ctypes.c_int64), ("bytes_reserved", ctypes.c_int64), ("budget", ctypes.c_int64),
+                ("setups", ctypes.c_int64), ("cache_hits", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("setup_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 EXPORTS = ["hh_default_opts", "hh_setup", "hh_solve", "hh_solve_batch", "hh_submit", "hh_poll", "hh_assemble_rhs",
-           "hh_apply_operator", "hh_apply_preconditioner", "hh_apply_preconditioner_noalloc", "hh_get_factor", "hh_get_stats", "hh_reset_stats",
-           "hh_destroy", "hh_last_error"]
+           "hh_apply_operator", "hh_apply_preconditioner", "hh_apply_preconditioner_noalloc", "hh_get_factor",
+           "hh_get_stats", "hh_reset_stats", "hh_destroy", "hh_last_error", "hh_server_create", "hh_server_submit",
+           "hh_server_poll", "hh_server_get_stats", "hh_server_destroy"]
 
 _lib = None
 
@@ -92,8 +103,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hh_destroy.restype = None
     L.hh_last_error.argtypes = []
     L.hh_last_error.restype = ctypes.c_char_p
+    L.hh_server_create.argtypes = [ctypes.POINTER(hh_opts), ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.hh_server_submit.argtypes = [vp, d, i, i, u32, i, vp, vp, d, ctypes.POINTER(ctypes.c_uint64)]
+    L.hh_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hh_result)]
+    L.hh_server_get_stats.argtypes = [vp, ctypes.POINTER(hh_server_stats)]
+    L.hh_server_destroy.argtypes = [vp]
+    L.hh_server_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("hh_default_opts", "hh_reset_stats", "hh_destroy", "hh_last_error"):
+        if name not in ("hh_default_opts", "hh_reset_stats", "hh_destroy", "hh_last_error", "hh_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -244,3 +261,55 @@ class Handle:
 
     def reset_stats(self):
         self.lib.hh_reset_stats(self.h)
+
+
+class Server:
+    """hh_server_create ... hh_server_destroy: solves of many problems (k, n) behind one
+    submit / poll interface, with a device-resident factor cache admitted by memory."""
+
+    def __init__(self, mem_budget: int = 0, **opts):
+        self.lib = load()
+        self.opts = default_opts(**opts)
+        s = ctypes.c_void_p()
+        st = self.lib.hh_server_create(ctypes.byref(self.opts), int(mem_budget), ctypes.byref(s))
+        if st != HH_OK:
+            raise HHError(st, "hh_server_create")
+        self.s = s
+
+    def submit(self, k: float, n: int, strips: int, sources, x, tol: float = 1e-6, dirs="LR+RL+BT+TB") -> int:
+        src = np.ascontiguousarray(np.atleast_2d(np.asarray(sources, dtype=np.float64)))
+        t = ctypes.c_uint64()
+        st = self.lib.hh_server_submit(self.s, float(k), int(n), int(strips), dirs_mask(dirs), src.shape[0],
+                                       src.ctypes.data, _ptr(x), float(tol), ctypes.byref(t))
+        if st != HH_OK:
+            raise HHError(st, "hh_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """(status, hh_result or None); HH_EPENDING while queued or running."""
+        res = hh_result()
+        st = self.lib.hh_server_poll(self.s, ctypes.c_uint64(ticket), ctypes.byref(res))
+        return st, (None if st == HH_EPENDING else res)
+
+    def stats(self) -> dict:
+        st = hh_server_stats()
+        if self.lib.hh_server_get_stats(self.s, ctypes.byref(st)) != HH_OK:
+            raise HHError(HH_EINVAL, "hh_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.hh_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
