@@ -112,6 +112,8 @@ typedef struct {
   int64_t gsdot_launches;  double gsdot_ms;  double gsdot_flops;
   double gs_flops;         /* FP64 flops of the whole gs class (both passes, dot + update) */
   int64_t wide_steps;      /* wide GEMM steps in one sweep of the last column count */
+  int ns_blocks;           /* strip inverses computed by Newton-Schulz from the previous one */
+  int ns_iterations;       /* their iterations (two GEMMs each) */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -51,7 +51,8 @@ class hh_stats(ctypes.Structure):
                 ("m", ctypes.c_int), ("ldf", ctypes.c_int), ("columns", ctypes.c_int), ("sweep_steps", ctypes.c_int64),
                 ("gemm_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double),
                 ("tensor_cores", ctypes.c_int), ("gsdot_launches", ctypes.c_int64), ("gsdot_ms", ctypes.c_double),
-                ("gsdot_flops", ctypes.c_double), ("gs_flops", ctypes.c_double), ("wide_steps", ctypes.c_int64)]
+                ("gsdot_flops", ctypes.c_double), ("gs_flops", ctypes.c_double), ("wide_steps", ctypes.c_int64),
+                ("ns_blocks", ctypes.c_int), ("ns_iterations", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -536,6 +536,8 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->gsdot_ms = E.ms[Engine::K_GSDOT];
   st->gsdot_flops = E.flops[Engine::K_GSDOT];
   st->gs_flops = E.flops[Engine::K_GS];
+  st->ns_blocks = E.ns_blocks;
+  st->ns_iterations = E.ns_iterations;
   for (const SweepStep& sp : E.opts.single_sweep ? E.steps_single : E.steps_double)
     st->wide_steps += (int64_t)(sp.ns * E.last_columns > 8);
   return HH_OK;

@@ -105,6 +105,7 @@ class Engine {
   double setup_ms_total = 0;
   int last_columns = 0;
   int64_t sweep_calls = 0;
+  int ns_blocks = 0, ns_iterations = 0;  // strip inverses by Newton-Schulz, and its iterations
   Tick cur_tick[K_NCLASS];
   bool tick_open[K_NCLASS] = {false, false, false, false, false, false};
 

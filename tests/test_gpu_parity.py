@@ -73,6 +73,30 @@ def test_strip_factors_fp64(k, n, N):
             assert rel(h.get_factor(j), ref[j]) < 1e-11, j
 
 
+@pytest.mark.parametrize("k,n,N", [(20.0, 32, 4), (12.0, 16, 8), (100.0, 256, 16)])
+def test_strip_factors_fp32_newton_schulz(k, n, N):
+    """complex64 factors: F_0, F_1 by pivoted elimination, F_j (j >= 2) by Newton-Schulz from
+    F_{j-1}; every one against the inverse of the oracle's Schur complement to complex64
+    accuracy (the Schur complements have condition numbers near 6)."""
+    A, *_ = fem.global_system(k, n)
+    Ad = A.toarray() if n <= 64 else None
+    m, R = n + 1, n // N
+    As = A.tocsr()
+    blk = lambda a, b: (Ad[a * m:(a + 1) * m, b * m:(b + 1) * m] if Ad is not None
+                        else As[a * m:(a + 1) * m, b * m:(b + 1) * m].toarray())
+    Dbot, Dint, Dtop = blk(0, 0), blk(1, 1), blk(n, n)
+    L, U = blk(1, 0), blk(0, 1)
+    ref = [np.linalg.inv(Dbot)]
+    for j in range(1, R):
+        ref.append(np.linalg.inv(Dint - L @ ref[-1] @ U))
+    ref.append(np.linalg.inv(Dtop - L @ ref[-1] @ U))
+    with hh.Handle(k, n, N, precision="fp32") as h:
+        st = h.stats()
+        assert st["ns_blocks"] >= R - 2 and st["ns_iterations"] <= 12 * st["ns_blocks"]
+        for j in range(R + 1):
+            assert rel(h.get_factor(j), ref[j]) < 2e-5, j
+
+
 @pytest.mark.parametrize("k,n,N", CASES)
 @pytest.mark.parametrize("double", [True, False])
 def test_preconditioner_fp64(k, n, N, double):
