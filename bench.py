@@ -480,7 +480,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--serve-nreq", type=int, default=40, help="requests of the mixed-k serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving stream (1/s)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "solve1"],
                     help="sweep: time hh_apply_preconditioner alone (4 columns) -- the profiling case")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--strips", type=int, default=32)
@@ -488,6 +488,22 @@ def main():
     args = ap.parse_args()
     if args.mode == "sweep":
         run_sweep_only(args)
+        return
+    if args.mode == "solve1":
+        # setup and one solve of the default workload, nothing else: the profiling case
+        import torch
+        import __graft_entry__
+        import paper_2408_11929_gb300 as hh
+        __graft_entry__.build()
+        w = hh_inputs.workload(WORKLOAD)
+        with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32") as h:
+            b = torch.from_numpy(h.assemble_rhs(w.sources[0])).cuda()
+            x, res = h.solve(b, tol=w.tol)
+            torch.cuda.synchronize()
+            st = h.stats()
+        print(json.dumps({"mode": "solve1", "iterations": res.iterations, "status": hh.STATUS_NAMES[res.status],
+                          "rel_res_explicit": res.rel_res_explicit, "kernel_launches": st["kernel_launches"]}),
+              flush=True)
         return
     if args.mode == "serve":
         import __graft_entry__
