@@ -114,6 +114,9 @@ typedef struct {
   int64_t wide_steps;      /* wide GEMM steps in one sweep of the last column count */
   int ns_blocks;           /* strip inverses computed by Newton-Schulz from the previous one */
   int ns_iterations;       /* their iterations (two GEMMs each) */
+  int tc_bnc, tc_nsplit;   /* autotuned tensor-core step for the last column count: complex
+                              columns per CTA (64 or 32) and K split (0 = fill the SMs) */
+  double tc_us;            /* its time per step when tuned (us) */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -538,6 +538,14 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->gs_flops = E.flops[Engine::K_GS];
   st->ns_blocks = E.ns_blocks;
   st->ns_iterations = E.ns_iterations;
+  {
+    const auto it = E.tc_tuned.find(E.last_columns);
+    if (it != E.tc_tuned.end()) {
+      st->tc_bnc = it->second.shape == 1 ? 32 : 64;
+      st->tc_nsplit = it->second.nsplit;
+      st->tc_us = it->second.us;
+    }
+  }
   for (const SweepStep& sp : E.opts.single_sweep ? E.steps_single : E.steps_double)
     st->wide_steps += (int64_t)(sp.ns * E.last_columns > 8);
   return HH_OK;

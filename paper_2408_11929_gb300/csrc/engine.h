@@ -68,13 +68,21 @@ class Engine {
   // boxes of the tensor-core step (16 and 18 rows), cached per (array, columns per strip)
   struct LineMaps {
     const void* ptr = nullptr;
-    int C = -1;
+    int C = -1, bnc = 0;
     CUtensorMap base{}, src{};
   };
-  LineMaps line_maps[6];
+  LineMaps line_maps[8];
   int line_maps_next = 0;
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
-  const LineMaps* line_maps_for(const void* buf, int C);
+  const LineMaps* line_maps_for(const void* buf, int C, int bnc);
+  // autotuned tensor-core step per column count: tile shape (0: 64 columns x 3 stages,
+  // 1: 32 columns x 4 stages) and K split (0 = fill the SMs)
+  struct TcChoice {
+    int shape = 0, nsplit = 0;
+    double us = 0;
+  };
+  std::map<int, TcChoice> tc_tuned;
+  int tune_tc(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes);
   // sweeps replayed as CUDA graphs (opts.use_graph), one per (arrays, columns, kind)
   struct SweepGraph {
     const void *rin, *v, *w, *partial;

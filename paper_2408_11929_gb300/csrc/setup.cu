@@ -296,8 +296,8 @@ static void setup_gemm(Engine& E, const typename Cx<R>::T* A, const typename Cx<
 // F_j = S^-1 by Newton-Schulz from X_0 = F_{j-1}.  Successive Schur complements of the strip
 // recursion are close (||I - S_j F_{j-1}||_2 between 0.04 and 0.14 from j = 2 on at k = 100
 // and 200, cond(S_j) about 6), so a few iterations of two GEMMs replace the pivoted
-// elimination.  Stops when the RMS entry of I - S X is at most 1e-6 (or stops decreasing
-// below 1e-4); returns false (F_j untouched beyond scratch use) when the start is not
+// elimination.  Stops when the RMS entry of I - S X is at most 2e-7, about the complex64
+// floor (or stops decreasing below 1e-4); returns false (F_j untouched beyond scratch use) when the start is not
 // contractive or 12 iterations do not converge, and the caller falls back to elimination.
 template <typename R>
 static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename Cx<R>::T* X0, typename Cx<R>::T* Fj,
@@ -319,7 +319,7 @@ static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename 
     double s = 0;
     for (int b = 0; b < nblk; ++b) s += part_host[b];
     const double rms = std::sqrt(s / ((double)m * m));
-    const bool done = rms <= 1e-6 || (rms < 1e-4 && rms > 0.5 * prev);
+    const bool done = rms <= 2e-7 || (rms < 1e-4 && rms > 0.5 * prev);
     if (it == 0 && std::sqrt(s) >= 0.9 * std::sqrt((double)m)) return false;  // not contractive
     if (done) {
       if (X != Fj) cudaMemcpyAsync(Fj, X, sizeof(T) * (size_t)m * ld, cudaMemcpyDeviceToDevice, E.stream);

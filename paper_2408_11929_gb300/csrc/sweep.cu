@@ -418,6 +418,32 @@ static double step_bytes(const Engine& E, const SweepStep& s, int C) {
                                          (s.out_mode != OUT_SET));
 }
 
+// One wide step on the tensor cores with tile shape CF and K split nsplit_req (0: split until
+// the SMs are filled); the K slices meet in split_reduce_kernel.
+template <class CF>
+static cudaError_t launch_tc_step(Engine& E, const LineOperand<float2>& op, int fblock, int C, int nsplit_req,
+                                  const void* Rin, void* partial_buf, size_t partial_bytes) {
+  const int ncols = op.ns * C;
+  const int gx = (E.m + tc::BM - 1) / tc::BM, gy = (ncols + CF::BNC - 1) / CF::BNC;
+  int nsplit = nsplit_req > 0 ? nsplit_req : std::max(1, std::min(8, (E.num_sms - 4) / (gx * gy)));
+  while (nsplit > 1 && (size_t)nsplit * E.m * ncols * sizeof(float2) > partial_bytes) --nsplit;
+  const int kchunk = ((E.m + nsplit - 1) / nsplit + tc::BKC - 1) / tc::BKC * tc::BKC;
+  nsplit = (E.m + kchunk - 1) / kchunk;  // no empty split
+  float2* partial = nsplit > 1 ? reinterpret_cast<float2*>(partial_buf) : nullptr;
+  const Engine::LineMaps* mb = E.line_maps_for(op.base ? op.base : Rin, C, CF::BNC);
+  const Engine::LineMaps* ms = E.line_maps_for(op.src ? op.src : Rin, C, CF::BNC);
+  if (!mb || !ms) return cudaErrorInvalidValue;
+  tc_line_gemm_kernel<CF><<<dim3(gx, gy, nsplit), tc::THREADS, CF::SMEM, E.stream>>>(
+      E.tmap_hi, E.tmap_lo, mb->base, ms->src, fblock, E.m, op, E.coef, kchunk, partial, E.err,
+      E.opts.timeout_cycles);
+  E.count_launch();
+  if (nsplit > 1) {
+    split_reduce_kernel<float><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(partial, nsplit, E.m, op);
+    E.count_launch();
+  }
+  return cudaSuccess;
+}
+
 template <typename R>
 static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, int C, bool single, void* partial_buf,
                                   size_t partial_bytes, bool allow_tick) {
@@ -433,9 +459,6 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
   constexpr size_t gemm_smem = line_gemm_smem<R, BM, BN, BK, STG>();
   auto gemm_fn = line_gemm_kernel<R, BM, BN, BK, 4, 4, STG>;
   cudaFuncSetAttribute((const void*)gemm_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem);
-  if (E.tc_ready)
-    cudaFuncSetAttribute((const void*)tc_line_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tc::SMEM);
   cudaFuncSetAttribute((const void*)line_gemv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)std::min<size_t>((size_t)E.m * 8 * sizeof(T), gemv_cap));
   // allow_tick: time the wide GEMM steps one by one (a sampled, eager sweep)
@@ -460,27 +483,15 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
                                                                                           E.coef);
       E.count_launch();
     } else if (std::is_same<R, float>::value && E.tc_ready && C % 2 == 0) {
-      // tensor-core step: 128 rows x 64 complex columns per CTA, K split to fill the SMs
-      const int gx = (E.m + tc::BM - 1) / tc::BM, gy = (ncols + tc::BNC - 1) / tc::BNC;
-      int nsplit = std::max(1, std::min(8, (E.num_sms - 4 + gx * gy - 1) / (gx * gy)));
-      while (nsplit > 1 && (size_t)nsplit * E.m * ncols * sizeof(T) > partial_bytes) --nsplit;
-      const int kchunk = ((E.m + nsplit - 1) / nsplit + tc::BKC - 1) / tc::BKC * tc::BKC;
-      nsplit = (E.m + kchunk - 1) / kchunk;  // no empty split
-      float2* partial = nsplit > 1 ? reinterpret_cast<float2*>(partial_buf) : nullptr;
       LineOperand<float2> opf;
       std::memcpy(&opf, &op, sizeof(opf));
-      const Engine::LineMaps* mb = E.line_maps_for(op.base ? op.base : Rin, C);
-      const Engine::LineMaps* ms = E.line_maps_for(op.src ? op.src : Rin, C);
-      if (!mb || !ms) return cudaErrorInvalidValue;
+      const auto it = E.tc_tuned.find(C);
+      const Engine::TcChoice ch = it != E.tc_tuned.end() ? it->second : Engine::TcChoice{};
       if (tick_gemm) E.tick_begin(Engine::K_GEMM);
-      tc_line_gemm_kernel<<<dim3(gx, gy, nsplit), tc::THREADS, tc::SMEM, E.stream>>>(
-          E.tmap_hi, E.tmap_lo, mb->base, ms->src, s.f, E.m, opf, E.coef, kchunk, partial, E.err,
-          E.opts.timeout_cycles);
-      E.count_launch();
-      if (nsplit > 1) {
-        split_reduce_kernel<float><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(partial, nsplit, E.m, opf);
-        E.count_launch();
-      }
+      const cudaError_t le = ch.shape == 1
+                                 ? launch_tc_step<tc::Narrow>(E, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes)
+                                 : launch_tc_step<tc::Wide>(E, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes);
+      if (le != cudaSuccess) return le;
       if (tick_gemm) E.tick_end(Engine::K_GEMM, step_bytes(E, s, C), 8.0 * E.m * E.m * (double)ncols);
     } else {
       const int gx = (E.m + BM - 1) / BM, gy = (ncols + BN - 1) / BN;
@@ -529,6 +540,10 @@ int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool sin
                               size_t partial_bytes, bool allow_graph) {
   // Every 8th sweep of a profiled handle times its GEMM steps one by one and so runs
   // eagerly; all other sweeps replay a captured graph of their launches.
+  if (precision == HH_PREC_FP32 && tc_ready && allow_graph && C % 2 == 0 && !tc_tuned.count(C)) {
+    const int rc = tune_tc(C, Rin, V, W, partial, partial_bytes);
+    if (rc) return rc;
+  }
   const bool sampled = opts.profile && (sweep_calls++ % 8 == 0);
   auto launch = [&](bool tick) {
     return precision == HH_PREC_FP32
@@ -644,22 +659,80 @@ int Engine::prepare_tensor_cores() {
       return HH_ECUDA;
     }
   }
+  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Wide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::Wide::SMEM);
+  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Narrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::Narrow::SMEM);
   tc_ready = true;
   return HH_OK;
 }
 
-const Engine::LineMaps* Engine::line_maps_for(const void* buf, int C) {
+// Autotuner of the tensor-core step for C columns per strip: one representative wide step
+// (all strips, coupled operand) is timed with CUDA events for each tile shape and K split
+// (one warm-up and three timed launches each, writing to a scratch array), and the fastest
+// is kept for every later sweep with this column count.
+int Engine::tune_tc(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes) {
+  const std::vector<SweepStep>& steps = opts.single_sweep ? steps_single : steps_double;
+  const SweepStep* pick = nullptr;
+  for (const SweepStep& s : steps)
+    if (s.ns == N && s.src != SB_NONE && (!pick || s.cpl > pick->cpl)) pick = &s;
+  if (!pick) {
+    tc_tuned[C] = TcChoice{};
+    return HH_OK;
+  }
+  void* tmp = nullptr;
+  if (dmalloc(&tmp, sweep_ws_bytes(C))) return HH_ENOMEM;
+  auto buf = [&](int b) -> float2* {
+    return b == SB_RIN ? (float2*)Rin : (b == SB_V ? (float2*)V : (b == SB_W ? (float2*)W : nullptr));
+  };
+  LineOperand<float2> op{};
+  op.base = buf(pick->base); op.base_j = pick->base_j;
+  op.src = buf(pick->src); op.src_j = pick->src_j; op.src_ds = pick->src_ds; op.cpl = pick->cpl; op.neg = pick->neg;
+  op.out = (float2*)tmp; op.out_j = pick->out_j; op.out_mode = OUT_SET;
+  op.acc = nullptr; op.acc_j = 0; op.acc_mode = 0;
+  op.s0 = pick->s0; op.ns = pick->ns; op.N = N; op.C = C;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  TcChoice best;
+  best.us = 1e30;
+  const int splits[4] = {0, 1, 2, 4};
+  for (int shape = 0; shape < 2; ++shape)
+    for (int ns : splits) {
+      auto run = [&]() {
+        return shape == 1 ? launch_tc_step<tc::Narrow>(*this, op, pick->f, C, ns, Rin, partial, partial_bytes)
+                          : launch_tc_step<tc::Wide>(*this, op, pick->f, C, ns, Rin, partial, partial_bytes);
+      };
+      if (run() != cudaSuccess) continue;
+      cudaEventRecord(a, stream);
+      for (int r = 0; r < 3; ++r) run();
+      cudaEventRecord(b, stream);
+      cudaEventSynchronize(b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      const double us = ms * 1e3 / 3;
+      if (us < best.us) best = TcChoice{shape, ns, us};
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaStreamSynchronize(stream);
+  dfree(tmp);
+  tc_tuned[C] = best;
+  return check_device_error("tensor-core autotune");
+}
+
+const Engine::LineMaps* Engine::line_maps_for(const void* buf, int C, int bnc) {
   for (const LineMaps& lm : line_maps)
-    if (lm.ptr == buf && lm.C == C) return &lm;
+    if (lm.ptr == buf && lm.C == C && lm.bnc == bnc) return &lm;
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(encode_fn);
   if (!encode || C % 2) return nullptr;
   LineMaps& lm = line_maps[line_maps_next];
-  line_maps_next = (line_maps_next + 1) % 6;
+  line_maps_next = (line_maps_next + 1) % 8;
   const cuuint64_t dims[3] = {(cuuint64_t)2 * N * C, (cuuint64_t)m, (cuuint64_t)(R + 1)};
   const cuuint64_t strides[2] = {(cuuint64_t)2 * N * C * sizeof(float), (cuuint64_t)m * 2 * N * C * sizeof(float)};
   const cuuint32_t estr[3] = {1, 1, 1};
-  const cuuint32_t box_b[3] = {(cuuint32_t)(2 * tc::BNC), (cuuint32_t)tc::RAW_BASE_ROWS, 1};
-  const cuuint32_t box_s[3] = {(cuuint32_t)(2 * tc::BNC), (cuuint32_t)tc::RAW_SRC_ROWS, 1};
+  const cuuint32_t box_b[3] = {(cuuint32_t)(2 * bnc), (cuuint32_t)tc::RAW_BASE_ROWS, 1};
+  const cuuint32_t box_s[3] = {(cuuint32_t)(2 * bnc), (cuuint32_t)tc::RAW_SRC_ROWS, 1};
   void* p = const_cast<void*>(buf);
   if (encode(&lm.base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p, dims, strides, box_b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -673,6 +746,7 @@ const Engine::LineMaps* Engine::line_maps_for(const void* buf, int C) {
   }
   lm.ptr = buf;
   lm.C = C;
+  lm.bnc = bnc;
   return &lm;
 }
 

@@ -12,7 +12,7 @@
 // accumulation in tensor memory (about 2^-21 relative per product, against 2^-24 for an FP32
 // FMA).  F's split is stored at setup; x is split while the B tile is built.
 //
-// CTA: 448 threads.  Lane 0 of warp 12 issues, per stage, four TMA loads on one mbarrier:
+// CTA: 320 threads.  Lane 0 of warp 12 issues, per stage, four TMA loads on one mbarrier:
 // the A tiles (hi, lo) and the raw line rows the stage's x is formed from (16 rows of the
 // base line, 18 rows of the coupled line with one halo row each side), the raw rows landing
 // in the slot's B area.  Eight warps build every stage's B tiles together (two node pairs
@@ -21,7 +21,9 @@
 // lo B tiles (128-byte swizzled, K-major).  Warp 8 also owns the tensor-memory allocation;
 // lane 0 of warp 9 issues the MMAs.  Epilogue: the eight warps move the accumulator (one row
 // per thread, two column halves) into a padded shared tile, then write whole rows with
-// coalesced 16-byte stores.  Three stages of 64 KB.  Every wait is
+// coalesced 16-byte stores.  Two tile shapes are compiled: 64 complex columns with three
+// 64 KB stages, and 32 columns with four 48 KB stages; the sweep's autotuner picks one per
+// column count.  Every wait is
 #pragma once
 #include <cuda.h>
 
@@ -31,25 +33,38 @@
 namespace hh {
 namespace tc {
 
-constexpr int BM = 128;             // rows of F per CTA = tensor-memory lanes
-constexpr int BNC = 64;             // complex columns per CTA
-constexpr int BN = 2 * BNC;         // MMA N: real-part rows then imaginary-part rows of B
-constexpr int BKC = 16;             // complex node indices per stage
-constexpr int STAGES = 3;
-constexpr int TILE = 128 * 128;     // bytes of one operand tile: 128 rows x 128 B
-constexpr int STAGE_BYTES = 4 * TILE;  // A hi, A lo, B hi, B lo
+constexpr int BM = 128;          // rows of F per CTA = tensor-memory lanes
+constexpr int BKC = 16;          // complex node indices per stage
+constexpr int TILE = 128 * 128;  // bytes of one A tile: 128 rows x 128 B
 constexpr int BUILDERS = 256;    // 8 warps: B tiles, then the epilogue
 constexpr int TMA_WARP = BUILDERS / 32, MMA_WARP = TMA_WARP + 1;
 constexpr int THREADS = BUILDERS + 64;
-constexpr int TMEM_COLS = 128;
-constexpr int RAW_ROW = BNC * 8;                  // bytes of one raw node row of the tile (complex64)
 constexpr int RAW_BASE_ROWS = BKC, RAW_SRC_ROWS = BKC + 2;
-constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 
-// instruction descriptor of kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
-// 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Tile shape: BNC complex columns per CTA (MMA N = 2 BNC), STAGES ring slots.  Two shapes are
+// compiled and the autotuner of the sweep picks one per column count.
+template <int BNC_, int STAGES_>
+struct Cfg {
+  static constexpr int BNC = BNC_;
+  static constexpr int BN = 2 * BNC_;  // real-part rows then imaginary-part rows of B
+  static constexpr int STAGES = STAGES_;
+  static constexpr int BTILE = BN * 128;  // bytes of one B tile: BN rows x 128 B
+  static constexpr int STAGE_BYTES = 2 * TILE + 2 * BTILE;  // A hi, A lo, B hi, B lo
+  static constexpr int PAIR_GROUPS = BUILDERS / BNC;                // threads per tile column
+  static constexpr int PAIRS_PER_THREAD = (BKC / 2) / PAIR_GROUPS;  // node pairs per thread per stage
+  static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;              // a power of two, at least 32
+  static constexpr int RAW_ROW = BNC * 8;  // bytes of one raw node row of the tile (complex64)
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+  // instruction descriptor of kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
+  // 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(PAIRS_PER_THREAD >= 1 && (BKC / 2) % PAIR_GROUPS == 0, "builder mapping");
+  static_assert(BNC % 32 == 0, "the epilogue moves 32 columns per tensor-memory load");
+  static_assert(SMEM <= 232448, "shared memory");
+};
+using Wide = Cfg<64, 3>;
+using Narrow = Cfg<32, 4>;
 
 // shared-memory matrix descriptor, K-major, 128-byte swizzle: start address >> 4 (bits
 // 0-13), leading offset unused by swizzled K-major layouts (1), stride offset between 8-row
@@ -81,11 +96,11 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 // 32 consecutive 32-bit columns of this thread's lane
@@ -128,12 +143,17 @@ __device__ __forceinline__ bool aborted(const int* flag) { return *(volatile con
 // count per strip C must be even (16-byte aligned rows).  With partial != nullptr the CTA
 // writes its slice to partial[(z * m + row) * ncols + col] for split_reduce_kernel, else it
 // applies the step's output modes itself.
+template <class CF>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     tc_line_gemm_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                         const __grid_constant__ CUtensorMap map_base, const __grid_constant__ CUtensorMap map_src,
                         int fblock, int m, LineOperand<float2> op, Coef cf, int kchunk, float2* __restrict__ partial,
                         int* err, long long budget) {
   using namespace tc;
+  constexpr int BNC = CF::BNC, BN = CF::BN, STAGES = CF::STAGES, BTILE = CF::BTILE;
+  constexpr int STAGE_BYTES = CF::STAGE_BYTES, PAIR_GROUPS = CF::PAIR_GROUPS;
+  constexpr int PAIRS_PER_THREAD = CF::PAIRS_PER_THREAD, TMEM_COLS = CF::TMEM_COLS, RAW_ROW = CF::RAW_ROW;
+  (void)BN;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   const uint32_t raw_s = smem_u32(tc_smem_raw);
   unsigned char* sm = tc_smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);
@@ -218,13 +238,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         if (tc::aborted(abort_s)) break;
         tc::fence_after();
         const uint32_t a_hi = smem_u32(sm + (size_t)s * STAGE_BYTES);
-        const uint32_t a_lo = a_hi + TILE, b_hi = a_hi + 2 * TILE, b_lo = a_hi + 3 * TILE;
+        const uint32_t a_lo = a_hi + TILE, b_hi = a_hi + 2 * TILE, b_lo = b_hi + BTILE;
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {  // K = 8 TF32 values (32 bytes) per MMA
           const uint32_t off = kk * 32;
-          tc::mma_tf32(tmem, tc::sw128_desc(a_hi + off), tc::sw128_desc(b_hi + off), (kt | kk) != 0);
-          tc::mma_tf32(tmem, tc::sw128_desc(a_hi + off), tc::sw128_desc(b_lo + off), 1);
-          tc::mma_tf32(tmem, tc::sw128_desc(a_lo + off), tc::sw128_desc(b_hi + off), 1);
+          tc::mma_tf32(tmem, tc::sw128_desc(a_hi + off), tc::sw128_desc(b_hi + off), CF::IDESC, (kt | kk) != 0);
+          tc::mma_tf32(tmem, tc::sw128_desc(a_hi + off), tc::sw128_desc(b_lo + off), CF::IDESC, 1);
+          tc::mma_tf32(tmem, tc::sw128_desc(a_lo + off), tc::sw128_desc(b_hi + off), CF::IDESC, 1);
         }
         tc::commit(&empty[s]);
       }
@@ -232,8 +252,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     }
   } else {
     // ---------------------------------------------------------------- B builders
-    const int c = threadIdx.x & (BNC - 1);  // complex column within the tile
-    const int pg = threadIdx.x >> 6;        // this thread builds node pairs pg and pg + 4 of a stage
+    const int c = threadIdx.x % BNC;  // complex column within the tile
+    const int pg = threadIdx.x / BNC;  // this thread forms node pairs pg, pg + PAIR_GROUPS, ... of a stage
     const bool cvalid = colc0 + c < ncols;
     const double2 ve = cf.vert(0), vi = cf.vert(1);
     const float2 vert_edge = make_float2((float)ve.x, (float)ve.y), vert_int = make_float2((float)vi.x, (float)vi.y);
@@ -257,14 +277,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       }
       const int k0 = kbeg + kt * BKC;
       unsigned char* bh = sm + (size_t)s * STAGE_BYTES + 2 * TILE;
-      unsigned char* bl = bh + TILE;
+      unsigned char* bl = bh + BTILE;
       // raw rows from shared memory: base row k - k0, coupled row k - k0 + 1
       const float2* rb = reinterpret_cast<const float2*>(bh);
       const float2* rs = reinterpret_cast<const float2*>(bh + RAW_BASE_ROWS * RAW_ROW);
-      float2 x[4];
+      float2 x[2 * PAIRS_PER_THREAD];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int kk = 2 * (pg + 4 * (u >> 1)) + (u & 1);  // node within the stage
+      for (int u = 0; u < 2 * PAIRS_PER_THREAD; ++u) {
+        const int kk = 2 * (pg + PAIR_GROUPS * (u >> 1)) + (u & 1);  // node within the stage
         const int k = k0 + kk;
         float2 v = has_base ? rb[kk * BNC + c] : make_float2(0.f, 0.f);
         if (has_src) {
@@ -285,8 +305,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       // every builder has read its raw rows before any of them is overwritten
       asm volatile("bar.sync 1, %0;" ::"n"(BUILDERS) : "memory");
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int j = pg + 4 * q;  // 16-byte chunk = node pair within the stage
+      for (int q = 0; q < PAIRS_PER_THREAD; ++q) {
+        const int j = pg + PAIR_GROUPS * q;  // 16-byte chunk = node pair within the stage
         const float2 x0 = x[2 * q], x1 = x[2 * q + 1];
         const float re4[4] = {x0.x, -x0.y, x1.x, -x1.y};
         const float im4[4] = {x0.y, x0.x, x1.y, x1.x};
@@ -313,7 +333,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     tc::fence_after();
     float2* stile = reinterpret_cast<float2*>(sm);
     constexpr int SROW = BNC + 2;  // row stride (complex) of the staging tile
-    {
+    if ((warp >> 2) < BNC / 32) {
       const int wq = warp & 3;       // tensor-memory lane quarter of this warp
       const int r = wq * 32 + lane;  // accumulator row
       const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16);
@@ -331,12 +351,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     asm volatile("bar.sync 2, %0;" ::"n"(BUILDERS) : "memory");
     if (ok && !tc::aborted(abort_s)) {
       const int N = op.N, C = op.C;
-      // one warp per row: lane l holds complex columns 2l, 2l + 1
-      for (int r = warp; r < BM; r += BUILDERS / 32) {
+      // BNC / 2 lanes per row, each with complex columns 2l, 2l + 1
+      constexpr int LPR = BNC / 2, RPW = 32 / LPR;  // lanes per row, rows per warp pass
+      for (int r = warp * RPW + lane / LPR; r < BM; r += (BUILDERS / 32) * RPW) {
+        const int l = lane % LPR;
         const int gr = row0 + r;
-        const int gc = colc0 + 2 * lane;
+        const int gc = colc0 + 2 * l;
         if (gr >= m || gc >= ncols) continue;
-        const float4 v = *reinterpret_cast<const float4*>(stile + r * SROW + 2 * lane);
+        const float4 v = *reinterpret_cast<const float4*>(stile + r * SROW + 2 * l);
         const float2 z0 = make_float2(v.x, v.y), z1 = make_float2(v.z, v.w);
         if (partial) {
           float2* p = partial + ((size_t)blockIdx.z * m + gr) * ncols + gc;
