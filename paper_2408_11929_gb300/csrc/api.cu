@@ -177,8 +177,10 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   cudaEventRecord(a, stream);
-  int rc = factor();
+  int rc = load_encoder();
+  if (rc == HH_OK) rc = factor();
   if (rc == HH_OK) rc = prepare_tensor_cores();
+  free_dense_scratch();
   cudaEventRecord(b, stream);
   cudaEventSynchronize(b);
   float t_ms = 0;
@@ -207,6 +209,7 @@ Engine::~Engine() {
   dfree(factors); dfree(bar); dfree(err);
   dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial);
   dfree(factors_hi); dfree(factors_lo);
+  free_dense_scratch();
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 

@@ -64,6 +64,22 @@ class Engine {
   CUtensorMap tmap_hi{}, tmap_lo{};
   bool tc_ready = false;
   int prepare_tensor_cores();  // sweep.cu
+  // Dense complex64 GEMM C = A B (or A (-B)) of m x m blocks (leading dimension ldf) on the
+  // tensor cores, for the setup: A is split into TF32 hi / lo scratch, B's rows are the
+  // kernel's line operand.  load_encoder() must have succeeded.
+  int load_encoder();
+  bool tc_dense_ok() const { return encode_fn != nullptr; }
+  int tc_dense_gemm(const void* A, const void* B, void* C, bool negate_b, bool add = false);
+  void free_dense_scratch();
+  void* dense_hi = nullptr;
+  void* dense_lo = nullptr;
+  CUtensorMap dense_map_hi{}, dense_map_lo{};
+  struct DenseMaps {
+    const void* ptr = nullptr;
+    CUtensorMap base{}, src{};
+  };
+  DenseMaps dense_maps[4];
+  int dense_maps_next = 0;
   // 3-D views of a sweep array (floats of a node row, node rows, lines) with the raw-row
   // boxes of the tensor-core step (16 and 18 rows), cached per (array, columns per strip)
   struct LineMaps {

@@ -230,6 +230,8 @@ int interface_blocks(Engine& E, typename Cx<R>::T* bufA, typename Cx<R>::T* bufB
   for (int j = 1; j <= Rr - 1; ++j) {
     lmul_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(Y, Z, m, ld, E.coef);
     E.tick_begin(Engine::K_SETUP);
+    // the recursion chains R - 1 products, so it stays on the exact complex64 / complex128
+    // GEMM: TF32 x 3 products here doubled the sweep's error at n = 256
     if constexpr (sizeof(R) == 4) {  // 64 x 64 tiles (33 KB of shared memory for complex64)
       dim3 grid((m + 63) / 64, (m + 63) / 64);
       dense_gemm_kernel<R, 64, 64, 4, 4><<<grid, 256, 0, E.stream>>>(F + (size_t)j * blk, ld, Z, ld, Yn[j & 1], ld, m,
@@ -257,7 +259,8 @@ int interface_blocks(Engine& E, typename Cx<R>::T* bufA, typename Cx<R>::T* bufB
 // block writes its part of ||I - T||_F^2 to part[blockIdx.x] (summed on the host in a fixed
 // order, so the iteration count does not depend on the schedule).
 template <typename R>
-__global__ void ns_residual_kernel(typename Cx<R>::T* __restrict__ Tm, int ld, int m, double* __restrict__ part) {
+__global__ void ns_residual_kernel(typename Cx<R>::T* __restrict__ Tm, int ld, int m, double* __restrict__ part,
+                                   double shift = 2.0) {
   double acc = 0;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)m * m;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -265,7 +268,7 @@ __global__ void ns_residual_kernel(typename Cx<R>::T* __restrict__ Tm, int ld, i
     auto& t = Tm[(size_t)i * ld + c];
     const double ex = (i == c ? 1.0 : 0.0) - (double)t.x, ey = -(double)t.y;
     acc += ex * ex + ey * ey;
-    t.x = (R)((i == c ? 2.0 : 0.0) - (double)t.x);
+    t.x = (R)((i == c ? shift : 0.0) - (double)t.x);
     t.y = -t.y;
   }
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -279,10 +282,15 @@ __global__ void ns_residual_kernel(typename Cx<R>::T* __restrict__ Tm, int ld, i
   }
 }
 
-// complex64 C = A B (m x m, leading dimension ld) on the CUDA-core GEMM of the setup
+// C = A B (m x m, leading dimension ld): complex64 on the tensor cores when they are in use,
+// else on the CUDA-core GEMM of the setup
 template <typename R>
 static void setup_gemm(Engine& E, const typename Cx<R>::T* A, const typename Cx<R>::T* B, typename Cx<R>::T* C) {
   const int m = E.m, ld = E.ldf;
+  if (sizeof(R) == 4 && E.tc_dense_ok()) {
+    E.tc_dense_gemm(A, B, C, false);
+    return;
+  }
   if constexpr (sizeof(R) == 4) {
     dim3 grid((m + 63) / 64, (m + 63) / 64);
     dense_gemm_kernel<R, 64, 64, 4, 4><<<grid, 256, 0, E.stream>>>(A, ld, B, ld, C, ld, m, 1.0);
@@ -298,7 +306,9 @@ static void setup_gemm(Engine& E, const typename Cx<R>::T* A, const typename Cx<
 // and 200, cond(S_j) about 6), so a few iterations of two GEMMs replace the pivoted
 // elimination.  Stops when the RMS entry of I - S X is at most 2e-7, about the complex64
 // floor (or stops decreasing below 1e-4); returns false (F_j untouched beyond scratch use) when the start is not
-// contractive or 12 iterations do not converge, and the caller falls back to elimination.
+// contractive or 16 iterations do not converge, and the caller falls back to elimination.
+// With tensor cores the GEMMs are TF32 x 3 (about 2^-21 per product), which sets the floor
+// the iteration stops at.
 template <typename R>
 static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename Cx<R>::T* X0, typename Cx<R>::T* Fj,
                           typename Cx<R>::T* Tb, typename Cx<R>::T* Xb, double* part_dev, double* part_host,
@@ -310,7 +320,7 @@ static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename 
   T* bufs[2] = {Fj, Xb};
   double prev = 1e300;
   iters = 0;
-  for (int it = 0; it < 12; ++it) {
+  for (int it = 0; it < 16; ++it) {
     setup_gemm<R>(E, S, X, Tb);
     ns_residual_kernel<R><<<nblk, 256, 0, E.stream>>>(Tb, ld, m, part_dev);
     E.count_launch();
@@ -323,6 +333,19 @@ static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename 
     if (it == 0 && std::sqrt(s) >= 0.9 * std::sqrt((double)m)) return false;  // not contractive
     if (done) {
       if (X != Fj) cudaMemcpyAsync(Fj, X, sizeof(T) * (size_t)m * ld, cudaMemcpyDeviceToDevice, E.stream);
+      if constexpr (sizeof(R) == 4) {
+        if (E.tc_dense_ok()) {
+          // The TF32 x 3 products leave X at their floor (about 1e-6).  One refinement step
+          // restores complex64 accuracy: the residual I - S X from the exact complex64 GEMM,
+          // and the small correction X (I - S X) on the tensor cores added to X.
+          const int m_ = E.m;
+          dim3 grid((m_ + 63) / 64, (m_ + 63) / 64);
+          dense_gemm_kernel<R, 64, 64, 4, 4><<<grid, 256, 0, E.stream>>>(S, ld, Fj, ld, Tb, ld, m_, 1.0);
+          ns_residual_kernel<R><<<nblk, 256, 0, E.stream>>>(Tb, ld, m, part_dev, 1.0);
+          E.count_launch(2);
+          if (E.tc_dense_gemm(Fj, Tb, Fj, false, true) != HH_OK) return false;
+        }
+      }
       return true;
     }
     if (it > 2 && rms > prev) return false;  // diverging
@@ -374,7 +397,7 @@ int factor_impl(Engine& E) {
     E.tick_begin(Engine::K_SETUP);
     schur_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(X, ld, j ? 1 : 0, type, E.coef, bufA, ld, m, col);
     E.count_launch();
-    if (use_ns && j >= 2) {
+    if (use_ns && j >= (E.tc_dense_ok() ? 1 : 2)) {
       int iters = 0;
       if (newton_schulz<R>(E, bufA, X, F + (size_t)j * m * ld, bufC, bufD, part_dev, part_host, iters)) {
         E.tick_end(Engine::K_SETUP, 0.0, (2.0 * iters + 1) * 8.0 * m * (double)m * m);

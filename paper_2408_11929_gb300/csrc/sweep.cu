@@ -627,14 +627,9 @@ __global__ void tf32_split_kernel(const float* __restrict__ F, float* __restrict
   }
 }
 
-int Engine::prepare_tensor_cores() {
+int Engine::load_encoder() {
   if (precision != HH_PREC_FP32 || !opts.tensor_cores) return HH_OK;
-  const size_t nfloat = (size_t)factor_blocks() * m * ldf * 2;
-  if (dmalloc(&factors_hi, nfloat * sizeof(float)) || dmalloc(&factors_lo, nfloat * sizeof(float))) return HH_ENOMEM;
-  tf32_split_kernel<<<grid_for(nfloat), 256, 0, stream>>>(reinterpret_cast<const float*>(factors),
-                                                         reinterpret_cast<float*>(factors_hi),
-                                                         reinterpret_cast<float*>(factors_lo), nfloat);
-  count_launch();
+  if (encode_fn) return HH_OK;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -644,7 +639,94 @@ int Engine::prepare_tensor_cores() {
     return HH_ECUDA;
   }
   encode_fn = fn;
-  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Wide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::Wide::SMEM);
+  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Narrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::Narrow::SMEM);
+  return HH_OK;
+}
+
+void Engine::free_dense_scratch() {
+  dfree(dense_hi);
+  dfree(dense_lo);
+  dense_hi = dense_lo = nullptr;
+  for (DenseMaps& d : dense_maps) d.ptr = nullptr;
+}
+
+int Engine::tc_dense_gemm(const void* A, const void* B, void* C, bool negate_b, bool add) {
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(encode_fn);
+  if (!encode) return (set_error("tensor-map encoder not loaded"), HH_ECUDA);
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * m, (cuuint64_t)m, 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)ldf * 2 * sizeof(float), (cuuint64_t)m * ldf * 2 * sizeof(float)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (!dense_hi) {
+    const size_t bytes = (size_t)m * ldf * 2 * sizeof(float);
+    if (dmalloc(&dense_hi, bytes) || dmalloc(&dense_lo, bytes)) return HH_ENOMEM;
+    const cuuint32_t box[3] = {32, (cuuint32_t)tc::BM, 1};
+    for (int h = 0; h < 2; ++h)
+      if (encode(h ? &dense_map_lo : &dense_map_hi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h ? dense_lo : dense_hi, dims,
+                 strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return (set_error("cuTensorMapEncodeTiled failed for the setup scratch"), HH_ECUDA);
+  }
+  // B viewed as rows of 2 ldf floats (the line operand of the step kernel, one line)
+  DenseMaps* dm = nullptr;
+  for (DenseMaps& d : dense_maps)
+    if (d.ptr == B) dm = &d;
+  if (!dm) {
+    dm = &dense_maps[dense_maps_next];
+    dense_maps_next = (dense_maps_next + 1) % 4;
+    const cuuint64_t bd[3] = {(cuuint64_t)2 * ldf, (cuuint64_t)m, 1};
+    const cuuint32_t box_b[3] = {(cuuint32_t)(2 * tc::Wide::BNC), (cuuint32_t)tc::RAW_BASE_ROWS, 1};
+    const cuuint32_t box_s[3] = {(cuuint32_t)(2 * tc::Wide::BNC), (cuuint32_t)tc::RAW_SRC_ROWS, 1};
+    void* p = const_cast<void*>(B);
+    if (encode(&dm->base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p, bd, strides, box_b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        encode(&dm->src, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p, bd, strides, box_s, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      dm->ptr = nullptr;
+      return (set_error("cuTensorMapEncodeTiled failed for a setup matrix"), HH_ECUDA);
+    }
+    dm->ptr = B;
+  }
+  const size_t nfloat = (size_t)m * ldf * 2;
+  tf32_split_kernel<<<grid_for(nfloat), 256, 0, stream>>>(reinterpret_cast<const float*>(A),
+                                                         reinterpret_cast<float*>(dense_hi),
+                                                         reinterpret_cast<float*>(dense_lo), nfloat);
+  LineOperand<float2> op{};
+  if (negate_b) {  // x = 0 - identity(B)
+    op.src = reinterpret_cast<const float2*>(B);
+    op.cpl = XC_IDENT;
+    op.neg = 1;
+  } else {
+    op.base = reinterpret_cast<const float2*>(B);
+    op.cpl = XC_NONE;
+  }
+  op.out = reinterpret_cast<float2*>(C);
+  op.out_mode = add ? OUT_ADD : OUT_SET;
+  op.s0 = 0; op.ns = m; op.N = ldf; op.C = 1;  // a node row = one row of the matrix
+  const int gx = (m + tc::BM - 1) / tc::BM, gy = (m + tc::Wide::BNC - 1) / tc::Wide::BNC;
+  const int kchunk = (m + tc::BKC - 1) / tc::BKC * tc::BKC;
+  tc_line_gemm_kernel<tc::Wide><<<dim3(gx, gy, 1), tc::THREADS, tc::Wide::SMEM, stream>>>(
+      dense_map_hi, dense_map_lo, dm->base, dm->src, 0, m, op, coef, kchunk, nullptr, err, opts.timeout_cycles);
+  count_launch(2);
+  return HH_OK;
+}
+
+int Engine::prepare_tensor_cores() {
+  if (precision != HH_PREC_FP32 || !opts.tensor_cores) return HH_OK;
+  int rc = load_encoder();
+  if (rc) return rc;
+  free_dense_scratch();
+  const size_t nfloat = (size_t)factor_blocks() * m * ldf * 2;
+  if (dmalloc(&factors_hi, nfloat * sizeof(float)) || dmalloc(&factors_lo, nfloat * sizeof(float))) return HH_ENOMEM;
+  tf32_split_kernel<<<grid_for(nfloat), 256, 0, stream>>>(reinterpret_cast<const float*>(factors),
+                                                         reinterpret_cast<float*>(factors_hi),
+                                                         reinterpret_cast<float*>(factors_lo), nfloat);
+  count_launch();
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(encode_fn);
   // rows of 2m floats (interleaved complex), m rows per block, factor_blocks() blocks
   const cuuint64_t dims[3] = {(cuuint64_t)2 * m, (cuuint64_t)m, (cuuint64_t)factor_blocks()};
   const cuuint64_t strides[2] = {(cuuint64_t)ldf * 2 * sizeof(float), (cuuint64_t)m * ldf * 2 * sizeof(float)};
@@ -659,10 +741,6 @@ int Engine::prepare_tensor_cores() {
       return HH_ECUDA;
     }
   }
-  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Wide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tc::Wide::SMEM);
-  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Narrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tc::Narrow::SMEM);
   tc_ready = true;
   return HH_OK;
 }
