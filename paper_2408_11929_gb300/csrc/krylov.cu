@@ -69,6 +69,32 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* 32 * NV
   __syncthreads();
 }
 
+// Sum of 32 values over the threads of a block, reduce-scatter style: at each of the five
+// warp levels a lane keeps half of its values and receives the partner's half of them, so a
+// lane adds 16 + 8 + 4 + 2 + 1 = 31 values instead of 5 x 32 (the adds run on the FP64 pipe,
+// the bottleneck of the Gram-Schmidt kernels).  Lane q of the warp ends with value q; the
+// warps meet in shared memory and thread q < 32 returns the block's sum of value q.
+__device__ __forceinline__ double block_sum32_scatter(double (&v)[32], double* sh /* 32 x warps */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const double send = upper ? v[i] : v[i + h];
+      const double keep = upper ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  __syncthreads();
+  sh[wid * 32 + lane] = v[0];
+  __syncthreads();
+  double r = 0;
+  if (threadIdx.x < 32)
+    for (int w = 0; w < nw; ++w) r += sh[w * 32 + threadIdx.x];
+  return r;
+}
+
 // ------------------------------------------------------------------ operator
 __global__ void spmv_kernel(const double2* __restrict__ x, double2* __restrict__ y, int ncols, Coef cf) {
   const int n = cf.n, m = n + 1;
@@ -253,7 +279,7 @@ __global__ void __launch_bounds__(256) gs_dot_kernel(KState S, const double2* __
   const size_t chunk = (D + S.GX - 1) / S.GX;
   const size_t g0 = blockIdx.x * chunk, g1 = min(D, g0 + chunk);
   const double2* Wr = W + (size_t)r * TT * D;
-  __shared__ double sh[32 * AB * TT * 2];
+  __shared__ double sh[32 * (AB * TT * 2 > 8 ? AB * TT * 2 : 8)];
   for (int a0 = 0; a0 < nV; a0 += AB) {
     double acc[AB * TT * 2];
 #pragma unroll
@@ -278,15 +304,27 @@ __global__ void __launch_bounds__(256) gs_dot_kernel(KState S, const double2* __
         }
       }
     }
-    block_sum<AB * TT * 2>(acc, sh);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int ab = 0; ab < AB; ++ab) {
+    if constexpr (AB * TT * 2 == 32) {
+      // value q = (ab TT + b) 2 + part lands on thread q
+      const double sum = block_sum32_scatter(acc, sh);
+      if (threadIdx.x < 32) {
+        const int q = threadIdx.x, ab = q / (TT * 2), b = (q / 2) % TT, part = q & 1;
         if (a0 + ab < nV) {
+          const size_t p = ((size_t)r * S.maxV + a0 + ab) * TT + b;
+          reinterpret_cast<double*>(&S.Hpart[p * S.GX + blockIdx.x])[part] = sum;
+        }
+      }
+    } else {
+      block_sum<AB * TT * 2>(acc, sh);
+      if (threadIdx.x == 0) {
 #pragma unroll
-          for (int b = 0; b < TT; ++b) {
-            const size_t p = ((size_t)r * S.maxV + a0 + ab) * TT + b;
-            S.Hpart[p * S.GX + blockIdx.x] = make_double2(acc[(ab * TT + b) * 2], acc[(ab * TT + b) * 2 + 1]);
+        for (int ab = 0; ab < AB; ++ab) {
+          if (a0 + ab < nV) {
+#pragma unroll
+            for (int b = 0; b < TT; ++b) {
+              const size_t p = ((size_t)r * S.maxV + a0 + ab) * TT + b;
+              S.Hpart[p * S.GX + blockIdx.x] = make_double2(acc[(ab * TT + b) * 2], acc[(ab * TT + b) * 2 + 1]);
+            }
           }
         }
       }
