@@ -68,8 +68,11 @@ typedef struct {
   int bcr_depth;          /* reserved: 0 = block Thomas strip solves (the only value accepted) */
   int64_t timeout_cycles; /* SM clock budget of every device-side wait (default 4e9) */
   void* stream;           /* cudaStream_t to run on, or NULL for the handle's own stream */
-  int use_graph;          /* 1 (default): each sweep (its 200-odd dependent launches) is captured
-                             once per array set and column count and replayed as a CUDA graph */
+  int use_graph;          /* 1 (default): every Arnoldi step (table gather, pack, the sweep's
+                             200-odd dependent launches, unpack, operator, Gram-Schmidt, block QR,
+                             Givens update, next sources) is captured once per number of active
+                             right-hand sides and replayed as a CUDA graph; sweeps run on their own
+                             (hh_apply_preconditioner) are captured the same way */
   int profile;            /* 1: time every kernel class with CUDA events (hh_get_stats) */
   int gs_passes;          /* Gram-Schmidt passes against the basis and within the new block:
                              2 (default, CGS2) or 1 (the single pass whose inner products
@@ -117,6 +120,8 @@ typedef struct {
   int tc_bnc, tc_nsplit;   /* autotuned tensor-core step for the last column count: complex
                               columns per CTA (64 or 32) and K split (0 = fill the SMs) */
   double tc_us;            /* its time per step when tuned (us) */
+  int64_t iterations_total; /* Arnoldi steps run, timed or replayed from their graph (with
+                               opts.profile the classes above time every 8th step) */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

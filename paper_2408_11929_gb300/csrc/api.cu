@@ -541,6 +541,7 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->gs_flops = E.flops[Engine::K_GS];
   st->ns_blocks = E.ns_blocks;
   st->ns_iterations = E.ns_iterations;
+  st->iterations_total = E.iterations_total;
   {
     const auto it = E.tc_tuned.find(E.last_columns);
     if (it != E.tc_tuned.end()) {
@@ -562,6 +563,7 @@ void hh_reset_stats(hh_handle* h) {
     E.launches[c] = 0; E.ms[c] = 0; E.bytes[c] = 0; E.flops[c] = 0;
   }
   E.kernel_launches = 0;
+  E.iterations_total = 0;
 }
 
 hh_status hh_submit(hh_handle* h, const double* rhs, double* x, double tol, hh_ticket* ticket) {

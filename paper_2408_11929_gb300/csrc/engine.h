@@ -130,6 +130,7 @@ class Engine {
   int last_columns = 0;
   int64_t sweep_calls = 0;
   int ns_blocks = 0, ns_iterations = 0;  // strip inverses by Newton-Schulz, and its iterations
+  int64_t iterations_total = 0;           // Arnoldi steps run (timed or replayed)
   Tick cur_tick[K_NCLASS];
   bool tick_open[K_NCLASS] = {false, false, false, false, false, false};
 
@@ -173,6 +174,10 @@ class Engine {
   int run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool single, void* partial,
                         size_t partial_bytes, bool allow_graph = true);
   int apply_preconditioner_noalloc(int dcode, int ncols, const double2* r, double2* z, bool single);
+  // the launches of one sweep, untimed and without a graph of their own (for captures)
+  int sweep_inline(const void* Rin, void* V, void* W, int C, bool single);
+  // runs the tensor-core autotuner for C columns per strip if it has not run yet
+  int ensure_tuned(int C);
   size_t sweep_elem() const { return precision == HH_PREC_FP32 ? 8 : 16; }
   size_t sweep_ws_bytes(int C) const;          // bytes of one packed sweep array
   double sweep_flops(int C, bool single) const;

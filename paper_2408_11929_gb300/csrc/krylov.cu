@@ -728,6 +728,16 @@ struct SlotSolver::Impl {
   std::vector<void*> owned;
   double2* W = nullptr;       // S * t * D operator outputs / residual scratch
   unsigned* qbar = nullptr;   // per-slot barrier counters of the block QR
+  // captured Arnoldi steps, one per number of active slots
+  struct StepGraph {
+    int nact;
+    cudaGraphExec_t exec;
+    int64_t kernels;
+  };
+  std::vector<StepGraph> step_graphs;
+  bool step_graph_broken = false;
+  int64_t iter_calls = 0;
+  static constexpr int HH_EAGAIN_STEP = -1000;
   double2* xstage = nullptr;  // S * D solutions of slots whose caller buffer is host memory
   int* d_act = nullptr;
   IterTables T{};
@@ -750,6 +760,7 @@ struct SlotSolver::Impl {
   explicit Impl(Engine& e) : E(e) {}
   ~Impl() {
     cudaStreamSynchronize(E.stream);
+    for (auto& g : step_graphs) cudaGraphExecDestroy(g.exec);
     for (void* p : owned) E.dfree(p);
     for (void* p : pool) E.dfree(p);
     for (auto& sl : slots)
@@ -888,13 +899,13 @@ struct SlotSolver::Impl {
 
   template <int TT>
   // nv: basis vectors of all active slots (each projected against its t new columns)
-  void gs_and_qr(cudaError_t& ce, double nv) {
+  void gs_and_qr(cudaError_t& ce, double nv, bool tick) {
     dim3 gsgrid(K.GX, S);
     for (int pass = 0; pass < K.passes; ++pass) {
-      E.tick_begin(Engine::K_GSDOT);
+      if (tick) E.tick_begin(Engine::K_GSDOT);
       gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K, W);
       // one complex multiply-add (8 real flops) per basis element and new column
-      E.tick_end(Engine::K_GSDOT, nv * D * 16.0 + (double)t * D * 16.0 * nv / 4.0, 8.0 * nv * t * D);
+      if (tick) E.tick_end(Engine::K_GSDOT, nv * D * 16.0 + (double)t * D * 16.0 * nv / 4.0, 8.0 * nv * t * D);
       gs_reduce_kernel<<<S, 256, 0, E.stream>>>(K, pass == 0);
       const size_t smem = (size_t)K.maxV * TT * sizeof(double2) + (size_t)K.maxV * sizeof(void*);
       cudaFuncSetAttribute((const void*)gs_update_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -931,36 +942,21 @@ struct SlotSolver::Impl {
       cudaMemcpyAsync(K.Zcur, h_zcur, sizeof(double2*) * S, cudaMemcpyHostToDevice, E.stream);
       cudaMemcpyAsync(K.Vcur, h_vcur, sizeof(double2*) * S, cudaMemcpyHostToDevice, E.stream);
       cudaMemcpyAsync(d_act, h_act, sizeof(int) * nact, cudaMemcpyHostToDevice, E.stream);
-      gather_tables_kernel<<<1, 256, 0, E.stream>>>(K, d_act, nact, T, W);
-      E.count_launch();
-      const int C = nact * t;
-      launch_pack(E, T.src, T.scale, C, t, codes, E.w_rin);
-      int rc = E.run_sweep(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0);
-      if (rc) return rc;
-      launch_unpack_tab(E, E.w_v, C, t, codes, T.zdst);
-      E.tick_begin(Engine::K_SPMV);
-      spmv_tab_kernel<<<E.grid_for(D * C), 256, 0, E.stream>>>(T.zdst, T.wdst, C, E.coef);
-      E.count_launch();
-      E.tick_end(Engine::K_SPMV, 2.0 * C * D * 16.0, 0);
       double nv = 0;  // basis vectors of the active slots before this iteration's block
       for (int a = 0; a < nact; ++a) nv += 1.0 + (double)(slots[h_act[a]].blocks.size() / 2 - 1) * t;
-      E.tick_begin(Engine::K_GS);
-      cudaError_t ce = cudaSuccess;
-      switch (t) {
-        case 1: gs_and_qr<1>(ce, nv); break;
-        case 2: gs_and_qr<2>(ce, nv); break;
-        case 3: gs_and_qr<3>(ce, nv); break;
-        default: gs_and_qr<4>(ce, nv); break;
+      // Every 8th iteration of a profiled handle runs eagerly with its kernels timed one class
+      // at a time; the others replay the captured step for this number of active slots.
+      const bool timed = !E.opts.use_graph || step_graph_broken || (E.opts.profile && iter_calls % 8 == 0);
+      ++iter_calls;
+      ++E.iterations_total;
+      int rc = HH_OK;
+      if (!timed) rc = replay_step(nact, nv);
+      if (timed || rc == HH_EAGAIN_STEP) {
+        cudaError_t ce = cudaSuccess;
+        rc = enqueue_step(nact, nv, true, ce);
+        if (ce != cudaSuccess) return (E.set_cuda_error(ce, "qr launch"), HH_ECUDA);
       }
-      E.tick_end(Engine::K_GS, K.passes * (2.0 * nv * D * 16 + 3.0 * C * D * 16) + 6.0 * C * D * 16,
-                 K.passes * 16.0 * nv * t * D);
-      if (ce != cudaSuccess) return (E.set_cuda_error(ce, "qr launch"), HH_ECUDA);
-      const size_t hsmem = (size_t)(K.maxZ + 2) * sizeof(double2);
-      cudaFuncSetAttribute((const void*)hess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
-      hess_kernel<<<S, 32, hsmem, E.stream>>>(K);
-      source_sum_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K);
-      source_final_kernel<<<S, 32, 0, E.stream>>>(K);
-      E.count_launch(3);
+      if (rc) return rc;
     }
     cudaMemcpyAsync(h_done, K.done, sizeof(int) * S, cudaMemcpyDeviceToHost, E.stream);
     cudaError_t se = cudaStreamSynchronize(E.stream);
@@ -968,6 +964,84 @@ struct SlotSolver::Impl {
     int rc = E.check_device_error("iteration");
     if (rc) return rc;
     return finalize(out);
+  }
+
+  // The kernels of one iteration for nact active slots (their tables already on the device).
+  // timed: eager, with the per-class timing and the sweep as its own graph; otherwise the
+  // launches are being captured, so the sweep is launched inline and nothing is timed.
+  int enqueue_step(int nact, double nv, bool timed, cudaError_t& ce) {
+    const int C = nact * t;
+    gather_tables_kernel<<<1, 256, 0, E.stream>>>(K, d_act, nact, T, W);
+    E.count_launch();
+    launch_pack(E, T.src, T.scale, C, t, codes, E.w_rin);
+    int rc = timed ? E.run_sweep(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0)
+                   : E.sweep_inline(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0);
+    if (rc) return rc;
+    launch_unpack_tab(E, E.w_v, C, t, codes, T.zdst);
+    if (timed) E.tick_begin(Engine::K_SPMV);
+    spmv_tab_kernel<<<E.grid_for(D * C), 256, 0, E.stream>>>(T.zdst, T.wdst, C, E.coef);
+    E.count_launch();
+    if (timed) E.tick_end(Engine::K_SPMV, 2.0 * C * D * 16.0, 0);
+    if (timed) E.tick_begin(Engine::K_GS);
+    const bool tick_dot = timed;
+    switch (t) {
+      case 1: gs_and_qr<1>(ce, nv, tick_dot); break;
+      case 2: gs_and_qr<2>(ce, nv, tick_dot); break;
+      case 3: gs_and_qr<3>(ce, nv, tick_dot); break;
+      default: gs_and_qr<4>(ce, nv, tick_dot); break;
+    }
+    if (timed)
+      E.tick_end(Engine::K_GS, K.passes * (2.0 * nv * D * 16 + 3.0 * C * D * 16) + 6.0 * C * D * 16,
+                 K.passes * 16.0 * nv * t * D);
+    if (ce != cudaSuccess) return HH_ECUDA;
+    const size_t hsmem = (size_t)(K.maxZ + 2) * sizeof(double2);
+    cudaFuncSetAttribute((const void*)hess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+    hess_kernel<<<S, 32, hsmem, E.stream>>>(K);
+    source_sum_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K);
+    source_final_kernel<<<S, 32, 0, E.stream>>>(K);
+    E.count_launch(3);
+    return HH_OK;
+  }
+
+  // Replays (capturing on first use) the step graph for nact active slots.  Returns
+  // HH_EAGAIN_STEP when the step cannot be captured here; the caller then runs it eagerly
+  // and no later step tries again.
+  int replay_step(int nact, double nv) {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    for (const StepGraph& g : step_graphs)
+      if (g.nact == nact) {
+        exec = g.exec;
+        kernels = g.kernels;
+      }
+    if (!exec) {
+      const int C = nact * t;
+      int rc = E.ensure_tuned(C);  // tuning runs kernels and synchronises: not inside a capture
+      if (rc) return rc;
+      cudaGraph_t graph = nullptr;
+      const int64_t before = E.kernel_launches;
+      cudaError_t ce = cudaStreamBeginCapture(E.stream, cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        cudaError_t kce = cudaSuccess;
+        rc = enqueue_step(nact, nv, false, kce);
+        ce = cudaStreamEndCapture(E.stream, &graph);
+        if (ce == cudaSuccess && (rc != HH_OK || kce != cudaSuccess)) ce = cudaErrorStreamCaptureInvalidated;
+      }
+      kernels = E.kernel_launches - before;
+      E.kernel_launches = before;
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) {
+        cudaGetLastError();
+        step_graph_broken = true;
+        return HH_EAGAIN_STEP;
+      }
+      step_graphs.push_back(StepGraph{nact, exec, kernels});
+    }
+    cudaError_t ce = cudaGraphLaunch(exec, E.stream);
+    if (ce != cudaSuccess) return (E.set_cuda_error(ce, "step graph launch"), HH_ECUDA);
+    E.count_launch((int)kernels);
+    return HH_OK;
   }
 
   // Solution, explicit residual and result of every slot that has just finished.

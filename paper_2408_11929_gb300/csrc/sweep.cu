@@ -588,6 +588,19 @@ int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool sin
   return HH_OK;
 }
 
+int Engine::sweep_inline(const void* Rin, void* V, void* W, int C, bool single) {
+  cudaError_t ce = precision == HH_PREC_FP32
+                       ? launch_steps_t<float>(*this, Rin, V, W, C, single, w_partial, w_partial_bytes, false)
+                       : launch_steps_t<double>(*this, Rin, V, W, C, single, w_partial, w_partial_bytes, false);
+  if (ce != cudaSuccess) { set_cuda_error(ce, "sweep launch"); return HH_ECUDA; }
+  return HH_OK;
+}
+
+int Engine::ensure_tuned(int C) {
+  if (precision != HH_PREC_FP32 || !tc_ready || C % 2 || tc_tuned.count(C)) return HH_OK;
+  return tune_tc(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
+}
+
 // launch helpers used by krylov.cu / api.cu / noalloc.cu
 template <typename R>
 static void launch_pack_t(Engine& E, const double2* const* srcptr, const double* scale, int C, int t, int4 codes,
