@@ -199,12 +199,13 @@ print(json.dumps(dict(t_asm=t_asm, t_fact=t_fact, t_solve=t_solve, t_mv=t_mv)))
 """
 
 
-def oracle_sample(w, iters: int, nsolve: int = 6) -> dict:
-    """Times the oracle on one strip of the workload in a single-threaded subprocess and
-    scales it to one full solve: iterations x directions x (2N - 1) strip solves + matvecs
-    (Gram-Schmidt and the strip factorisation excluded, as the GPU step excludes setup)."""
+def oracle_sample(w, iters: int, nsolve: int = 6, threads: int = 1) -> dict:
+    """Times the oracle on one strip of the workload in a subprocess with `threads` BLAS
+    threads and scales it to one full solve: iterations x directions x (2N - 1) strip solves +
+    matvecs (Gram-Schmidt and the strip factorisation excluded, as the GPU step excludes setup)."""
     code = CPU_SAMPLE_CODE % dict(root=ROOT, k=w.k, n=w.n, N=w.strips, iters=iters, nsolve=nsolve)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -338,12 +339,20 @@ def run_gpu(args, ws, rank, local):
         g = golden(w)
         err = None
         iters_oracle = None
+        oracle_cmp = None
         if g is not None:
             idx = np.array(g["sample_nodes"])
             r0 = g["rhs"]["0"]
             xt = np.array(r0["tight_x_sample_re"]) + 1j * np.array(r0["tight_x_sample_im"])
+            xs = np.array(r0["x_sample_re"]) + 1j * np.array(r0["x_sample_im"])
             err = float(np.linalg.norm(x_host[idx] - xt) / np.linalg.norm(xt))
             iters_oracle = r0["iterations"]
+            oracle_cmp = {
+                "vs_oracle_same_tol": float(np.linalg.norm(x_host[idx] - xs) / np.linalg.norm(xs)),
+                "vs_oracle_tight": err,
+                "oracle_own_stop_error": float(np.linalg.norm(xs - xt) / np.linalg.norm(xt)),
+                "oracle_rel_res_explicit": r0["rel_res_explicit"],
+                "sample": "%d stored nodes (tests/golden)" % len(idx)}
         out = {
             "metric": METRIC, "value": units / tmax, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
@@ -352,6 +361,13 @@ def run_gpu(args, ws, rank, local):
             "time_to_tol_ms": tmax / args.steps * 1e3, "iterations": iters[-1], "iterations_oracle": iters_oracle,
             "status": hh.STATUS_NAMES[status], "rel_res_explicit": rel_exp, "setup_ms": setup_ms,
             "error_vs_oracle_tight": err,
+            "error_vs_oracle": oracle_cmp,
+            "setup": {"ms": setup_ms, "flops": st["setup_flops"],
+                      "tflops": st["setup_flops"] / (setup_ms / 1e3) / 1e12 if setup_ms else None,
+                      "frac_of_tf32_peak": (st["setup_flops"] / (setup_ms / 1e3) / 1e12 / peaks["tf32_tflops"])
+                      if setup_ms else None,
+                      "setup_plus_solve_ms": setup_ms + tmax / args.steps * 1e3,
+                      "newton_schulz_blocks": st["ns_blocks"], "newton_schulz_iterations": st["ns_iterations"]},
             "roofline": dominant,
             "roofline_others": others,
             "phase_roofline": {
@@ -572,6 +588,10 @@ def main():
                            f"({d['t_mv'] * 1e3:.0f} ms), scaled to {d['iters']} iterations x 4 directions x "
                            f"{2 * w.strips - 1} strip solves; single thread (OMP/OPENBLAS_NUM_THREADS=1)"),
                 "host_cores_available": os.cpu_count()}
+            dn = oracle_sample(w, out["iterations_oracle"] or out["iterations"], nsolve=4, threads=os.cpu_count() or 1)
+            out["cpu_baseline_all_cores"] = {"value": 1.0 / dn["solve_s_est"], "unit": "solves/s",
+                                             "cores": os.cpu_count(), "kind": "oracle",
+                                             "sample": "as cpu_baseline with BLAS/LAPACK threads = all host cores"}
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist

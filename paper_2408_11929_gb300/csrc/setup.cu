@@ -400,7 +400,8 @@ int factor_impl(Engine& E) {
     if (use_ns && j >= (E.tc_dense_ok() ? 1 : 2)) {
       int iters = 0;
       if (newton_schulz<R>(E, bufA, X, F + (size_t)j * m * ld, bufC, bufD, part_dev, part_host, iters)) {
-        E.tick_end(Engine::K_SETUP, 0.0, (2.0 * iters + 1) * 8.0 * m * (double)m * m);
+        // 2 GEMMs per iteration, the final residual GEMM, and the two of the refinement step
+        E.tick_end(Engine::K_SETUP, 0.0, (2.0 * iters + 1 + (E.tc_dense_ok() ? 2 : 0)) * 8.0 * m * (double)m * m);
         ++E.ns_blocks;
         E.ns_iterations += iters;
         status = E.check_device_error("strip setup");
