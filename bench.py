@@ -456,6 +456,37 @@ def run_serving(nreq: int, rate_hz: float, seed: int = 0) -> dict:
         "kind": "open loop, Poisson arrivals, mixed k; latency includes queueing and the setup of uncached problems"}
 
 
+def run_batch(name: str = "k200_n512_b64") -> dict:
+    """The batching configuration: all right-hand sides of the workload in one hh_solve_batch
+    (complex64 sweeps on the tensor cores; every sweep serves all columns and directions).
+    One warm-up batch, then one timed batch with CUDA events."""
+    import torch
+    import paper_2408_11929_gb300 as hh
+    w = hh_inputs.workload(name)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        h = hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", stream=stream.cuda_stream)
+        setup_s = time.perf_counter() - t0
+        B = torch.cat([torch.from_numpy(h.assemble_rhs(src)) for src in w.sources]).cuda()
+        X = torch.zeros_like(B)
+        h.solve_batch(B, w.nrhs, X, tol=w.tol)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, res = h.solve_batch(B, w.nrhs, X, tol=w.tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        h.close()
+    its = [r.iterations for r in res]
+    return {"workload": name, "k": w.k, "n": w.n, "strips": w.strips, "nrhs": w.nrhs, "tol": w.tol,
+            "ms_per_batch": ms, "solves_per_s": w.nrhs / (ms / 1e3), "setup_s": setup_s,
+            "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+            "all_ok": all(r.status == hh.HH_OK for r in res),
+            "max_rel_res_explicit": max(r.rel_res_explicit for r in res)}
+
+
 def run_sweep_only(args):
     """One direction's double sweep on 4 columns (the column count of one 4-direction solve
     iteration), k = 0.39 n, timed with CUDA events on the launching stream."""
@@ -504,6 +535,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-right-hand-side batch")
     ap.add_argument("--serve-nreq", type=int, default=40, help="requests of the mixed-k serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving stream (1/s)")
     ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "solve1"],
@@ -572,6 +604,8 @@ def main():
         dist.init_process_group("nccl")
     out = run_gpu(args, ws, rank, local)
     if rank == 0:
+        if not args.no_batch:
+            out["batch"] = run_batch()
         if args.serve_nreq > 0:
             out["serving"] = run_serving(args.serve_nreq, args.serve_rate)
             out["latency_ms"]["serving_p50"] = out["serving"]["p50_ms"]
