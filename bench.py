@@ -466,25 +466,34 @@ def run_batch(name: str = "k200_n512_b64") -> dict:
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
-        h = hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", stream=stream.cuda_stream)
+        h = hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", profile=1, stream=stream.cuda_stream)
         setup_s = time.perf_counter() - t0
         B = torch.cat([torch.from_numpy(h.assemble_rhs(src)) for src in w.sources]).cuda()
         X = torch.zeros_like(B)
         h.solve_batch(B, w.nrhs, X, tol=w.tol)
         torch.cuda.synchronize()
+        h.reset_stats()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         _, res = h.solve_batch(B, w.nrhs, X, tol=w.tol)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+        st = h.stats()
         h.close()
     its = [r.iterations for r in res]
+    ng = max(1, st["gemm_launches"])
+    gemm_ms = st["gemm_ms"] / ng if st["gemm_ms"] > 0 else None
+    gemm_tf = (st["gemm_flops"] / ng) / (gemm_ms / 1e3) / 1e12 if gemm_ms else None
+    peaks = measured_peaks()
     return {"workload": name, "k": w.k, "n": w.n, "strips": w.strips, "nrhs": w.nrhs, "tol": w.tol,
             "ms_per_batch": ms, "solves_per_s": w.nrhs / (ms / 1e3), "setup_s": setup_s,
             "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
             "all_ok": all(r.status == hh.HH_OK for r in res),
-            "max_rel_res_explicit": max(r.rel_res_explicit for r in res)}
+            "max_rel_res_explicit": max(r.rel_res_explicit for r in res),
+            "gemm_step": {"avg_launch_ms": gemm_ms, "tflops_algorithmic": gemm_tf,
+                          "frac_of_tf32_peak": gemm_tf / peaks["tf32_tflops"] if gemm_tf else None,
+                          "launches_timed": st["gemm_launches"], "tile": st["tc_bnc"], "k_split": st["tc_nsplit"]}}
 
 
 def run_sweep_only(args):

@@ -129,6 +129,7 @@ class Engine {
   double setup_ms_total = 0;
   int last_columns = 0;
   int64_t sweep_calls = 0;
+  bool sample_next_sweep = false;  // the next eager sweep times its GEMM steps one by one
   int ns_blocks = 0, ns_iterations = 0;  // strip inverses by Newton-Schulz, and its iterations
   int64_t iterations_total = 0;           // Arnoldi steps run (timed or replayed)
   Tick cur_tick[K_NCLASS];

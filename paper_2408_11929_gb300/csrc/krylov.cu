@@ -974,6 +974,7 @@ struct SlotSolver::Impl {
     gather_tables_kernel<<<1, 256, 0, E.stream>>>(K, d_act, nact, T, W);
     E.count_launch();
     launch_pack(E, T.src, T.scale, C, t, codes, E.w_rin);
+    if (timed) E.sample_next_sweep = E.opts.profile != 0;
     int rc = timed ? E.run_sweep(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0)
                    : E.sweep_inline(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0);
     if (rc) return rc;
