@@ -506,7 +506,7 @@ def run_sweep_only(args):
     k = 400.0 * args.n / 1024
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        h = hh.Handle(k, args.n, args.strips, "LR+RL+BT+TB", precision=args.precision, profile=1,
+        h = hh.Handle(k, args.n, args.strips, "LR+RL+BT+TB", precision=args.precision, profile=1, autotune=0,
                       stream=stream.cuda_stream)
         dofs = (args.n + 1) ** 2
         r = torch.from_numpy(np.ascontiguousarray(hh_inputs.random_vector(dofs, 4, seed=1).ravel())).cuda()
@@ -563,7 +563,9 @@ def main():
         import paper_2408_11929_gb300 as hh
         __graft_entry__.build()
         w = hh_inputs.workload(WORKLOAD)
-        with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32") as h:
+        # autotune off: under a profiler the tuner's timings are blurred by the per-launch
+        # overhead; the default shape is the one the tuner picks for this workload
+        with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", autotune=0) as h:
             b = torch.from_numpy(h.assemble_rhs(w.sources[0])).cuda()
             x, res = h.solve(b, tol=w.tol)
             torch.cuda.synchronize()

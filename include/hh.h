@@ -82,7 +82,11 @@ typedef struct {
   int tensor_cores;       /* HH_PREC_FP32 only.  1 (default): the wide sweep steps run on the
                              tensor cores (tcgen05, TF32 operands split hi + lo, three products,
                              FP32 accumulation); 0: FP32 FMA on the CUDA cores */
-  int reserved[3];
+  int autotune;           /* 1 (default): time the tensor-core step's tile shapes and K splits on
+                             the first sweep of each column count and keep the fastest; 0: 64
+                             complex columns per CTA, K split to fill the SMs (for runs under a
+                             profiler, whose per-launch overhead would blur the timings) */
+  int reserved[2];
 } hh_opts;
 
 typedef struct {

@@ -399,6 +399,7 @@ void hh_default_opts(hh_opts* o) {
   o->gs_passes = 2;
   o->serve_slots = 8;
   o->tensor_cores = 1;
+  o->autotune = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {

@@ -803,7 +803,9 @@ struct SlotSolver::Impl {
     K.GX = std::max(1, std::min(E.num_sms * 2 / S + 1, (int)((D + 255) / 256)));
     K.GX = std::min(K.GX, E.num_sms * 2);
     const int cap = E.num_sms * E.coop_per_sm;
-    K.GQ = std::max(1, cap / S);
+    // one CTA per SM per slot: every reduction of the block QR meets at a barrier and sums the
+    // partials of all GQ CTAs, so more CTAs cost more than the extra parallelism brings
+    K.GQ = std::max(1, std::min(cap / S, E.num_sms));
     if (K.GQ * S > cap) return (set_error("too many slots for one cooperative QR launch"), HH_EINVAL);
     K.beta = dev<double>(S); K.done = dev<int>(S); K.status = dev<int>(S);
     K.nV = dev<int>(S); K.nZ = dev<int>(S); K.iters = dev<int>(S); K.nacc = dev<int>(S);

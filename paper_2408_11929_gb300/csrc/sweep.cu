@@ -787,6 +787,10 @@ int Engine::prepare_tensor_cores() {
 // (one warm-up and three timed launches each, writing to a scratch array), and the fastest
 // is kept for every later sweep with this column count.
 int Engine::tune_tc(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes) {
+  if (!opts.autotune) {
+    tc_tuned[C] = TcChoice{};
+    return HH_OK;
+  }
   const std::vector<SweepStep>& steps = opts.single_sweep ? steps_single : steps_double;
   const SweepStep* pick = nullptr;
   for (const SweepStep& s : steps)
