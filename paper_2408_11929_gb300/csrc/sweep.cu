@@ -334,47 +334,28 @@ __global__ void __launch_bounds__(256) line_gemv_split_kernel(const typename Cx<
                                                               LineOperand<typename Cx<R>::T> op,
                                                               const typename Cx<R>::T* __restrict__ x) {
   using T = typename Cx<R>::T;
-  extern __shared__ __align__(16) unsigned char gv_smem[];
-  T* xs = reinterpret_cast<T*>(gv_smem);  // x, column-major [ncols][m]
   __shared__ T red[8][RPC][8];
   const int ncols = op.ns * op.C;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = blockIdx.x * RPC;
   const int kw = ((m + 7) / 8 + 31) / 32 * 32;  // node indices per warp, a multiple of 32
   const int kb = warp * kw, ke = min(m, kb + kw);
-  constexpr int U = 5;  // 32-wide node groups whose factor entries are loaded before use
   T acc[RPC][8];
 #pragma unroll
   for (int r = 0; r < RPC; ++r)
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[r][c] = mk<T>(0, 0);
-  T a[RPC][U];
-  auto load_chunk = [&](int k0) {
+#pragma unroll 2
+  for (int k = kb + lane; k < ke; k += 32) {
+    T a[RPC];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + 32 * u + lane;
+    for (int r = 0; r < RPC; ++r) a[r] = row0 + r < m ? __ldg(A + (size_t)(row0 + r) * lda + k) : mk<T>(0, 0);
 #pragma unroll
-      for (int r = 0; r < RPC; ++r)
-        a[r][u] = (k < ke && row0 + r < m) ? __ldg(A + (size_t)(row0 + r) * lda + k) : mk<T>(0, 0);
-    }
-  };
-  load_chunk(kb);  // the first factor loads are in flight while x is staged
-  for (int i = threadIdx.x; i < m * ncols; i += blockDim.x) xs[i] = __ldcg(x + i);
-  __syncthreads();  // every thread, once
-  for (int k0 = kb; k0 < ke; k0 += 32 * U) {
-    if (k0 != kb) load_chunk(k0);
+    for (int c = 0; c < 8; ++c) {
+      if (c < ncols) {
+        const T xv = __ldcg(x + (size_t)c * m + k);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + 32 * u + lane;
-      if (k < ke) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c < ncols) {
-            const T xv = xs[(size_t)c * m + k];
-#pragma unroll
-            for (int r = 0; r < RPC; ++r) cfma(acc[r][c], a[r][u], xv);
-          }
-        }
+        for (int r = 0; r < RPC; ++r) cfma(acc[r][c], a[r], xv);
       }
     }
   }
@@ -480,8 +461,6 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
   cudaFuncSetAttribute((const void*)gemm_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem);
   cudaFuncSetAttribute((const void*)line_gemv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)std::min<size_t>((size_t)E.m * 8 * sizeof(T), gemv_cap));
-  cudaFuncSetAttribute((const void*)line_gemv_split_kernel<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)std::min<size_t>((size_t)E.m * 8 * sizeof(T), gemv_cap));
   // allow_tick: time the wide GEMM steps one by one (a sampled, eager sweep)
   const bool tick_gemm = allow_tick && E.opts.profile;
   for (const SweepStep& s : steps) {
@@ -498,8 +477,7 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
       T* xs = reinterpret_cast<T*>(partial_buf);  // narrow steps leave the split-K buffer free
       line_xbuild_kernel<R><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(E.m, op, E.coef, xs);
       constexpr int RPC = 4;
-      line_gemv_split_kernel<R, RPC><<<(E.m + RPC - 1) / RPC, 256, (size_t)E.m * ncols * sizeof(T), E.stream>>>(
-          A, E.ldf, E.m, op, xs);
+      line_gemv_split_kernel<R, RPC><<<(E.m + RPC - 1) / RPC, 256, 0, E.stream>>>(A, E.ldf, E.m, op, xs);
       E.count_launch(2);
     } else if (ncols <= 8 && (size_t)E.m * ncols * sizeof(T) <= gemv_cap) {
       line_gemv_kernel<R><<<(E.m + 7) / 8, 256, (size_t)E.m * ncols * sizeof(T), E.stream>>>(A, E.ldf, E.m, op,
