@@ -317,6 +317,7 @@ def run_gpu(args, ws, rank, local):
             "launches_timed": st["gemm_launches"],
             "share_of_step": gemm_total_ms / step_total_ms if step_total_ms > 0 else None,
             "autotuned": {"complex_columns_per_cta": st["tc_bnc"], "k_split": st["tc_nsplit"] or "fill SMs",
+                          "k_slices_summed_in_cluster": bool(st["tc_cluster"]),
                           "us_when_tuned": st["tc_us"]} if tc_on else None,
             "peak_src": peaks["tf32_src"] if tc_on else
             "derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x %.0f MHz" % peaks["sm_mhz"],

@@ -85,7 +85,10 @@ typedef struct {
   int autotune;           /* 1 (default): time the tensor-core step's tile shapes and K splits on
                              the first sweep of each column count and keep the fastest; 0: 64
                              complex columns per CTA, K split to fill the SMs (for runs under a
-                             profiler, whose per-launch overhead would blur the timings) */
+                             profiler, whose per-launch overhead would blur the timings);
+                             -(1 + 7 s + v): candidate v (K split 0 = fill the SMs, 1, 2, 4 summed
+                             by a reduction kernel; 2, 4, 8 summed in a thread-block cluster) of
+                             shape s (0: 64 columns, 1: 32 columns), for tests */
   int reserved[2];
 } hh_opts;
 
@@ -123,9 +126,12 @@ typedef struct {
   int ns_iterations;       /* their iterations (two GEMMs each) */
   int tc_bnc, tc_nsplit;   /* autotuned tensor-core step for the last column count: complex
                               columns per CTA (64 or 32) and K split (0 = fill the SMs) */
+  int tc_cluster;          /* 1 when its K slices are summed in a thread-block cluster */
   double tc_us;            /* its time per step when tuned (us) */
   int64_t iterations_total; /* Arnoldi steps run, timed or replayed from their graph (with
                                opts.profile the classes above time every 8th step) */
+  int step_graphs;          /* Arnoldi-step graphs captured by the handle's solvers */
+  int step_graph_fallback;  /* 1 if a step could not be captured and ran eagerly */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

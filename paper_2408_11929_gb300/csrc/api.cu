@@ -543,11 +543,14 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->ns_blocks = E.ns_blocks;
   st->ns_iterations = E.ns_iterations;
   st->iterations_total = E.iterations_total;
+  st->step_graphs = E.step_graphs_captured;
+  st->step_graph_fallback = E.step_graph_fallback ? 1 : 0;
   {
     const auto it = E.tc_tuned.find(E.last_columns);
     if (it != E.tc_tuned.end()) {
       st->tc_bnc = it->second.shape == 1 ? 32 : 64;
       st->tc_nsplit = it->second.nsplit;
+      st->tc_cluster = it->second.cluster ? 1 : 0;
       st->tc_us = it->second.us;
     }
   }

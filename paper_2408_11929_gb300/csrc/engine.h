@@ -95,6 +95,7 @@ class Engine {
   // 1: 32 columns x 4 stages) and K split (0 = fill the SMs)
   struct TcChoice {
     int shape = 0, nsplit = 0;
+    bool cluster = false;  // K slices summed in a thread-block cluster instead of split_reduce
     double us = 0;
   };
   std::map<int, TcChoice> tc_tuned;
@@ -132,6 +133,8 @@ class Engine {
   bool sample_next_sweep = false;  // the next eager sweep times its GEMM steps one by one
   int ns_blocks = 0, ns_iterations = 0;  // strip inverses by Newton-Schulz, and its iterations
   int64_t iterations_total = 0;           // Arnoldi steps run (timed or replayed)
+  int step_graphs_captured = 0;           // Arnoldi-step graphs captured
+  bool step_graph_fallback = false;       // a step could not be captured
   Tick cur_tick[K_NCLASS];
   bool tick_open[K_NCLASS] = {false, false, false, false, false, false};
 

@@ -1037,9 +1037,11 @@ struct SlotSolver::Impl {
       if (ce != cudaSuccess) {
         cudaGetLastError();
         step_graph_broken = true;
+        E.step_graph_fallback = true;
         return HH_EAGAIN_STEP;
       }
       step_graphs.push_back(StepGraph{nact, exec, kernels});
+      ++E.step_graphs_captured;
     }
     cudaError_t ce = cudaGraphLaunch(exec, E.stream);
     if (ce != cudaSuccess) return (E.set_cuda_error(ce, "step graph launch"), HH_ECUDA);

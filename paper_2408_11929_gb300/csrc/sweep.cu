@@ -422,17 +422,39 @@ static double step_bytes(const Engine& E, const SweepStep& s, int C) {
 // the SMs are filled); the K slices meet in split_reduce_kernel.
 template <class CF>
 static cudaError_t launch_tc_step(Engine& E, const LineOperand<float2>& op, int fblock, int C, int nsplit_req,
-                                  const void* Rin, void* partial_buf, size_t partial_bytes) {
+                                  const void* Rin, void* partial_buf, size_t partial_bytes, bool cluster = false) {
   const int ncols = op.ns * C;
   const int gx = (E.m + tc::BM - 1) / tc::BM, gy = (ncols + CF::BNC - 1) / CF::BNC;
   int nsplit = nsplit_req > 0 ? nsplit_req : std::max(1, std::min(8, (E.num_sms - 4) / (gx * gy)));
-  while (nsplit > 1 && (size_t)nsplit * E.m * ncols * sizeof(float2) > partial_bytes) --nsplit;
+  if (!cluster)
+    while (nsplit > 1 && (size_t)nsplit * E.m * ncols * sizeof(float2) > partial_bytes) --nsplit;
   const int kchunk = ((E.m + nsplit - 1) / nsplit + tc::BKC - 1) / tc::BKC * tc::BKC;
   nsplit = (E.m + kchunk - 1) / kchunk;  // no empty split
-  float2* partial = nsplit > 1 ? reinterpret_cast<float2*>(partial_buf) : nullptr;
   const Engine::LineMaps* mb = E.line_maps_for(op.base ? op.base : Rin, C, CF::BNC);
   const Engine::LineMaps* ms = E.line_maps_for(op.src ? op.src : Rin, C, CF::BNC);
   if (!mb || !ms) return cudaErrorInvalidValue;
+  if (cluster && nsplit > 1) {
+    // the K slices of a tile form one cluster and meet in distributed shared memory
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(gx, gy, nsplit);
+    cfg.blockDim = dim3(tc::THREADS);
+    cfg.dynamicSmemBytes = CF::SMEM;
+    cfg.stream = E.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = nsplit;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    float2* nopartial = nullptr;
+    const cudaError_t ce =
+        cudaLaunchKernelEx(&cfg, tc_line_gemm_kernel<CF, true>, E.tmap_hi, E.tmap_lo, mb->base, ms->src, fblock, E.m,
+                           op, E.coef, kchunk, nopartial, E.err, E.opts.timeout_cycles);
+    E.count_launch();
+    return ce;
+  }
+  float2* partial = nsplit > 1 ? reinterpret_cast<float2*>(partial_buf) : nullptr;
   tc_line_gemm_kernel<CF><<<dim3(gx, gy, nsplit), tc::THREADS, CF::SMEM, E.stream>>>(
       E.tmap_hi, E.tmap_lo, mb->base, ms->src, fblock, E.m, op, E.coef, kchunk, partial, E.err,
       E.opts.timeout_cycles);
@@ -489,9 +511,10 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
       const auto it = E.tc_tuned.find(C);
       const Engine::TcChoice ch = it != E.tc_tuned.end() ? it->second : Engine::TcChoice{};
       if (tick_gemm) E.tick_begin(Engine::K_GEMM);
-      const cudaError_t le = ch.shape == 1
-                                 ? launch_tc_step<tc::Narrow>(E, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes)
-                                 : launch_tc_step<tc::Wide>(E, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes);
+      const cudaError_t le =
+          ch.shape == 1
+              ? launch_tc_step<tc::Narrow>(E, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes, ch.cluster)
+              : launch_tc_step<tc::Wide>(E, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes, ch.cluster);
       if (le != cudaSuccess) return le;
       if (tick_gemm) E.tick_end(Engine::K_GEMM, step_bytes(E, s, C), 8.0 * E.m * E.m * (double)ncols);
     } else {
@@ -658,6 +681,10 @@ int Engine::load_encoder() {
                        (int)tc::Wide::SMEM);
   cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Narrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)tc::Narrow::SMEM);
+  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Wide, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::Wide::SMEM);
+  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Narrow, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::Narrow::SMEM);
   return HH_OK;
 }
 
@@ -764,9 +791,20 @@ int Engine::prepare_tensor_cores() {
 // (all strips, coupled operand) is timed with CUDA events for each tile shape and K split
 // (one warm-up and three timed launches each, writing to a scratch array), and the fastest
 // is kept for every later sweep with this column count.
+// the autotuner's candidates: K splits summed by split_reduce_kernel (0 = fill the SMs), then
+// K splits summed in a thread-block cluster
+static const int kTcSplits[7] = {0, 1, 2, 4, 2, 4, 8};
+static bool tc_candidate_cluster(int variant) { return variant >= 4; }
+
 int Engine::tune_tc(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes) {
-  if (!opts.autotune) {
+  if (opts.autotune == 0) {
     tc_tuned[C] = TcChoice{};
+    return HH_OK;
+  }
+  if (opts.autotune < 0) {  // one candidate, chosen by the caller: -(1 + 7 shape + variant)
+    const int idx = -opts.autotune - 1;
+    const int variant = idx % 7;
+    tc_tuned[C] = TcChoice{(idx / 7) % 2, kTcSplits[variant], tc_candidate_cluster(variant), 0.0};
     return HH_OK;
   }
   const std::vector<SweepStep>& steps = opts.single_sweep ? steps_single : steps_double;
@@ -793,14 +831,18 @@ int Engine::tune_tc(int C, const void* Rin, void* V, void* W, void* partial, siz
   cudaEventCreate(&b);
   TcChoice best;
   best.us = 1e30;
-  const int splits[4] = {0, 1, 2, 4};
   for (int shape = 0; shape < 2; ++shape)
-    for (int ns : splits) {
+    for (int variant = 0; variant < 7; ++variant) {
+      const bool cl = tc_candidate_cluster(variant);
+      const int ns = kTcSplits[variant];
       auto run = [&]() {
-        return shape == 1 ? launch_tc_step<tc::Narrow>(*this, op, pick->f, C, ns, Rin, partial, partial_bytes)
-                          : launch_tc_step<tc::Wide>(*this, op, pick->f, C, ns, Rin, partial, partial_bytes);
+        return shape == 1 ? launch_tc_step<tc::Narrow>(*this, op, pick->f, C, ns, Rin, partial, partial_bytes, cl)
+                          : launch_tc_step<tc::Wide>(*this, op, pick->f, C, ns, Rin, partial, partial_bytes, cl);
       };
-      if (run() != cudaSuccess) continue;
+      if (run() != cudaSuccess) {  // e.g. a cluster shape the GPU cannot co-schedule
+        cudaGetLastError();
+        continue;
+      }
       cudaEventRecord(a, stream);
       for (int r = 0; r < 3; ++r) run();
       cudaEventRecord(b, stream);
@@ -808,7 +850,7 @@ int Engine::tune_tc(int C, const void* Rin, void* V, void* W, void* partial, siz
       float ms = 0;
       cudaEventElapsedTime(&ms, a, b);
       const double us = ms * 1e3 / 3;
-      if (us < best.us) best = TcChoice{shape, ns, us};
+      if (us < best.us) best = TcChoice{shape, ns, cl, us};
     }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -134,6 +134,27 @@ __device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
 
 __device__ __forceinline__ bool aborted(const int* flag) { return *(volatile const int*)flag != 0; }
 
+// thread-block clusters: rank of this CTA, all threads of the cluster meet, and a 16-byte
+// load from the shared memory of another CTA of the cluster (same offset in its window)
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float4 ld_cluster_f4(const void* local, unsigned rank) {
+  unsigned remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(remote)
+               : "memory");
+  return v;
+}
+
 }  // namespace tc
 
 // grid = (ceil(m / 128), ceil(ncols / 64), nsplit); split z covers node indices
@@ -143,7 +164,10 @@ __device__ __forceinline__ bool aborted(const int* flag) { return *(volatile con
 // count per strip C must be even (16-byte aligned rows).  With partial != nullptr the CTA
 // writes its slice to partial[(z * m + row) * ncols + col] for split_reduce_kernel, else it
 // applies the step's output modes itself.
-template <class CF>
+// CLUSTER: the K slices of a tile run as one thread-block cluster (cluster dims (1, 1,
+// gridDim.z)) and are summed through distributed shared memory at the end, in rank order,
+// instead of through partial (which must then be nullptr).
+template <class CF, bool CLUSTER = false>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     tc_line_gemm_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                         const __grid_constant__ CUtensorMap map_base, const __grid_constant__ CUtensorMap map_src,
@@ -349,7 +373,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         __uint_as_float(im[q + 1]));
     }
     asm volatile("bar.sync 2, %0;" ::"n"(BUILDERS) : "memory");
-    if (ok && !tc::aborted(abort_s)) {
+    if (!CLUSTER && ok && !tc::aborted(abort_s)) {
       const int N = op.N, C = op.C;
       // BNC / 2 lanes per row, each with complex columns 2l, 2l + 1
       constexpr int LPR = BNC / 2, RPW = 32 / LPR;  // lanes per row, rows per warp pass
@@ -380,6 +404,38 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   }
   tc::fence_before();
   __syncthreads();
+  if constexpr (CLUSTER) {
+    // every CTA's staged tile is complete; CTA q of the cluster sums rows
+    // [q BM / nsplit, (q + 1) BM / nsplit) of all tiles in rank order and writes them
+    constexpr int SROW = BNC + 2;
+    const float2* stile = reinterpret_cast<const float2*>(sm);
+    const unsigned nsplit = gridDim.z, q = tc::cluster_rank();
+    tc::cluster_sync();
+    const int rows = (BM + (int)nsplit - 1) / (int)nsplit, r0 = (int)q * rows;
+    const bool good = !tc::aborted(abort_s) && *(volatile int*)err == 0;
+    const int N = op.N, C = op.C;
+    for (int e = threadIdx.x; e < rows * (BNC / 2); e += THREADS) {
+      const int r = r0 + e / (BNC / 2), l = e % (BNC / 2);
+      if (r >= BM) break;
+      const int gr = row0 + r, gc = colc0 + 2 * l;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (unsigned z = 0; z < nsplit; ++z) {
+        const float4 p = tc::ld_cluster_f4(stile + r * SROW + 2 * l, z);
+        v.x += p.x; v.y += p.y; v.z += p.z; v.w += p.w;
+      }
+      if (!good || gr >= m || gc >= ncols) continue;
+      const float2 z0 = make_float2(v.x, v.y), z1 = make_float2(v.z, v.w);
+      float2* o = op.out + ((size_t)(op.out_j * m + gr) * N + op.s0) * C + gc;
+      float2* a2 = op.acc ? op.acc + ((size_t)(op.acc_j * m + gr) * N + op.s0) * C + gc : nullptr;
+      apply_out(o, z0, op.out_mode);
+      if (a2) apply_out(a2, op.out_mode == OUT_SET ? z0 : *o, op.acc_mode);
+      if (gc + 1 < ncols) {
+        apply_out(o + 1, z1, op.out_mode);
+        if (a2) apply_out(a2 + 1, op.out_mode == OUT_SET ? z1 : o[1], op.acc_mode);
+      }
+    }
+    tc::cluster_sync();  // no CTA leaves while another still reads its tile
+  }
   if (warp == TMA_WARP) {
     tc::fence_after();
     tc::tmem_dealloc(tmem, TMEM_COLS);

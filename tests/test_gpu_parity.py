@@ -332,3 +332,37 @@ def test_tensor_core_sweeps(k, n, N):
     print(f"tensor-core vs oracle {worst_t:.2e}, CUDA-core vs oracle {worst_c:.2e}")
     assert worst_c < 2e-4
     assert worst_t < 2e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_graphs_replayed_and_equal_to_eager(precision):
+    """Every Arnoldi step is captured as a CUDA graph (including the cooperative block QR) and
+    replayed; the result equals the eager solve (use_graph = 0) to rounding."""
+    k, n, N = 30.0, 48, 4
+    src = hh_inputs.centre_source()
+    with hh.Handle(k, n, N, precision=precision) as h:
+        b = h.assemble_rhs(src)
+        xg, rg = h.solve(b, tol=1e-8)
+        st = h.stats()
+    with hh.Handle(k, n, N, precision=precision, use_graph=0) as h:
+        xe, re_ = h.solve(b, tol=1e-8)
+    assert st["step_graphs"] >= 1 and st["step_graph_fallback"] == 0
+    assert rg.iterations == re_.iterations
+    assert rel(xg, xe) < (1e-12 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("cand", range(14))
+def test_tensor_core_step_candidates(cand):
+    """Every candidate of the tensor-core step's autotuner (two tile shapes; K split by a
+    reduction kernel or in a thread-block cluster) gives the complex64 sweep within the bar."""
+    k, n, N = 60.0, 256, 8
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], 4, seed=9)
+    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + cand)) as h:
+        for d in ("BT", "LR"):
+            sw = sweep.Sweeper(A, k, n, N, d)
+            z = h.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
+            st = h.stats()
+            assert st["tc_bnc"] == (32 if cand >= 7 else 64) and st["tc_cluster"] == int(cand % 7 >= 4)
+            for c in range(4):
+                assert rel(z[c], sw.apply(r[c])) < 2e-4, (d, c)
