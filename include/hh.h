@@ -89,7 +89,11 @@ typedef struct {
                              -(1 + 7 s + v): candidate v (K split 0 = fill the SMs, 1, 2, 4 summed
                              by a reduction kernel; 2, 4, 8 summed in a thread-block cluster) of
                              shape s (0: 64 columns, 1: 32 columns), for tests */
-  int reserved[2];
+  int fuse_chains;        /* 1 (default): each interface chain of at most 8 columns (the N-2 and
+                             N-1 dependent strip-to-strip steps of a double sweep) runs as one
+                             cooperative launch that keeps its factor block in shared memory and
+                             puts a grid barrier between the steps; 0: two launches per step */
+  int reserved[1];
 } hh_opts;
 
 typedef struct {

@@ -166,8 +166,8 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   const size_t fcopies = (precision == HH_PREC_FP32 && opts.tensor_cores) ? 3 : 1;
   if (fcopies * fbytes + (64ull << 20) > free_b)
     return (set_error("strip factors do not fit in free device memory"), HH_ENOMEM);
-  if (dmalloc(&factors, fbytes) || dmalloc((void**)&bar, 64) || dmalloc((void**)&err, 64)) return HH_ENOMEM;
-  cudaMemsetAsync(bar, 0, 64, stream);
+  if (dmalloc(&factors, fbytes) || dmalloc((void**)&bar, BAR_BYTES) || dmalloc((void**)&err, 64)) return HH_ENOMEM;
+  cudaMemsetAsync(bar, 0, BAR_BYTES, stream);
   cudaMemsetAsync(err, 0, 64, stream);
   steps_double = build_steps(n, N, true);
   steps_single = build_steps(n, N, false);
@@ -400,6 +400,7 @@ void hh_default_opts(hh_opts* o) {
   o->serve_slots = 8;
   o->tensor_cores = 1;
   o->autotune = 1;
+  o->fuse_chains = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {

@@ -59,6 +59,10 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Words reserved per barrier in a barrier buffer (the counter is the first; the rest keeps
+// barriers of different users on separate cache lines).
+constexpr int GRID_BAR_WORDS = 64;
+
 // Grid-wide barrier for a cooperative (co-resident) launch.  *count starts at 0 for the
 // launch and only grows; `target` is the caller's running arrival target.  Every wait is
 // bounded by `budget` SM cycles: on expiry the device error word is set and false is

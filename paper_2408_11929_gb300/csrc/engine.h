@@ -109,7 +109,11 @@ class Engine {
     int64_t kernels;  // launches per replay
   };
   std::vector<SweepGraph> sweep_graphs;
-  unsigned* bar = nullptr;  // grid barrier counter
+  // grid barriers (GRID_BAR_WORDS words each): BAR_SETUP for the pivoted Gauss-Jordan of the
+  // strip setup, BAR_CHAIN for the sweep's interface chains
+  enum { BAR_SETUP = 0, BAR_CHAIN = 1, BAR_COUNT = 2 };
+  static constexpr size_t BAR_BYTES = (size_t)BAR_COUNT * 64 * sizeof(unsigned);
+  unsigned* bar = nullptr;
   int* err = nullptr;       // device error word
   std::vector<SweepStep> steps_double, steps_single;  // sweep schedules
   size_t bytes_allocated = 0;

@@ -43,6 +43,9 @@ struct KState {
   const double2** srcptr;
   double* scale;
   double* res_exp;
+  // per slot, new column b, plane q: (Re w, Im w - Re w, Re w + Im w) of the new columns, the
+  // operand of the inner products in Gauss's three-multiplication form (slots x t x 3 x D)
+  double* Wp;
 };
 
 // ------------------------------------------------------------------ reductions
@@ -270,39 +273,91 @@ __global__ void scale_copy_kernel(KState S) {
 }
 
 // ------------------------------------------------------------------ Gram-Schmidt vs the basis
+// The inner products conj(v) w and the updates w - v h run in Gauss's three-multiplication
+// form of the complex product (three real FMAs instead of four; the FP64 pipe bounds both
+// kernels).  For conj(v) w with dv = Re v - Im v, wd = Im w - Re w, ws = Re w + Im w:
+//   a1 = Re w dv,  a2 = Re v wd,  a3 = Im v ws;  Re = a1 + a3,  Im = a1 + a2,
+// each of a1, a2, a3 summed over the rows first.  The error stays within a small multiple of
+// the unit roundoff times |v| |w| summed over the rows, the normwise bound of the plain form.
+
+// Planes (Re w, Im w - Re w, Re w + Im w) of the new columns, for the first pass's inner products.
+template <int TT>
+__global__ void __launch_bounds__(256) gs_wprep_kernel(KState S, const double2* __restrict__ W) {
+  const int r = blockIdx.y;
+  if (S.done[r]) return;
+  const size_t D = S.D;
+  const double2* Wr = W + (size_t)r * TT * D;
+  double* P = S.Wp + (size_t)r * TT * 3 * D;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < D; g += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int b = 0; b < TT; ++b) {
+      const double2 w = Wr[b * D + g];
+      P[(b * 3 + 0) * D + g] = w.x;
+      P[(b * 3 + 1) * D + g] = w.y - w.x;
+      P[(b * 3 + 2) * D + g] = w.x + w.y;
+    }
+  }
+}
+
 template <int TT, int AB>
-__global__ void __launch_bounds__(256) gs_dot_kernel(KState S, const double2* __restrict__ W) {
+__global__ void __launch_bounds__(256) gs_dot_kernel(KState S) {
   const int r = blockIdx.y;
   if (S.done[r]) return;
   const int nV = S.nV[r];
   const size_t D = S.D;
   const size_t chunk = (D + S.GX - 1) / S.GX;
   const size_t g0 = blockIdx.x * chunk, g1 = min(D, g0 + chunk);
-  const double2* Wr = W + (size_t)r * TT * D;
+  const double* P = S.Wp + (size_t)r * TT * 3 * D;
   __shared__ double sh[32 * (AB * TT * 2 > 8 ? AB * TT * 2 : 8)];
   for (int a0 = 0; a0 < nV; a0 += AB) {
-    double acc[AB * TT * 2];
+    double a1[AB * TT], a2[AB * TT], a3[AB * TT];
 #pragma unroll
-    for (int q = 0; q < AB * TT * 2; ++q) acc[q] = 0;
+    for (int q = 0; q < AB * TT; ++q) a1[q] = a2[q] = a3[q] = 0;
     const double2* vp[AB];
 #pragma unroll
     for (int ab = 0; ab < AB; ++ab) vp[ab] = (a0 + ab < nV) ? S.Vptr[(size_t)r * S.maxV + a0 + ab] : nullptr;
-    for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-      double2 w[TT];
+    // the next row's operands are loaded before this row's multiply-adds (one CTA per SM at
+    // this register count: the loads of a row would otherwise stall its warp for a full
+    // memory latency)
+    double nwr[TT], nwd[TT], nws[TT];
+    double2 nvv[AB];
+    auto fetch = [&](size_t g) {
 #pragma unroll
-      for (int b = 0; b < TT; ++b) w[b] = Wr[b * D + g];
+      for (int b = 0; b < TT; ++b) {
+        nwr[b] = P[(b * 3 + 0) * D + g];
+        nwd[b] = P[(b * 3 + 1) * D + g];
+        nws[b] = P[(b * 3 + 2) * D + g];
+      }
+#pragma unroll
+      for (int ab = 0; ab < AB; ++ab) nvv[ab] = vp[ab] ? vp[ab][g] : make_double2(0, 0);
+    };
+    if (g0 + threadIdx.x < g1) fetch(g0 + threadIdx.x);
+    for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+      double wr[TT], wd[TT], ws[TT];
+      double2 vv[AB];
+#pragma unroll
+      for (int b = 0; b < TT; ++b) { wr[b] = nwr[b]; wd[b] = nwd[b]; ws[b] = nws[b]; }
+#pragma unroll
+      for (int ab = 0; ab < AB; ++ab) vv[ab] = nvv[ab];
+      if (g + blockDim.x < g1) fetch(g + blockDim.x);
 #pragma unroll
       for (int ab = 0; ab < AB; ++ab) {
-        if (vp[ab]) {
-          const double2 v = vp[ab][g];
+        const double2 v = vv[ab];
+        const double dv = v.x - v.y;
 #pragma unroll
-          for (int b = 0; b < TT; ++b) {
-            const int q = (ab * TT + b) * 2;
-            acc[q] = fma(v.x, w[b].x, acc[q]); acc[q] = fma(v.y, w[b].y, acc[q]);
-            acc[q + 1] = fma(v.x, w[b].y, acc[q + 1]); acc[q + 1] = fma(-v.y, w[b].x, acc[q + 1]);
-          }
+        for (int b = 0; b < TT; ++b) {
+          const int q = ab * TT + b;
+          a1[q] = fma(wr[b], dv, a1[q]);
+          a2[q] = fma(v.x, wd[b], a2[q]);
+          a3[q] = fma(v.y, ws[b], a3[q]);
         }
       }
+    }
+    double acc[AB * TT * 2];
+#pragma unroll
+    for (int q = 0; q < AB * TT; ++q) {
+      acc[2 * q] = a1[q] + a3[q];
+      acc[2 * q + 1] = a1[q] + a2[q];
     }
     if constexpr (AB * TT * 2 == 32) {
       // value q = (ab TT + b) 2 + part lands on thread q
@@ -345,34 +400,57 @@ __global__ void gs_reduce_kernel(KState S, int first) {
   }
 }
 
+// w_b -= sum_a v_a h_ab in the three-multiplication form: with sv = Re v + Im v,
+// hd = Im h - Re h, hs = Re h + Im h:  p1 = sum Re h sv, p2 = sum Re v hd, p3 = sum Im v hs,
+// Re(v h) summed = p1 - p3, Im = p1 + p2.  write_planes: also store the planes of the updated
+// columns for the next pass's inner products.
 template <int TT>
-__global__ void __launch_bounds__(256) gs_update_kernel(KState S, double2* __restrict__ W) {
+__global__ void __launch_bounds__(256) gs_update_kernel(KState S, double2* __restrict__ W, int write_planes) {
   const int r = blockIdx.y;
   if (S.done[r]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nV = S.nV[r];
-  double2* Hs = reinterpret_cast<double2*>(smem_raw);
-  const double2** vps = reinterpret_cast<const double2**>(Hs + (size_t)nV * TT);
-  for (int p = threadIdx.x; p < nV * TT; p += blockDim.x) Hs[p] = S.Hthis[(size_t)r * S.maxV * TT + p];
+  double* Hs = reinterpret_cast<double*>(smem_raw);  // nV x TT x (Re h, hd, hs)
+  const double2** vps = reinterpret_cast<const double2**>(Hs + (size_t)nV * TT * 3);
+  for (int p = threadIdx.x; p < nV * TT; p += blockDim.x) {
+    const double2 h = S.Hthis[(size_t)r * S.maxV * TT + p];
+    Hs[3 * p] = h.x;
+    Hs[3 * p + 1] = h.y - h.x;
+    Hs[3 * p + 2] = h.x + h.y;
+  }
   for (int a = threadIdx.x; a < nV; a += blockDim.x) vps[a] = S.Vptr[(size_t)r * S.maxV + a];
   __syncthreads();
   const size_t D = S.D;
   double2* Wr = W + (size_t)r * TT * D;
+  double* P = S.Wp + (size_t)r * TT * 3 * D;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < D; g += (size_t)gridDim.x * blockDim.x) {
-    double2 w[TT];
+    double p1[TT], p2[TT], p3[TT];
 #pragma unroll
-    for (int b = 0; b < TT; ++b) w[b] = Wr[b * D + g];
+    for (int b = 0; b < TT; ++b) p1[b] = p2[b] = p3[b] = 0;
+#pragma unroll 4
     for (int a = 0; a < nV; ++a) {
       const double2 v = vps[a][g];
+      const double sv = v.x + v.y;
+      const double* h = Hs + (size_t)a * TT * 3;
 #pragma unroll
       for (int b = 0; b < TT; ++b) {
-        const double2 hh = Hs[a * TT + b];
-        w[b].x = fma(-v.x, hh.x, w[b].x); w[b].x = fma(v.y, hh.y, w[b].x);
-        w[b].y = fma(-v.x, hh.y, w[b].y); w[b].y = fma(-v.y, hh.x, w[b].y);
+        p1[b] = fma(h[3 * b], sv, p1[b]);
+        p2[b] = fma(v.x, h[3 * b + 1], p2[b]);
+        p3[b] = fma(v.y, h[3 * b + 2], p3[b]);
       }
     }
 #pragma unroll
-    for (int b = 0; b < TT; ++b) Wr[b * D + g] = w[b];
+    for (int b = 0; b < TT; ++b) {
+      double2 w = Wr[b * D + g];
+      w.x -= p1[b] - p3[b];
+      w.y -= p1[b] + p2[b];
+      Wr[b * D + g] = w;
+      if (write_planes) {
+        P[(b * 3 + 0) * D + g] = w.x;
+        P[(b * 3 + 1) * D + g] = w.y - w.x;
+        P[(b * 3 + 2) * D + g] = w.x + w.y;
+      }
+    }
   }
 }
 
@@ -390,7 +468,7 @@ __device__ __forceinline__ bool qr_reduce(double (&v)[2 * TT], const KState& S, 
     for (int q = 0; q < TT; ++q) part[(size_t)blockIdx.x * TT + q] = make_double2(v[2 * q], v[2 * q + 1]);
   // the CTAs of one right-hand side meet on its own counter: right-hand sides take different
   // numbers of reductions (their deflation decisions differ)
-  if (!grid_sync(bar + r, target, err, budget, gridDim.x)) return false;
+  if (!grid_sync(bar + (size_t)r * GRID_BAR_WORDS, target, err, budget, gridDim.x)) return false;
   double w[2 * TT];
 #pragma unroll
   for (int q = 0; q < 2 * TT; ++q) w[q] = 0;
@@ -412,7 +490,7 @@ __device__ __forceinline__ bool qr_reduce(double (&v)[2 * TT], const KState& S, 
 
 // ------------------------------------------------------------------ block QR (cooperative)
 // Grid (GQ, nrhs).  Every reduction: per-CTA partials into qpart[parity], a barrier among the
-// GQ CTAs of the right-hand side (bar[r]), then every CTA of the right-hand side sums the GQ
+// GQ CTAs of the right-hand side (its own barrier words), then every CTA of the right-hand side sums the GQ
 // partials in the same order, so all of them take the same deflation decisions and run the
 // same sequence of reductions.
 template <int TT>
@@ -824,12 +902,13 @@ struct SlotSolver::Impl {
     K.tolv = dev<double>(S); K.Zcur = dev<double2*>(S); K.Vcur = dev<double2*>(S);
     K.adm = dev<int>(S); K.fin = dev<int>(S); K.xout = dev<double2*>(S); K.bdev = dev<double2>((size_t)S * D);
     W = dev<double2>((size_t)S * t * D);
-    qbar = dev<unsigned>(S);
+    K.Wp = dev<double>((size_t)S * t * 3 * D);
+    qbar = dev<unsigned>((size_t)S * GRID_BAR_WORDS);
     xstage = dev<double2>((size_t)S * D);
     d_act = dev<int>(S);
     T.src = (const double2**)dev<double2*>((size_t)S * t); T.scale = dev<double>((size_t)S * t);
     T.zdst = dev<double2*>((size_t)S * t); T.wdst = dev<double2*>((size_t)S * t);
-    if (!W || !xstage || !T.wdst || !K.bdev || !K.Rrot) return HH_ENOMEM;
+    if (!W || !K.Wp || !xstage || !T.wdst || !K.bdev || !K.Rrot) return HH_ENOMEM;
     h_act = host<int>(S); h_done = host<int>(S); h_iters = host<int>(S); h_status = host<int>(S);
     h_mask = host<int>(S); h_rho = host<double>(S); h_beta = host<double>(S); h_res = host<double>(S);
     h_tolv = host<double>(S);
@@ -903,18 +982,21 @@ struct SlotSolver::Impl {
   // nv: basis vectors of all active slots (each projected against its t new columns)
   void gs_and_qr(cudaError_t& ce, double nv, bool tick) {
     dim3 gsgrid(K.GX, S);
+    gs_wprep_kernel<TT><<<gsgrid, 256, 0, E.stream>>>(K, W);
+    E.count_launch();
     for (int pass = 0; pass < K.passes; ++pass) {
       if (tick) E.tick_begin(Engine::K_GSDOT);
-      gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K, W);
-      // one complex multiply-add (8 real flops) per basis element and new column
-      if (tick) E.tick_end(Engine::K_GSDOT, nv * D * 16.0 + (double)t * D * 16.0 * nv / 4.0, 8.0 * nv * t * D);
+      gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K);
+      // one complex multiply-add (8 real flops) per basis element and new column; the basis
+      // (16 bytes per element) is read once, the column planes (24 bytes) once per 4 vectors
+      if (tick) E.tick_end(Engine::K_GSDOT, nv * D * 16.0 + (double)t * D * 24.0 * nv / 4.0, 8.0 * nv * t * D);
       gs_reduce_kernel<<<S, 256, 0, E.stream>>>(K, pass == 0);
-      const size_t smem = (size_t)K.maxV * TT * sizeof(double2) + (size_t)K.maxV * sizeof(void*);
+      const size_t smem = (size_t)K.maxV * TT * 3 * sizeof(double) + (size_t)K.maxV * sizeof(void*);
       cudaFuncSetAttribute((const void*)gs_update_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      gs_update_kernel<TT><<<gsgrid, 256, smem, E.stream>>>(K, W);
+      gs_update_kernel<TT><<<gsgrid, 256, smem, E.stream>>>(K, W, pass + 1 < K.passes ? 1 : 0);
       E.count_launch(3);
     }
-    cudaMemsetAsync(qbar, 0, sizeof(unsigned) * S, E.stream);
+    cudaMemsetAsync(qbar, 0, sizeof(unsigned) * S * GRID_BAR_WORDS, E.stream);
     void* args[] = {(void*)&K, (void*)&W, (void*)&qbar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
     ce = E.launch_coop((const void*)qr_kernel<TT>, K.GQ, 256, 0, args, S);
   }

@@ -93,8 +93,9 @@ struct hh_server {
     const size_t C = (size_t)t * opts.serve_slots;
     const size_t sweep = 3 * (R + 1) * m * N * C * elem + 8 * m * N * C * elem;
     const size_t D = m * m;
-    // per slot: t-column W, b, staging x, and the basis block pool of about 30 iterations
-    const size_t krylov = (size_t)opts.serve_slots * D * 16 * (t + 2 + 2 * 30 * t);
+    // per slot: t-column W and its three planes (1.5 t columns), b, staging x, and the basis
+    // block pool of about 30 iterations
+    const size_t krylov = (size_t)opts.serve_slots * D * 8 * (2 * t + 3 * t + 4 + 4 * 30 * t);
     return factors + sweep + krylov + (64u << 20);
   }
 

@@ -408,7 +408,7 @@ int factor_impl(Engine& E) {
         continue;
       }
     }
-    cudaMemsetAsync(E.bar, 0, sizeof(unsigned), E.stream);
+    cudaMemsetAsync(E.bar + Engine::BAR_SETUP * GRID_BAR_WORDS, 0, GRID_BAR_WORDS * sizeof(unsigned), E.stream);
     cudaMemsetAsync(piv, 0, m * sizeof(int), E.stream);
     void* args[] = {(void*)&bufA, (void*)&bufB, (void*)&col, (void*)&piv, (void*)&m, (void*)&ld,
                     (void*)&E.bar, (void*)&E.err, (void*)&E.opts.timeout_cycles};

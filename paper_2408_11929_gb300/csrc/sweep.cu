@@ -391,6 +391,98 @@ __global__ void __launch_bounds__(256) line_gemv_split_kernel(const typename Cx<
   }
 }
 
+// Interface chains (F2 and B1 above): L narrow steps y_{s_q} (op) M x, x = line src_j of strip
+// s_q + src_ds, where strip s_q + src_ds is the one step q-1 wrote (s_q = s_0 + q dir,
+// dir = -src_ds).  One cooperative launch runs the whole chain: every CTA copies its rows of M
+// into shared memory once and keeps them for all L steps, and a grid barrier separates the
+// steps, in place of two launches (x build, GEMV) per step that each re-read M.
+template <typename T>
+struct ChainOp {
+  const T* src;
+  T* out;
+  int src_j, out_j, s0, dir, src_ds, L, out_mode, N, C;
+};
+
+template <typename R, int CMAX>
+__global__ void __launch_bounds__(1024) chain_kernel(const typename Cx<R>::T* __restrict__ A, int lda, int m,
+                                                     ChainOp<typename Cx<R>::T> op, unsigned* bar, int* err,
+                                                     long long budget) {
+  using T = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int rows = (m + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * rows, nr = max(0, min(m, r0 + rows) - r0);
+  const int C = op.C, N = op.N;
+  const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // warps per row: each takes a contiguous slice of the nodes, a multiple of 32 long
+  const int ks = max(1, nwarp / rows);
+  const int kspan = ((m + ks - 1) / ks + 31) / 32 * 32;
+  const int lr = warp / ks, kq = warp % ks;
+  T* Ms = reinterpret_cast<T*>(smem_raw);  // rows x m: this CTA's rows of M
+  T* xs = Ms + (size_t)rows * m;           // C x m, column-major (lanes read consecutive nodes)
+  T* part = xs + (size_t)m * C;            // rows x ks x C partial sums of the warps
+  T* cur0 = part + (size_t)rows * ks * CMAX;  // 2 x (rows x C): the step's output lines, by step parity
+  for (int r = 0; r < nr; ++r)
+#pragma unroll 2
+    for (int k = threadIdx.x; k < m; k += blockDim.x) Ms[(size_t)r * m + k] = __ldg(A + (size_t)(r0 + r) * lda + k);
+  unsigned target = 0;
+  for (int q = 0; q < op.L; ++q) {
+    const int s = op.s0 + q * op.dir, sx = s + op.src_ds;
+    // the output lines of this step are not written by the chain's earlier steps: fetch them
+    // before the barrier (the buffer of this parity was last read two steps ago, before the
+    // barrier that ended step q - 1 began)
+    T* cur = cur0 + (q & 1) * rows * C;
+    if (threadIdx.x < nr * C) {
+      const int r = threadIdx.x / C, c = threadIdx.x - r * C;
+      cur[threadIdx.x] = __ldcg(op.out + ((size_t)(op.out_j * m + r0 + r) * N + s) * C + c);
+    }
+    // step q - 1 wrote the line read now: every CTA's rows of it must be in place
+    if (q > 0 && !grid_sync(bar, target, err, budget)) return;
+    const T* xsrc = op.src + ((size_t)op.src_j * m * N + sx) * C;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+      T v[CMAX];
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c)
+        if (c < C) v[c] = __ldcg(xsrc + (size_t)k * N * C + c);
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c)
+        if (c < C) xs[(size_t)c * m + k] = v[c];
+    }
+    __syncthreads();
+    if (lr < nr) {
+      T acc[CMAX];
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c) acc[c] = mk<T>(0, 0);
+      const T* mrow = Ms + (size_t)lr * m;
+      const int kb = kq * kspan, ke = min(m, kb + kspan);
+#pragma unroll 2
+      for (int k = kb + lane; k < ke; k += 32) {
+        const T a = mrow[k];
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c)
+          if (c < C) cfma(acc[c], a, xs[(size_t)c * m + k]);
+      }
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c) {
+        if (c < C) {
+          T v = acc[c];
+#pragma unroll
+          for (int o = 16; o; o >>= 1) v = cadd(v, shfl_xor(v, o));
+          if (lane == 0) part[((size_t)lr * ks + kq) * CMAX + c] = v;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nr * C) {
+      const int r = threadIdx.x / C, c = threadIdx.x - r * C;
+      T z = part[(size_t)r * ks * CMAX + c];
+      for (int j = 1; j < ks; ++j) z = cadd(z, part[((size_t)r * ks + j) * CMAX + c]);
+      T* o = op.out + ((size_t)(op.out_j * m + r0 + r) * N + s) * C + c;
+      const T c0 = cur[threadIdx.x];
+      *o = op.out_mode == OUT_SET ? z : (op.out_mode == OUT_SUB ? csub(c0, z) : cadd(c0, z));
+    }
+  }
+}
+
 size_t Engine::sweep_ws_bytes(int C) const { return (size_t)(R + 1) * m * N * C * sweep_elem(); }
 
 size_t Engine::sweep_partial_bytes(int C) const { return (size_t)8 * m * N * C * sweep_elem(); }
@@ -485,7 +577,53 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
                        (int)std::min<size_t>((size_t)E.m * 8 * sizeof(T), gemv_cap));
   // allow_tick: time the wide GEMM steps one by one (a sampled, eager sweep)
   const bool tick_gemm = allow_tick && E.opts.profile;
-  for (const SweepStep& s : steps) {
+  // interface chains: one cooperative launch per run of chained narrow steps
+  constexpr int chain_threads = 1024;
+  const int chain_grid = E.num_sms;
+  const int chain_rows = (E.m + chain_grid - 1) / chain_grid;
+  const int chain_ks = std::max(1, (chain_threads / 32) / chain_rows);
+  const size_t chain_smem = ((size_t)chain_rows * E.m + (size_t)E.m * C + (size_t)chain_rows * chain_ks * 8 +
+                             2 * (size_t)chain_rows * C) * sizeof(T);
+  int chain_fit = 0;
+  const void* chain_fn = C <= 4 ? (const void*)chain_kernel<R, 4> : (const void*)chain_kernel<R, 8>;
+  if (E.opts.fuse_chains && C <= 8 && chain_rows <= chain_threads / 32 && chain_rows * C <= chain_threads &&
+      chain_smem <= 220 * 1024) {
+    cudaFuncSetAttribute(chain_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chain_fit, chain_fn, chain_threads, chain_smem);
+  }
+  auto chainable = [](const SweepStep& x) {
+    return x.ns == 1 && x.cpl == XC_IDENT && !x.neg && x.base == SB_NONE && x.acc == SB_NONE && x.src_ds != 0 &&
+           x.src == x.out && x.src_j == x.out_j;
+  };
+  for (size_t si = 0; si < steps.size(); ++si) {
+    const SweepStep& s = steps[si];
+    if (chain_fit >= 1 && chainable(s)) {
+      const int dir = -s.src_ds;
+      size_t L = 1;
+      while (si + L < steps.size()) {
+        const SweepStep& u = steps[si + L];
+        if (!chainable(u) || u.f != s.f || u.src != s.src || u.src_j != s.src_j || u.src_ds != s.src_ds ||
+            u.out_mode != s.out_mode || u.s0 != s.s0 + (int)L * dir)
+          break;
+        ++L;
+      }
+      if (L >= 2) {
+        ChainOp<T> cop{};
+        cop.src = buf(s.src); cop.out = buf(s.out);
+        cop.src_j = s.src_j; cop.out_j = s.out_j; cop.s0 = s.s0; cop.dir = dir; cop.src_ds = s.src_ds;
+        cop.L = (int)L; cop.out_mode = s.out_mode; cop.N = E.N; cop.C = C;
+        const T* A = Fb + (size_t)s.f * blk;
+        unsigned* cbar = E.bar + Engine::BAR_CHAIN * GRID_BAR_WORDS;
+        cudaMemsetAsync(cbar, 0, GRID_BAR_WORDS * sizeof(unsigned), E.stream);
+        int lda = E.ldf, mm = E.m;
+        void* args[] = {(void*)&A, (void*)&lda, (void*)&mm, (void*)&cop, (void*)&cbar, (void*)&E.err,
+                        (void*)&E.opts.timeout_cycles};
+        const cudaError_t ce = E.launch_coop(chain_fn, chain_grid, chain_threads, chain_smem, args);
+        if (ce != cudaSuccess) return ce;
+        si += L - 1;
+        continue;
+      }
+    }
     LineOperand<T> op{};
     op.base = buf(s.base); op.base_j = s.base_j;
     op.src = buf(s.src); op.src_j = s.src_j; op.src_ds = s.src_ds; op.cpl = s.cpl; op.neg = s.neg;

@@ -366,3 +366,47 @@ def test_tensor_core_step_candidates(cand):
             assert st["tc_bnc"] == (32 if cand >= 7 else 64) and st["tc_cluster"] == int(cand % 7 >= 4)
             for c in range(4):
                 assert rel(z[c], sw.apply(r[c])) < 2e-4, (d, c)
+
+
+@pytest.mark.parametrize("precision,ncols", [("fp64", 2), ("fp64", 4), ("fp32", 4), ("fp32", 8)])
+@pytest.mark.parametrize("single", [0, 1])
+def test_fused_interface_chains(precision, ncols, single):
+    """The interface chains (N-2 and N-1 dependent strip-to-strip steps of Section 2's sweep)
+    run as one cooperative launch each, factor block kept in shared memory, grid barriers
+    between the steps: the sweep equals the two-launches-per-step form to rounding and the
+    oracle's sweep within the bar, with fewer launches.  16 strips: chains of 14 and 15 steps;
+    257 node rows spread raggedly over one CTA per SM."""
+    k, n, N = 40.0, 256, 16
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], ncols, seed=11)
+    rr = np.ascontiguousarray(r.ravel())
+    bar = 1e-10 if precision == "fp64" else 2e-4
+    with hh.Handle(k, n, N, precision=precision, single_sweep=single) as hf, \
+            hh.Handle(k, n, N, precision=precision, single_sweep=single, fuse_chains=0) as hu:
+        for d in sweep.DIRECTIONS:
+            hf.apply_preconditioner(d, rr, ncols)
+            hu.apply_preconditioner(d, rr, ncols)
+            hf.reset_stats()
+            hu.reset_stats()
+            zf = hf.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+            zu = hu.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+            lf, lu = hf.stats()["kernel_launches"], hu.stats()["kernel_launches"]
+            assert lf < lu, (lf, lu)
+            assert rel(zf, zu) < (1e-12 if precision == "fp64" else 1e-4)
+            sw = sweep.Sweeper(A, k, n, N, d)
+            for c in range(ncols):
+                assert rel(zf[c], sw.apply(r[c], not single)) < bar, (d, c)
+
+
+def test_fused_interface_chain_many_rows():
+    """n = 1536: 1537 node rows over one CTA per SM puts more rows on a CTA than it has warps
+    (each warp takes several rows); the fused chains equal the per-step form to rounding."""
+    k, n, N = 600.0, 1536, 16
+    rr = np.ascontiguousarray(hh_inputs.random_vector((n + 1) ** 2, 4, seed=12).ravel())
+    with hh.Handle(k, n, N, precision="fp32", autotune=0) as hf, \
+            hh.Handle(k, n, N, precision="fp32", autotune=0, fuse_chains=0) as hu:
+        for d in ("BT", "LR"):
+            zf = hf.apply_preconditioner(d, rr, 4)
+            zu = hu.apply_preconditioner(d, rr, 4)
+            assert np.all(np.isfinite(zf))
+            assert rel(zf, zu) < 1e-4
