@@ -88,12 +88,15 @@ typedef struct {
                              profiler, whose per-launch overhead would blur the timings);
                              -(1 + 7 s + v): candidate v (K split 0 = fill the SMs, 1, 2, 4 summed
                              by a reduction kernel; 2, 4, 8 summed in a thread-block cluster) of
-                             shape s (0: 64 columns, 1: 32 columns), for tests */
+                             shape s (0: 64 columns, 1: 32 columns, 2: 128 columns), for tests */
   int fuse_chains;        /* 1 (default): each interface chain of at most 8 columns (the N-2 and
                              N-1 dependent strip-to-strip steps of a double sweep) runs as one
                              cooperative launch that keeps its factor block in shared memory and
                              puts a grid barrier between the steps; 0: two launches per step */
-  int reserved[1];
+  int overlap_steps;      /* 1 (default): each tensor-core sweep step is launched with programmatic
+                             dependent launch, so that its prologue and first factor tiles overlap
+                             the end of the preceding kernel (it waits for that kernel before it
+                             reads the line data); 0: plain stream order */
 } hh_opts;
 
 typedef struct {

@@ -401,6 +401,7 @@ void hh_default_opts(hh_opts* o) {
   o->tensor_cores = 1;
   o->autotune = 1;
   o->fuse_chains = 1;
+  o->overlap_steps = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {
@@ -549,7 +550,7 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   {
     const auto it = E.tc_tuned.find(E.last_columns);
     if (it != E.tc_tuned.end()) {
-      st->tc_bnc = it->second.shape == 1 ? 32 : 64;
+      st->tc_bnc = it->second.shape == 1 ? 32 : (it->second.shape == 2 ? 128 : 64);
       st->tc_nsplit = it->second.nsplit;
       st->tc_cluster = it->second.cluster ? 1 : 0;
       st->tc_us = it->second.us;

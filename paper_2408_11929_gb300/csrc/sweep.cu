@@ -525,20 +525,33 @@ static cudaError_t launch_tc_step(Engine& E, const LineOperand<float2>& op, int 
   const Engine::LineMaps* mb = E.line_maps_for(op.base ? op.base : Rin, C, CF::BNC);
   const Engine::LineMaps* ms = E.line_maps_for(op.src ? op.src : Rin, C, CF::BNC);
   if (!mb || !ms) return cudaErrorInvalidValue;
-  if (cluster && nsplit > 1) {
-    // the K slices of a tile form one cluster and meet in distributed shared memory
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(gx, gy, nsplit);
-    cfg.blockDim = dim3(tc::THREADS);
-    cfg.dynamicSmemBytes = CF::SMEM;
-    cfg.stream = E.stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = nsplit;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+  // launch attributes: the K slices of a tile as one cluster (they meet in distributed shared
+  // memory), and programmatic dependent launch (the step's prologue and first factor tiles
+  // overlap the end of the preceding kernel; the kernel waits for it before touching the
+  // line data)
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(gx, gy, nsplit);
+  cfg.blockDim = dim3(tc::THREADS);
+  cfg.dynamicSmemBytes = CF::SMEM;
+  cfg.stream = E.stream;
+  cudaLaunchAttribute attr[2];
+  unsigned na = 0;
+  const bool in_cluster = cluster && nsplit > 1;
+  if (in_cluster) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = 1;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = nsplit;
+    ++na;
+  }
+  if (E.opts.overlap_steps) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  if (in_cluster) {
     float2* nopartial = nullptr;
     const cudaError_t ce =
         cudaLaunchKernelEx(&cfg, tc_line_gemm_kernel<CF, true>, E.tmap_hi, E.tmap_lo, mb->base, ms->src, fblock, E.m,
@@ -547,15 +560,27 @@ static cudaError_t launch_tc_step(Engine& E, const LineOperand<float2>& op, int 
     return ce;
   }
   float2* partial = nsplit > 1 ? reinterpret_cast<float2*>(partial_buf) : nullptr;
-  tc_line_gemm_kernel<CF><<<dim3(gx, gy, nsplit), tc::THREADS, CF::SMEM, E.stream>>>(
-      E.tmap_hi, E.tmap_lo, mb->base, ms->src, fblock, E.m, op, E.coef, kchunk, partial, E.err,
-      E.opts.timeout_cycles);
+  const cudaError_t ce =
+      cudaLaunchKernelEx(&cfg, tc_line_gemm_kernel<CF, false>, E.tmap_hi, E.tmap_lo, mb->base, ms->src, fblock, E.m,
+                         op, E.coef, kchunk, partial, E.err, E.opts.timeout_cycles);
   E.count_launch();
+  if (ce != cudaSuccess) return ce;
   if (nsplit > 1) {
     split_reduce_kernel<float><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(partial, nsplit, E.m, op);
     E.count_launch();
   }
   return cudaSuccess;
+}
+
+// tile shapes of the autotuner: 0 = 64, 1 = 32, 2 = 128 complex columns per CTA
+static constexpr int kTcShapes = 3;
+static int tc_shape_columns(int shape) { return shape == 1 ? 32 : (shape == 2 ? 128 : 64); }
+static cudaError_t launch_tc_shape(Engine& E, int shape, const LineOperand<float2>& op, int fblock, int C,
+                                   int nsplit_req, const void* Rin, void* partial_buf, size_t partial_bytes,
+                                   bool cluster) {
+  if (shape == 1) return launch_tc_step<tc::Narrow>(E, op, fblock, C, nsplit_req, Rin, partial_buf, partial_bytes, cluster);
+  if (shape == 2) return launch_tc_step<tc::Huge>(E, op, fblock, C, nsplit_req, Rin, partial_buf, partial_bytes, cluster);
+  return launch_tc_step<tc::Wide>(E, op, fblock, C, nsplit_req, Rin, partial_buf, partial_bytes, cluster);
 }
 
 template <typename R>
@@ -649,10 +674,8 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
       const auto it = E.tc_tuned.find(C);
       const Engine::TcChoice ch = it != E.tc_tuned.end() ? it->second : Engine::TcChoice{};
       if (tick_gemm) E.tick_begin(Engine::K_GEMM);
-      const cudaError_t le =
-          ch.shape == 1
-              ? launch_tc_step<tc::Narrow>(E, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes, ch.cluster)
-              : launch_tc_step<tc::Wide>(E, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes, ch.cluster);
+      const cudaError_t le = launch_tc_shape(E, ch.shape, opf, s.f, C, ch.nsplit, Rin, partial_buf, partial_bytes,
+                                             ch.cluster);
       if (le != cudaSuccess) return le;
       if (tick_gemm) E.tick_end(Engine::K_GEMM, step_bytes(E, s, C), 8.0 * E.m * E.m * (double)ncols);
     } else {
@@ -823,6 +846,10 @@ int Engine::load_encoder() {
                        (int)tc::Wide::SMEM);
   cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Narrow, true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::Narrow::SMEM);
+  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Huge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::Huge::SMEM);
+  cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Huge, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tc::Huge::SMEM);
   return HH_OK;
 }
 
@@ -942,7 +969,7 @@ int Engine::tune_tc(int C, const void* Rin, void* V, void* W, void* partial, siz
   if (opts.autotune < 0) {  // one candidate, chosen by the caller: -(1 + 7 shape + variant)
     const int idx = -opts.autotune - 1;
     const int variant = idx % 7;
-    tc_tuned[C] = TcChoice{(idx / 7) % 2, kTcSplits[variant], tc_candidate_cluster(variant), 0.0};
+    tc_tuned[C] = TcChoice{(idx / 7) % kTcShapes, kTcSplits[variant], tc_candidate_cluster(variant), 0.0};
     return HH_OK;
   }
   const std::vector<SweepStep>& steps = opts.single_sweep ? steps_single : steps_double;
@@ -969,14 +996,11 @@ int Engine::tune_tc(int C, const void* Rin, void* V, void* W, void* partial, siz
   cudaEventCreate(&b);
   TcChoice best;
   best.us = 1e30;
-  for (int shape = 0; shape < 2; ++shape)
+  for (int shape = 0; shape < kTcShapes; ++shape)
     for (int variant = 0; variant < 7; ++variant) {
       const bool cl = tc_candidate_cluster(variant);
       const int ns = kTcSplits[variant];
-      auto run = [&]() {
-        return shape == 1 ? launch_tc_step<tc::Narrow>(*this, op, pick->f, C, ns, Rin, partial, partial_bytes, cl)
-                          : launch_tc_step<tc::Wide>(*this, op, pick->f, C, ns, Rin, partial, partial_bytes, cl);
-      };
+      auto run = [&]() { return launch_tc_shape(*this, shape, op, pick->f, C, ns, Rin, partial, partial_bytes, cl); };
       if (run() != cudaSuccess) {  // e.g. a cluster shape the GPU cannot co-schedule
         cudaGetLastError();
         continue;

@@ -21,9 +21,10 @@
 // lo B tiles (128-byte swizzled, K-major).  Warp 8 also owns the tensor-memory allocation;
 // lane 0 of warp 9 issues the MMAs.  Epilogue: the eight warps move the accumulator (one row
 // per thread, two column halves) into a padded shared tile, then write whole rows with
-// coalesced 16-byte stores.  Two tile shapes are compiled: 64 complex columns with three
-// 64 KB stages, and 32 columns with four 48 KB stages; the sweep's autotuner picks one per
-// column count.  Every wait is
+// coalesced 16-byte stores.  Three tile shapes are compiled: 64 complex columns with three
+// 64 KB stages, 32 columns with four 48 KB stages, and 128 columns (the factor block is read
+// by one column tile only) with two 96 KB stages; the sweep's autotuner picks one per column
+// count.  Every wait is
 #pragma once
 #include <cuda.h>
 
@@ -41,8 +42,8 @@ constexpr int TMA_WARP = BUILDERS / 32, MMA_WARP = TMA_WARP + 1;
 constexpr int THREADS = BUILDERS + 64;
 constexpr int RAW_BASE_ROWS = BKC, RAW_SRC_ROWS = BKC + 2;
 
-// Tile shape: BNC complex columns per CTA (MMA N = 2 BNC), STAGES ring slots.  Two shapes are
-// compiled and the autotuner of the sweep picks one per column count.
+// Tile shape: BNC complex columns per CTA (MMA N = 2 BNC), STAGES ring slots.  Three shapes
+// are compiled and the autotuner of the sweep picks one per column count.
 template <int BNC_, int STAGES_>
 struct Cfg {
   static constexpr int BNC = BNC_;
@@ -65,6 +66,7 @@ struct Cfg {
 };
 using Wide = Cfg<64, 3>;
 using Narrow = Cfg<32, 4>;
+using Huge = Cfg<128, 2>;  // every column of a 4-direction sweep of one right-hand side in one tile
 
 // shared-memory matrix descriptor, K-major, 128-byte swizzle: start address >> 4 (bits
 // 0-13), leading offset unused by swizzled K-major layouts (1), stride offset between 8-row
@@ -78,6 +80,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 __device__ __forceinline__ uint32_t sw128_off(int r, int j) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
 }
+
+// Programmatic dependent launch: wait until the preceding grid has completed and its memory
+// is visible (immediate when the launch did not allow overlap), and let the next grid start
+// its prologue once every CTA of this one has passed this point.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
@@ -225,22 +233,36 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       // a multiple of 4 floats, i.e. 16-byte aligned)
       const int xb = 2 * (op.s0 * op.C + colc0);
       const int xs = 2 * ((op.s0 + op.src_ds) * op.C + colc0);
-      int issued = 0;
-      for (int kt = 0; kt < nk; ++kt) {
+      auto load_a = [&](int kt) {
+        const int s = kt % STAGES;
+        unsigned char* st = sm + (size_t)s * STAGE_BYTES;
+        mbar_expect_tx(&full_a[s], 2 * TILE + raw_bytes);
+        const int x = 2 * (kbeg + kt * BKC);  // a multiple of 32 floats: 128-byte aligned
+        tc::tma_load_3d(st, &map_hi, x, row0, fblock, &full_a[s]);
+        tc::tma_load_3d(st + TILE, &map_lo, x, row0, fblock, &full_a[s]);
+      };
+      auto load_raw = [&](int kt) {
+        const int s = kt % STAGES;
+        unsigned char* rawp = sm + (size_t)s * STAGE_BYTES + 2 * TILE;
+        const int k0 = kbeg + kt * BKC;
+        if (has_base) tc::tma_load_3d(rawp, &map_base, xb, k0, op.base_j, &full_a[s]);
+        if (has_src)
+          tc::tma_load_3d(rawp + RAW_BASE_ROWS * RAW_ROW, &map_src, xs, k0 - 1, op.src_j, &full_a[s]);
+      };
+      // the factor tiles of the first ring slots do not depend on the preceding step: they
+      // are requested before waiting for it, the line rows after
+      const int pre = min(nk, STAGES);
+      for (int kt = 0; kt < pre; ++kt) load_a(kt);
+      tc::griddep_wait();
+      for (int kt = 0; kt < pre; ++kt) load_raw(kt);
+      int issued = pre;
+      for (int kt = pre; kt < nk; ++kt) {
         const int s = kt % STAGES;
         const unsigned ph = (unsigned)(kt / STAGES) & 1u;
         if (!mbar_wait(&empty[s], ph ^ 1u, err, budget)) { *(volatile int*)abort_s = 1; break; }
         if (tc::aborted(abort_s)) break;
-        unsigned char* st = sm + (size_t)s * STAGE_BYTES;
-        mbar_expect_tx(&full_a[s], 2 * TILE + raw_bytes);
-        const int k0 = kbeg + kt * BKC;
-        const int x = 2 * k0;  // a multiple of 32 floats: 128-byte aligned
-        tc::tma_load_3d(st, &map_hi, x, row0, fblock, &full_a[s]);
-        tc::tma_load_3d(st + TILE, &map_lo, x, row0, fblock, &full_a[s]);
-        unsigned char* rawp = st + 2 * TILE;
-        if (has_base) tc::tma_load_3d(rawp, &map_base, xb, k0, op.base_j, &full_a[s]);
-        if (has_src)
-          tc::tma_load_3d(rawp + RAW_BASE_ROWS * RAW_ROW, &map_src, xs, k0 - 1, op.src_j, &full_a[s]);
+        load_a(kt);
+        load_raw(kt);
         issued = kt + 1;
       }
       if (tc::aborted(abort_s)) {
@@ -273,6 +295,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         tc::commit(&empty[s]);
       }
       tc::commit(accfull);
+      tc::griddep_launch_dependents();  // every MMA of this CTA is issued
     }
   } else {
     // ---------------------------------------------------------------- B builders
@@ -350,18 +373,20 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 
     // ---------------------------------------------------------------- epilogue
     // every MMA has completed once accfull fires, so the stage area is free: the accumulator
-    // goes to a padded [128][64 + 2] complex tile, then out by whole rows
+    // goes to a padded [128][BNC + 2] complex tile, then out by whole rows
     __syncwarp();
     const bool ok = mbar_wait(accfull, 0, err, budget);
     __syncwarp();
+    tc::griddep_wait();  // the preceding grid's writes are visible before this one's
     tc::fence_after();
     float2* stile = reinterpret_cast<float2*>(sm);
     constexpr int SROW = BNC + 2;  // row stride (complex) of the staging tile
-    if ((warp >> 2) < BNC / 32) {
+    // warp w reads tensor-memory lane quarter w % 4 (the only one it may access), complex
+    // columns [32 h, 32 h + 32) for h = w / 4, w / 4 + 2, ...
+    for (int h = warp >> 2; h < BNC / 32; h += BUILDERS / 128) {
       const int wq = warp & 3;       // tensor-memory lane quarter of this warp
       const int r = wq * 32 + lane;  // accumulator row
       const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16);
-      const int h = warp >> 2;       // complex columns [32 h, 32 h + 32) of the tile
       uint32_t re[32], im[32];
       tc::tmem_ld32(trow + 32 * h, re);
       tc::tmem_ld32(trow + BNC + 32 * h, im);
@@ -375,10 +400,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     asm volatile("bar.sync 2, %0;" ::"n"(BUILDERS) : "memory");
     if (!CLUSTER && ok && !tc::aborted(abort_s)) {
       const int N = op.N, C = op.C;
-      // BNC / 2 lanes per row, each with complex columns 2l, 2l + 1
-      constexpr int LPR = BNC / 2, RPW = 32 / LPR;  // lanes per row, rows per warp pass
-      for (int r = warp * RPW + lane / LPR; r < BM; r += (BUILDERS / 32) * RPW) {
-        const int l = lane % LPR;
+      // consecutive threads take consecutive column pairs (2l, 2l + 1) of a row
+      for (int e = threadIdx.x; e < BM * (BNC / 2); e += BUILDERS) {
+        const int r = e / (BNC / 2), l = e % (BNC / 2);
         const int gr = row0 + r;
         const int gc = colc0 + 2 * l;
         if (gr >= m || gc >= ncols) continue;
@@ -405,6 +429,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   tc::fence_before();
   __syncthreads();
   if constexpr (CLUSTER) {
+    tc::griddep_wait();  // every thread below may write the step's output
     // every CTA's staged tile is complete; CTA q of the cluster sums rows
     // [q BM / nsplit, (q + 1) BM / nsplit) of all tiles in rank order and writes them
     constexpr int SROW = BNC + 2;

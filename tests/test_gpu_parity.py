@@ -351,10 +351,11 @@ def test_step_graphs_replayed_and_equal_to_eager(precision):
     assert rel(xg, xe) < (1e-12 if precision == "fp64" else 1e-5)
 
 
-@pytest.mark.parametrize("cand", range(14))
+@pytest.mark.parametrize("cand", range(21))
 def test_tensor_core_step_candidates(cand):
-    """Every candidate of the tensor-core step's autotuner (two tile shapes; K split by a
-    reduction kernel or in a thread-block cluster) gives the complex64 sweep within the bar."""
+    """Every candidate of the tensor-core step's autotuner (three tile shapes; K split by a
+    reduction kernel or in a thread-block cluster) gives the complex64 sweep within the bar.
+    8 strips x 4 columns: 32 columns, a partial tile of every shape."""
     k, n, N = 60.0, 256, 8
     A, *_ = fem.global_system(k, n)
     r = hh_inputs.random_vector(A.shape[0], 4, seed=9)
@@ -363,8 +364,24 @@ def test_tensor_core_step_candidates(cand):
             sw = sweep.Sweeper(A, k, n, N, d)
             z = h.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
             st = h.stats()
-            assert st["tc_bnc"] == (32 if cand >= 7 else 64) and st["tc_cluster"] == int(cand % 7 >= 4)
+            assert st["tc_bnc"] == (64, 32, 128)[cand // 7] and st["tc_cluster"] == int(cand % 7 >= 4)
             for c in range(4):
+                assert rel(z[c], sw.apply(r[c])) < 2e-4, (d, c)
+
+
+@pytest.mark.parametrize("variant", [0, 3, 4, 6])
+def test_tensor_core_128_column_tiles(variant):
+    """The 128-column tile shape over two column tiles (32 strips x 8 columns = 256 columns),
+    K split by the reduction kernel or in a cluster, against the oracle sweep."""
+    k, n, N = 60.0, 256, 32
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], 8, seed=10)
+    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + 14 + variant)) as h:
+        for d in ("TB", "RL"):
+            sw = sweep.Sweeper(A, k, n, N, d)
+            z = h.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 8).reshape(8, -1)
+            assert h.stats()["tc_bnc"] == 128
+            for c in range(8):
                 assert rel(z[c], sw.apply(r[c])) < 2e-4, (d, c)
 
 
@@ -410,3 +427,22 @@ def test_fused_interface_chain_many_rows():
             zu = hu.apply_preconditioner(d, rr, 4)
             assert np.all(np.isfinite(zf))
             assert rel(zf, zu) < 1e-4
+
+
+@pytest.mark.parametrize("autotune", [0, -(1 + 7 + 5), -(1 + 14 + 0)])
+def test_overlapped_tensor_core_steps_equal_plain_order(autotune):
+    """Programmatic dependent launch of the tensor-core steps (prologue and factor tiles of a
+    step overlapping the end of the previous kernel) changes only the schedule: the sweeps
+    are bit-identical to plain stream order and a whole solve agrees to rounding, for the
+    default shape, a cluster candidate and the 128-column shape."""
+    k, n, N = 60.0, 256, 8
+    rr = np.ascontiguousarray(hh_inputs.random_vector((n + 1) ** 2, 4, seed=13).ravel())
+    src = hh_inputs.centre_source()
+    with hh.Handle(k, n, N, precision="fp32", autotune=autotune) as ho, \
+            hh.Handle(k, n, N, precision="fp32", autotune=autotune, overlap_steps=0) as hp:
+        for d in sweep.DIRECTIONS:
+            assert np.array_equal(ho.apply_preconditioner(d, rr, 4), hp.apply_preconditioner(d, rr, 4)), d
+        b = ho.assemble_rhs(src)
+        xo, ro = ho.solve(b, tol=1e-6)
+        xp, rp = hp.solve(b, tol=1e-6)
+    assert ro.iterations == rp.iterations and rel(xo, xp) < 1e-12
