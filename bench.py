@@ -308,7 +308,9 @@ def run_gpu(args, ws, rank, local):
         gemm_peak = peaks["tf32_tflops"] if tc_on else peaks["fp32_alu_tflops"]
         gemm_line = {
             "bound": "tensor" if tc_on else "alu",
-            "kernel": ("tc_line_gemm_kernel (tcgen05 kind::tf32, 3 products per K step) + split_reduce_kernel"
+            "kernel": (("tc_line_gemm_kernel (tcgen05 kind::tf32, 3 products per K step)" +
+                        (", K slices summed in a thread-block cluster" if st["tc_cluster"]
+                         else " + split_reduce_kernel"))
                        if tc_on else "line_gemm_kernel<float> + split_reduce_kernel") + ": wide sweep GEMM step",
             "achieved": achieved, "peak": gemm_peak, "unit": "TFLOP/s",
             "frac": (achieved / gemm_peak) if achieved else None,
@@ -497,6 +499,38 @@ def run_batch(name: str = "k200_n512_b64") -> dict:
                           "launches_timed": st["gemm_launches"], "tile": st["tc_bnc"], "k_split": st["tc_nsplit"]}}
 
 
+def run_candidates(args):
+    """Whole 4-column BT double sweeps (k = 0.39 n) for every forced candidate of the
+    tensor-core step's autotuner (hh_opts.autotune = -(1 + cand)): 3 warm-up sweeps, then the
+    mean of 20, CUDA events on the handle's stream."""
+    import torch
+    import __graft_entry__
+    import paper_2408_11929_gb300 as hh
+    __graft_entry__.build()
+    k = 400.0 * args.n / 1024
+    dofs = (args.n + 1) ** 2
+    r = torch.from_numpy(np.ascontiguousarray(hh_inputs.random_vector(dofs, 4, seed=1).ravel())).cuda()
+    z = torch.zeros_like(r)
+    out = {}
+    for cand in range(21):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            with hh.Handle(k, args.n, args.strips, precision="fp32", autotune=-(1 + cand),
+                           stream=stream.cuda_stream) as h:
+                for _ in range(3):
+                    h.apply_preconditioner("BT", r, 4, z)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(20):
+                    h.apply_preconditioner("BT", r, 4, z)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                out[cand] = e0.elapsed_time(e1) / 20
+    print(json.dumps({"mode": "candidates", "n": args.n, "strips": args.strips, "ms_per_sweep": out}), flush=True)
+
+
 def run_sweep_only(args):
     """One direction's double sweep on 4 columns (the column count of one 4-direction solve
     iteration), k = 0.39 n, timed with CUDA events on the launching stream."""
@@ -507,7 +541,8 @@ def run_sweep_only(args):
     k = 400.0 * args.n / 1024
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        h = hh.Handle(k, args.n, args.strips, "LR+RL+BT+TB", precision=args.precision, profile=1, autotune=0,
+        h = hh.Handle(k, args.n, args.strips, "LR+RL+BT+TB", precision=args.precision, profile=1,
+                      autotune=args.autotune,
                       stream=stream.cuda_stream)
         dofs = (args.n + 1) ** 2
         r = torch.from_numpy(np.ascontiguousarray(hh_inputs.random_vector(dofs, 4, seed=1).ravel())).cuda()
@@ -548,14 +583,20 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-right-hand-side batch")
     ap.add_argument("--serve-nreq", type=int, default=40, help="requests of the mixed-k serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving stream (1/s)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "solve1"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "solve1", "candidates"],
                     help="sweep: time hh_apply_preconditioner alone (4 columns) -- the profiling case")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--strips", type=int, default=32)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="--mode solve1/sweep: hh_opts.autotune (0: the default tile; -(1 + 7 shape + variant): "
+                         "one candidate, e.g. -13 = 32 columns, 4 K slices summed in a cluster)")
     args = ap.parse_args()
     if args.mode == "sweep":
         run_sweep_only(args)
+        return
+    if args.mode == "candidates":
+        run_candidates(args)
         return
     if args.mode == "solve1":
         # setup and one solve of the default workload, nothing else: the profiling case
@@ -564,9 +605,9 @@ def main():
         import paper_2408_11929_gb300 as hh
         __graft_entry__.build()
         w = hh_inputs.workload(WORKLOAD)
-        # autotune off: under a profiler the tuner's timings are blurred by the per-launch
-        # overhead; the default shape is the one the tuner picks for this workload
-        with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", autotune=0) as h:
+        # no autotuning: under a profiler the tuner's timings are blurred by the per-launch
+        # overhead; --autotune forces the candidate the tuner picks in the live bench
+        with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", autotune=args.autotune) as h:
             b = torch.from_numpy(h.assemble_rhs(w.sources[0])).cuda()
             x, res = h.solve(b, tol=w.tol)
             torch.cuda.synchronize()

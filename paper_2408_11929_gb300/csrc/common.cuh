@@ -163,6 +163,10 @@ struct Coef {
   double diag_t;
   double2 horiz_t[3];     // by line type
   double2 centre_t[3][3]; // [line type][node class: i = 0, interior, i = n]
+  // complex64 copies of the vertical and diagonal couplings (the FP64 -> FP32 conversion
+  // also runs on the FP64 pipe)
+  float2 vert_f[2];
+  float diag_f;
 
   __host__ void init(double k_, int n_) {
     k = k_;
@@ -175,6 +179,8 @@ struct Coef {
     vert_t[1] = make_double2(2 * (-0.5 - kkh / 24.0), 0.0);
     // coupling of node (i, l) to (i-1, l-1): the diagonal of one cell (hypotenuse of both halves)
     diag_t = -kkh / 12.0;
+    for (int e = 0; e < 2; ++e) vert_f[e] = make_float2((float)vert_t[e].x, (float)vert_t[e].y);
+    diag_f = (float)diag_t;
     for (int type = 0; type < 3; ++type) {
       // coupling along a line between (i, l) and (i+1, l)
       const int cnt = (type != LINE_TOP) + (type != LINE_BOT);

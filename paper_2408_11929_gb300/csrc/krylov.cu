@@ -99,59 +99,67 @@ __device__ __forceinline__ double block_sum32_scatter(double (&v)[32], double* s
 }
 
 // ------------------------------------------------------------------ operator
+// (A x)(i, j) at node g = j m + i of one column: the P1 stencil of Section 2 (centre, the two
+// neighbours on the line, the vertical neighbours and the two diagonal ones).  On interior
+// nodes every coefficient is real (the impedance term lives on the boundary), so two FP64
+// FMAs per neighbour suffice there instead of four; the dropped products are exact zeros.
+__device__ __forceinline__ double2 stencil_row(const double2* __restrict__ xc, size_t g, int i, int j, int n,
+                                               const Coef& cf) {
+  const int m = n + 1;
+  const double dg = cf.diag();
+  const int type = line_type(j, n);
+  double2 acc;
+  if (type == LINE_INT && i >= 1 && i < n) {
+    const double c0 = cf.centre_t[LINE_INT][1].x, hz = cf.horiz_t[LINE_INT].x, vt = cf.vert_t[1].x;
+    const double2 x0 = xc[g], xe = xc[g + 1], xw = xc[g - 1], xs = xc[g - m], xsw = xc[g - m - 1];
+    const double2 xn = xc[g + m], xne = xc[g + m + 1];
+    acc.x = c0 * x0.x;             acc.y = c0 * x0.y;
+    acc.x = fma(hz, xe.x, acc.x);  acc.y = fma(hz, xe.y, acc.y);
+    acc.x = fma(hz, xw.x, acc.x);  acc.y = fma(hz, xw.y, acc.y);
+    acc.x = fma(vt, xs.x, acc.x);  acc.y = fma(vt, xs.y, acc.y);
+    acc.x = fma(dg, xsw.x, acc.x); acc.y = fma(dg, xsw.y, acc.y);
+    acc.x = fma(vt, xn.x, acc.x);  acc.y = fma(vt, xn.y, acc.y);
+    acc.x = fma(dg, xne.x, acc.x); acc.y = fma(dg, xne.y, acc.y);
+    return acc;
+  }
+  acc = make_double2(0, 0);
+  cfma(acc, cf.centre(i, type), xc[g]);
+  const double2 hz = cf.horiz(type);
+  if (i + 1 <= n) cfma(acc, hz, xc[g + 1]);
+  if (i >= 1) cfma(acc, hz, xc[g - 1]);
+  const double2 vt = cf.vert(i);
+  if (j >= 1) {
+    cfma(acc, vt, xc[g - m]);
+    if (i >= 1) { const double2 v = xc[g - m - 1]; acc.x = fma(dg, v.x, acc.x); acc.y = fma(dg, v.y, acc.y); }
+  }
+  if (j + 1 <= n) {
+    cfma(acc, vt, xc[g + m]);
+    if (i + 1 <= n) { const double2 v = xc[g + m + 1]; acc.x = fma(dg, v.x, acc.x); acc.y = fma(dg, v.y, acc.y); }
+  }
+  return acc;
+}
+
+// grid (x, ncols): blockIdx.y is the column; 32-bit node indices
 __global__ void spmv_kernel(const double2* __restrict__ x, double2* __restrict__ y, int ncols, Coef cf) {
   const int n = cf.n, m = n + 1;
-  const size_t D = (size_t)m * m;
-  const double dg = cf.diag();
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < D * ncols; idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t c = idx / D, g = idx % D;
-    const int j = (int)(g / m), i = (int)(g % m);
-    const double2* xc = x + c * D;
-    const int type = line_type(j, n);
-    double2 acc = make_double2(0, 0);
-    cfma(acc, cf.centre(i, type), xc[g]);
-    const double2 hz = cf.horiz(type);
-    if (i + 1 <= n) cfma(acc, hz, xc[g + 1]);
-    if (i >= 1) cfma(acc, hz, xc[g - 1]);
-    const double2 vt = cf.vert(i);
-    if (j >= 1) {
-      cfma(acc, vt, xc[g - m]);
-      if (i >= 1) { const double2 v = xc[g - m - 1]; acc.x += dg * v.x; acc.y += dg * v.y; }
-    }
-    if (j + 1 <= n) {
-      cfma(acc, vt, xc[g + m]);
-      if (i + 1 <= n) { const double2 v = xc[g + m + 1]; acc.x += dg * v.x; acc.y += dg * v.y; }
-    }
-    y[idx] = acc;
+  const unsigned D = (unsigned)m * (unsigned)m;
+  const size_t c = blockIdx.y;
+  for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < D; g += gridDim.x * blockDim.x) {
+    const int j = (int)(g / (unsigned)m), i = (int)(g - (unsigned)j * (unsigned)m);
+    y[c * D + g] = stencil_row(x + c * D, g, i, j, n, cf);
   }
 }
 
-// y[c] = A x[c] for columns given by pointer tables
+// y[c] = A x[c] for columns given by pointer tables; grid (x, ncols)
 __global__ void spmv_tab_kernel(const double2* const* __restrict__ xcol, double2* const* __restrict__ ycol, int ncols,
                                 Coef cf) {
   const int n = cf.n, m = n + 1;
-  const size_t D = (size_t)m * m;
-  const double dg = cf.diag();
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < D * ncols; idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t c = idx / D, g = idx % D;
-    const int j = (int)(g / m), i = (int)(g % m);
-    const double2* xc = xcol[c];
-    const int type = line_type(j, n);
-    double2 acc = make_double2(0, 0);
-    cfma(acc, cf.centre(i, type), xc[g]);
-    const double2 hz = cf.horiz(type);
-    if (i + 1 <= n) cfma(acc, hz, xc[g + 1]);
-    if (i >= 1) cfma(acc, hz, xc[g - 1]);
-    const double2 vt = cf.vert(i);
-    if (j >= 1) {
-      cfma(acc, vt, xc[g - m]);
-      if (i >= 1) { const double2 v = xc[g - m - 1]; acc.x += dg * v.x; acc.y += dg * v.y; }
-    }
-    if (j + 1 <= n) {
-      cfma(acc, vt, xc[g + m]);
-      if (i + 1 <= n) { const double2 v = xc[g + m + 1]; acc.x += dg * v.x; acc.y += dg * v.y; }
-    }
-    ycol[c][g] = acc;
+  const unsigned D = (unsigned)m * (unsigned)m;
+  const double2* xc = xcol[blockIdx.y];
+  double2* yc = ycol[blockIdx.y];
+  for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < D; g += gridDim.x * blockDim.x) {
+    const int j = (int)(g / (unsigned)m), i = (int)(g - (unsigned)j * (unsigned)m);
+    yc[g] = stencil_row(xc, g, i, j, n, cf);
   }
 }
 
@@ -615,52 +623,76 @@ __device__ void givens(double2 a, double2 b, double& c, double2& s) {
   s = cmul(ph, make_double2(b.x / rr, -b.y / rr));
 }
 
-__global__ void hess_kernel(KState S) {
-  const int r = blockIdx.x;
-  if (threadIdx.x != 0 || S.done[r]) return;
+// One warp per slot.  The new Hessenberg columns, the stored rotations (when they fit, `stage`)
+// and the block R are loaded by all lanes into shared memory (one memory latency instead of
+// one per element); lane 0 then applies the rotations in order, which is inherently sequential.
+__global__ void hess_kernel(KState S, int stage) {
+  const int r = blockIdx.x, lane = threadIdx.x;
+  if (S.done[r]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* col = reinterpret_cast<double2*>(smem_raw);
+  double2* col = reinterpret_cast<double2*>(smem_raw);  // maxZ + 2
+  // rotations: staged copies, or the stored arrays themselves
+  double2* snS = stage ? col + S.maxZ + 2 : S.sn + (size_t)r * S.maxZ;
+  double* csS = stage ? reinterpret_cast<double*>(col + 2 * S.maxZ + 2) : S.cs + (size_t)r * S.maxZ;
   const int t = S.t;
   const int nold = S.nV[r], nacc = S.nacc[r];
   const size_t D = S.D;
   double2* g = S.g + (size_t)r * (S.maxZ + 1);
   if (nacc == 0) {
-    S.status[r] = HH_EBREAKDOWN;
-    S.done[r] = 1;
+    if (lane == 0) {
+      S.status[r] = HH_EBREAKDOWN;
+      S.done[r] = 1;
+    }
     return;
   }
   int nZ = S.nZ[r];
+  if (stage)
+    for (int i = lane; i < nZ; i += blockDim.x) {
+      csS[i] = S.cs[(size_t)r * S.maxZ + i];
+      snS[i] = S.sn[(size_t)r * S.maxZ + i];
+    }
   for (int j = 0; j < t; ++j) {
     const int pos = S.amap[r * t + j];
     if (pos < 0) continue;
     const int c = nZ;
     const int len = nold + pos + 1;  // == c + 2
-    for (int i = 0; i < nold; ++i) col[i] = S.Hacc[((size_t)r * S.maxV + i) * t + j];
-    for (int q = 0; q <= pos; ++q) col[nold + q] = S.Rnew[(size_t)r * t * t + q * t + j];
-    for (int i = len; i < c + 2; ++i) col[i] = make_double2(0, 0);
-    for (int i = 0; i < c; ++i) {
-      const double cs = S.cs[(size_t)r * S.maxZ + i];
-      const double2 sn = S.sn[(size_t)r * S.maxZ + i];
-      const double2 a0 = col[i], a1 = col[i + 1];
-      col[i] = cadd(cscale(a0, cs), cmul(sn, a1));
-      const double2 msc = make_double2(-sn.x, sn.y);  // -conj(sn)
-      col[i + 1] = cadd(cmul(msc, a0), cscale(a1, cs));
+    for (int i = lane; i < nold; i += blockDim.x) col[i] = S.Hacc[((size_t)r * S.maxV + i) * t + j];
+    for (int q = lane; q <= pos; q += blockDim.x) col[nold + q] = S.Rnew[(size_t)r * t * t + q * t + j];
+    for (int i = len + lane; i < c + 2; i += blockDim.x) col[i] = make_double2(0, 0);
+    __syncwarp();
+    if (lane == 0) {
+      for (int i = 0; i < c; ++i) {
+        const double cs = csS[i];
+        const double2 sn = snS[i];
+        const double2 a0 = col[i], a1 = col[i + 1];
+        col[i] = cadd(cscale(a0, cs), cmul(sn, a1));
+        const double2 msc = make_double2(-sn.x, sn.y);  // -conj(sn)
+        col[i + 1] = cadd(cmul(msc, a0), cscale(a1, cs));
+      }
+      double cs;
+      double2 sn;
+      givens(col[c], col[c + 1], cs, sn);
+      col[c] = cadd(cscale(col[c], cs), cmul(sn, col[c + 1]));
+      csS[c] = cs;
+      snS[c] = sn;
+      if (stage) {
+        S.cs[(size_t)r * S.maxZ + c] = cs;
+        S.sn[(size_t)r * S.maxZ + c] = sn;
+      }
+      const double2 g0 = g[c];
+      g[c] = cscale(g0, cs);
+      g[c + 1] = cmul(make_double2(-sn.x, sn.y), g0);
+      S.Zptr[(size_t)r * S.maxZ + c] = S.Zcur[r] + (size_t)j * D;
     }
-    double cs;
-    double2 sn;
-    givens(col[c], col[c + 1], cs, sn);
-    col[c] = cadd(cscale(col[c], cs), cmul(sn, col[c + 1]));
-    S.cs[(size_t)r * S.maxZ + c] = cs;
-    S.sn[(size_t)r * S.maxZ + c] = sn;
+    __syncwarp();
     double2* Rc = S.Rrot + (size_t)r * ((size_t)S.maxZ * (S.maxZ + 1) / 2) + (size_t)c * (c + 1) / 2;
-    for (int i = 0; i <= c; ++i) Rc[i] = col[i];
-    const double2 g0 = g[c];
-    g[c] = cscale(g0, cs);
-    g[c + 1] = cmul(make_double2(-sn.x, sn.y), g0);
-    S.Zptr[(size_t)r * S.maxZ + c] = S.Zcur[r] + (size_t)j * D;
+    for (int i = lane; i <= c; i += blockDim.x) Rc[i] = col[i];
+    __syncwarp();
     nZ = c + 1;
   }
-  for (int q = 0; q < nacc; ++q) S.Vptr[(size_t)r * S.maxV + nold + q] = S.Vcur[r] + (size_t)q * D;
+  for (int q = lane; q < nacc; q += blockDim.x) S.Vptr[(size_t)r * S.maxV + nold + q] = S.Vcur[r] + (size_t)q * D;
+  __syncwarp();
+  if (lane != 0) return;
   S.nV[r] = nold + nacc;
   S.nZ[r] = nZ;
   const int it = S.iters[r] + 1;
@@ -720,19 +752,29 @@ __global__ void source_final_kernel(KState S) {
 }
 
 // ------------------------------------------------------------------ final solution
+// y = R^-1 g by columns, one warp per slot: once y_i is known, the lanes subtract R(k, i) y_i
+// from the right-hand side of every row k < i (column i of the packed R is contiguous), so
+// each column costs one memory latency rather than one per entry.
 __global__ void backsub_kernel(KState S) {
-  const int r = blockIdx.x;
-  if (threadIdx.x != 0 || !S.fin[r]) return;
+  const int r = blockIdx.x, lane = threadIdx.x;
+  if (!S.fin[r]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sv = reinterpret_cast<double2*>(smem_raw);  // maxZ: right-hand side being reduced
   const int nZ = S.nZ[r];
   const double2* Rb = S.Rrot + (size_t)r * ((size_t)S.maxZ * (S.maxZ + 1) / 2);
   const double2* g = S.g + (size_t)r * (S.maxZ + 1);
   double2* y = S.y + (size_t)r * S.maxZ;
+  for (int k = lane; k < nZ; k += blockDim.x) sv[k] = g[k];
+  __syncwarp();
   for (int i = nZ - 1; i >= 0; --i) {
-    double2 s = g[i];
-    for (int c = i + 1; c < nZ; ++c) s = csub(s, cmul(Rb[(size_t)c * (c + 1) / 2 + i], y[c]));
-    const double2 d = Rb[(size_t)i * (i + 1) / 2 + i];
+    const double2* Ri = Rb + (size_t)i * (i + 1) / 2;  // column i: R(0..i, i)
+    const double2 d = Ri[i];
     const double dd = cabs2(d);
-    y[i] = cmul(s, make_double2(d.x / dd, -d.y / dd));
+    const double2 yi = cmul(sv[i], make_double2(d.x / dd, -d.y / dd));
+    __syncwarp();
+    if (lane == 0) y[i] = yi;
+    for (int k = lane; k < i; k += blockDim.x) sv[k] = csub(sv[k], cmul(Ri[k], yi));
+    __syncwarp();
   }
 }
 
@@ -1064,7 +1106,7 @@ struct SlotSolver::Impl {
     if (rc) return rc;
     launch_unpack_tab(E, E.w_v, C, t, codes, T.zdst);
     if (timed) E.tick_begin(Engine::K_SPMV);
-    spmv_tab_kernel<<<E.grid_for(D * C), 256, 0, E.stream>>>(T.zdst, T.wdst, C, E.coef);
+    spmv_tab_kernel<<<dim3(std::max(1u, E.grid_for(D * C) / C), C), 256, 0, E.stream>>>(T.zdst, T.wdst, C, E.coef);
     E.count_launch();
     if (timed) E.tick_end(Engine::K_SPMV, 2.0 * C * D * 16.0, 0);
     if (timed) E.tick_begin(Engine::K_GS);
@@ -1079,9 +1121,13 @@ struct SlotSolver::Impl {
       E.tick_end(Engine::K_GS, K.passes * (2.0 * nv * D * 16 + 3.0 * C * D * 16) + 6.0 * C * D * 16,
                  K.passes * 16.0 * nv * t * D);
     if (ce != cudaSuccess) return HH_ECUDA;
-    const size_t hsmem = (size_t)(K.maxZ + 2) * sizeof(double2);
+    // the Hessenberg column, and the rotations too when they fit in shared memory
+    const size_t hcol = (size_t)(K.maxZ + 2) * sizeof(double2);
+    const size_t hrot = (size_t)K.maxZ * (sizeof(double2) + sizeof(double));
+    const int stage = hcol + hrot <= 200 * 1024;
+    const size_t hsmem = hcol + (stage ? hrot : 0);
     cudaFuncSetAttribute((const void*)hess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
-    hess_kernel<<<S, 32, hsmem, E.stream>>>(K);
+    hess_kernel<<<S, 32, hsmem, E.stream>>>(K, stage);
     source_sum_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K);
     source_final_kernel<<<S, 32, 0, E.stream>>>(K);
     E.count_launch(3);
@@ -1146,12 +1192,15 @@ struct SlotSolver::Impl {
     cudaMemcpyAsync(K.fin, h_mask, sizeof(int) * S, cudaMemcpyHostToDevice, E.stream);
     cudaMemcpyAsync(T.zdst, h_tab0, sizeof(double2*) * nfin, cudaMemcpyHostToDevice, E.stream);
     cudaMemcpyAsync(T.wdst, h_tab1, sizeof(double2*) * nfin, cudaMemcpyHostToDevice, E.stream);
-    backsub_kernel<<<S, 32, 0, E.stream>>>(K);
+    cudaFuncSetAttribute((const void*)backsub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(K.maxZ * sizeof(double2)));
+    backsub_kernel<<<S, 32, (size_t)K.maxZ * sizeof(double2), E.stream>>>(K);
     const size_t xsmem = (size_t)K.maxZ * (sizeof(double2) + sizeof(void*));
     cudaFuncSetAttribute((const void*)xsol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem);
     xsol_kernel<<<dim3(K.GX, S), 256, xsmem, E.stream>>>(K);
     E.tick_begin(Engine::K_SPMV);
-    spmv_tab_kernel<<<E.grid_for(D * nfin), 256, 0, E.stream>>>((const double2* const*)T.zdst, T.wdst, nfin, E.coef);
+    spmv_tab_kernel<<<dim3(std::max(1u, E.grid_for(D * nfin) / nfin), nfin), 256, 0, E.stream>>>(
+        (const double2* const*)T.zdst, T.wdst, nfin, E.coef);
     E.tick_end(Engine::K_SPMV, 2.0 * nfin * D * 16.0, 0);
     resid_part_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K, W);
     resid_final_kernel<<<S, 32, 0, E.stream>>>(K);
@@ -1248,7 +1297,7 @@ int Engine::solve_batch_dev(int nrhs, const double2* b, double2* x, double tol, 
 int Engine::apply_operator(int ncols, const double2* x, double2* y) {
   const size_t D = (size_t)m * m;
   tick_begin(K_SPMV);
-  spmv_kernel<<<grid_for(D * ncols), 256, 0, stream>>>(x, y, ncols, coef);
+  spmv_kernel<<<dim3(std::max(1u, grid_for(D * ncols) / ncols), ncols), 256, 0, stream>>>(x, y, ncols, coef);
   count_launch();
   tick_end(K_SPMV, 2.0 * ncols * D * 16.0, 0);
   cudaError_t e = cudaStreamSynchronize(stream);

@@ -302,9 +302,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     const int c = threadIdx.x % BNC;  // complex column within the tile
     const int pg = threadIdx.x / BNC;  // this thread forms node pairs pg, pg + PAIR_GROUPS, ... of a stage
     const bool cvalid = colc0 + c < ncols;
-    const double2 ve = cf.vert(0), vi = cf.vert(1);
-    const float2 vert_edge = make_float2((float)ve.x, (float)ve.y), vert_int = make_float2((float)vi.x, (float)vi.y);
-    const float dg = (float)cf.diag();
+    const float2 vert_edge = cf.vert_f[0], vert_int = cf.vert_f[cf.n > 1 ? 1 : 0];
+    const float dg = cf.diag_f;
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % STAGES;
       const unsigned ph = (unsigned)(kt / STAGES) & 1u;
