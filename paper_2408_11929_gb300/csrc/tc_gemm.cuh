@@ -156,10 +156,10 @@ __device__ __forceinline__ float4 ld_cluster_f4(const void* local, unsigned rank
   unsigned remote;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
   float4 v;
+  // no memory clobber: the reads follow a cluster barrier and may be issued back to back
   asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(remote)
-               : "memory");
+               : "r"(remote));
   return v;
 }
 
@@ -438,24 +438,39 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     const int rows = (BM + (int)nsplit - 1) / (int)nsplit, r0 = (int)q * rows;
     const bool good = !tc::aborted(abort_s) && *(volatile int*)err == 0;
     const int N = op.N, C = op.C;
+    auto upd = [](float2 cur, float2 z, int mode) {
+      return mode == OUT_SET ? z : (mode == OUT_SUB ? make_float2(cur.x - z.x, cur.y - z.y)
+                                                     : make_float2(cur.x + z.x, cur.y + z.y));
+    };
     for (int e = threadIdx.x; e < rows * (BNC / 2); e += THREADS) {
       const int r = r0 + e / (BNC / 2), l = e % (BNC / 2);
       if (r >= BM) break;
       const int gr = row0 + r, gc = colc0 + 2 * l;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (unsigned z = 0; z < nsplit; ++z) {
-        const float4 p = tc::ld_cluster_f4(stile + r * SROW + 2 * l, z);
-        v.x += p.x; v.y += p.y; v.z += p.z; v.w += p.w;
-      }
-      if (!good || gr >= m || gc >= ncols) continue;
-      const float2 z0 = make_float2(v.x, v.y), z1 = make_float2(v.z, v.w);
+      const bool live = good && gr < m && gc < ncols, two = gc + 1 < ncols;
       float2* o = op.out + ((size_t)(op.out_j * m + gr) * N + op.s0) * C + gc;
       float2* a2 = op.acc ? op.acc + ((size_t)(op.acc_j * m + gr) * N + op.s0) * C + gc : nullptr;
-      apply_out(o, z0, op.out_mode);
-      if (a2) apply_out(a2, op.out_mode == OUT_SET ? z0 : *o, op.acc_mode);
-      if (gc + 1 < ncols) {
-        apply_out(o + 1, z1, op.out_mode);
-        if (a2) apply_out(a2 + 1, op.out_mode == OUT_SET ? z1 : o[1], op.acc_mode);
+      // the current output values and all slices' partial sums are requested together, so
+      // that their latencies overlap; the slices are summed in rank order
+      float2 o0 = make_float2(0.f, 0.f), o1 = o0, c0 = o0, c1 = o0;
+      if (live && op.out_mode != OUT_SET) { o0 = o[0]; if (two) o1 = o[1]; }
+      if (live && a2) { c0 = a2[0]; if (two) c1 = a2[1]; }
+      float4 p[8];
+#pragma unroll
+      for (int z = 0; z < 8; ++z)
+        if (z < (int)nsplit) p[z] = tc::ld_cluster_f4(stile + r * SROW + 2 * l, (unsigned)z);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int z = 0; z < 8; ++z)
+        if (z < (int)nsplit) { v.x += p[z].x; v.y += p[z].y; v.z += p[z].z; v.w += p[z].w; }
+      if (!live) continue;
+      // the second target takes the updated output (= the sum itself for OUT_SET)
+      const float2 n0 = upd(o0, make_float2(v.x, v.y), op.out_mode);
+      o[0] = n0;
+      if (a2) a2[0] = upd(c0, n0, op.acc_mode);
+      if (two) {
+        const float2 n1 = upd(o1, make_float2(v.z, v.w), op.out_mode);
+        o[1] = n1;
+        if (a2) a2[1] = upd(c1, n1, op.acc_mode);
       }
     }
     tc::cluster_sync();  // no CTA leaves while another still reads its tile
