@@ -146,14 +146,21 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, kind: str = "simt"):
-    """DRAM bytes per launch of the wide sweep GEMM step from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+def ncu_traffic(workload: str, kind: str = "simt", bnc=None, cluster=None):
+    """DRAM bytes of one wide sweep GEMM step (all its kernels) from the committed ncu summary,
+    if it was taken on the current kernel source and, for the tensor-core step, on the tile
+    shape and reduction the autotuner chose (else None)."""
     p = os.path.join(ROOT, "profiles", "line_gemm_traffic.json" if kind == "simt" else "tc_line_gemm_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("source_hash") != kernel_source_hash():
+        return None
+    if kind == "tc":
+        for cap in d.get("captures", []):
+            if (cap["workload"] == workload and cap["complex_columns_per_cta"] == bnc
+                    and bool(cap["cluster"]) == bool(cluster)):
+                return float(cap["dram_bytes_per_step"])
         return None
     e = d.get("workloads", {}).get(workload)
     return None if e is None else float(e["dram_bytes_per_launch"])
@@ -314,7 +321,8 @@ def run_gpu(args, ws, rank, local):
                        if tc_on else "line_gemm_kernel<float> + split_reduce_kernel") + ": wide sweep GEMM step",
             "achieved": achieved, "peak": gemm_peak, "unit": "TFLOP/s",
             "frac": (achieved / gemm_peak) if achieved else None,
-            "traffic": traffic if not tc_on else ncu_traffic(WORKLOAD, "tc"),
+            "traffic": (ncu_traffic(WORKLOAD, "tc", st["tc_bnc"], st["tc_cluster"]) if tc_on
+                        else ncu_traffic(WORKLOAD)),
             "algorithmic_flops_per_launch": gemm_flops, "avg_launch_ms": gemm_ms,
             "launches_timed": st["gemm_launches"],
             "share_of_step": gemm_total_ms / step_total_ms if step_total_ms > 0 else None,
@@ -338,7 +346,6 @@ def run_gpu(args, ws, rank, local):
                     "(it reads 16 bytes per 32 flops)"}
         ranked = sorted([gemm_line, gsdot_line], key=lambda r: -(r["share_of_step"] or 0))
         dominant, others = ranked[0], ranked[1:]
-        traffic = ncu_traffic(WORKLOAD)
         g = golden(w)
         err = None
         iters_oracle = None

@@ -395,14 +395,20 @@ __global__ void __launch_bounds__(256) gs_dot_kernel(KState S) {
   }
 }
 
+// Grid (pairs / 8, slots), one warp per (basis vector, new column) pair: the lanes take every
+// 32nd CTA partial and meet in a fixed shuffle tree (the same order on every run).
 __global__ void gs_reduce_kernel(KState S, int first) {
-  const int r = blockIdx.x;
+  const int r = blockIdx.y;
   if (S.done[r]) return;
   const int cnt = S.nV[r] * S.t;
-  for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-    const size_t base = ((size_t)r * S.maxV * S.t + p);
-    double2 s = make_double2(0, 0);
-    for (int q = 0; q < S.GX; ++q) s = cadd(s, S.Hpart[base * S.GX + q]);
+  const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (p >= cnt) return;
+  const size_t base = ((size_t)r * S.maxV * S.t + p);
+  double2 s = make_double2(0, 0);
+  for (int q = lane; q < S.GX; q += 32) s = cadd(s, S.Hpart[base * S.GX + q]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s = cadd(s, shfl_xor(s, o));
+  if (lane == 0) {
     S.Hthis[base] = s;
     S.Hacc[base] = first ? s : cadd(S.Hacc[base], s);
   }
@@ -498,9 +504,19 @@ __device__ __forceinline__ bool qr_reduce(double (&v)[2 * TT], const KState& S, 
 
 // ------------------------------------------------------------------ block QR (cooperative)
 // Grid (GQ, nrhs).  Every reduction: per-CTA partials into qpart[parity], a barrier among the
-// GQ CTAs of the right-hand side (its own barrier words), then every CTA of the right-hand side sums the GQ
-// partials in the same order, so all of them take the same deflation decisions and run the
-// same sequence of reductions.
+// GQ CTAs of the right-hand side (its own barrier words), then every CTA of the right-hand side
+// sums the GQ partials in the same order, so all of them take the same deflation decisions and
+// run the same sequence of reductions.
+//
+// Column j of the block is projected against the accepted vectors q_0..q_{acc-1} (two passes
+// by default), its norm r_jj decides deflation, and q_acc = w_j / r_jj.  The phases are fused
+// so that each reduction also carries what the next step needs:
+//   R1  |w_j|^2 of every column (nu_j, the deflation reference) and <w_0, w_1>;
+//   B   (pass 2 only) w_j -= sum c1_q q_q, then the second-pass inner products <q_q, w_j>;
+//   C   w_j -= sum c_q q_q (last pass), |w_j|^2, and the first-pass inner products of the next
+//       column, <q_q, w_{j+1}> and <w_j, w_{j+1}> (= r_jj <q_acc, w_{j+1}> once w_j is accepted).
+// Every thread owns the same elements (g0 + threadIdx.x + k blockDim.x) in every phase, so the
+// phases need no synchronisation besides the reductions: t = 4 takes 7 reductions.
 template <int TT>
 __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__ W, unsigned* bar, int* err,
                                                  long long budget) {
@@ -513,6 +529,7 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
   double2* Vr = S.Vcur[r];
   __shared__ double sh[32 * 8];
   __shared__ double2 red_out[TT];
+  const double* ro = reinterpret_cast<const double*>(red_out);
   unsigned target = 0;
   int parity = 0;
   const bool writer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -523,81 +540,127 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
     return qr_reduce<TT>(v, S, r, parity, bar, target, err, budget, sh, red_out);
   };
 
-  // Every thread owns the same elements (g0 + threadIdx.x + k * blockDim.x) in every phase,
-  // so phases need no block synchronisation besides the reductions.
+  // R1: norms in doubles 0..TT-1, <w_0, w_1> in slot NS
+  constexpr int NS = (TT + 1) / 2;
   double nu[TT];
+  double2 xn = make_double2(0, 0);  // <w_j, w_{j+1}> of the column being decided
   {
     double v[2 * TT];
 #pragma unroll
     for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
     if (active)
-      for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x)
+      for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        double2 wv[TT];
 #pragma unroll
-        for (int j = 0; j < TT; ++j) v[2 * j] += cabs2(Wr[j * D + g]);
+        for (int j = 0; j < TT; ++j) {
+          wv[j] = Wr[j * D + g];
+          v[j] += cabs2(wv[j]);
+        }
+        if constexpr (TT > 1) {
+          double2 x = make_double2(v[2 * NS], v[2 * NS + 1]);
+          cfma_conj(x, wv[0], wv[1]);
+          v[2 * NS] = x.x;
+          v[2 * NS + 1] = x.y;
+        }
+      }
     if (!reduce(v)) return;
 #pragma unroll
-    for (int j = 0; j < TT; ++j) nu[j] = sqrt(red_out[j].x);
+    for (int j = 0; j < TT; ++j) nu[j] = sqrt(ro[j]);
+    if constexpr (TT > 1) xn = red_out[NS];
   }
   int acc = 0;  // accepted new vectors so far (the same in every CTA)
   int amap[TT];
+  double2 dn[TT];  // first-pass coefficients <q_q, w_{j+1}> for the next column
+#pragma unroll
+  for (int q = 0; q < TT; ++q) dn[q] = make_double2(0, 0);
+  double rj = nu[0];  // the first column has nothing to be projected against
 #pragma unroll
   for (int j = 0; j < TT; ++j) {
     double2* w = Wr + j * D;
-    double nrm = 0;  // |w_j|^2 of this thread's elements after the last pass
-    if (acc > 0) {
-      for (int pass = 0; pass < S.passes; ++pass) {
+    if (j > 0) {
+      double2 cur[TT], tot[TT];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) cur[q] = tot[q] = dn[q];
+      if (acc > 0 && S.passes >= 2) {
+        // phase B
         double v[2 * TT];
 #pragma unroll
         for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
         if (active)
           for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-            const double2 wv = w[g];
-#pragma unroll
-            for (int q = 0; q < TT - 1; ++q)
-              if (q < acc) {
-                const double2 vq = Vr[q * D + g];
-                v[2 * q] = fma(vq.x, wv.x, v[2 * q]); v[2 * q] = fma(vq.y, wv.y, v[2 * q]);
-                v[2 * q + 1] = fma(vq.x, wv.y, v[2 * q + 1]); v[2 * q + 1] = fma(-vq.y, wv.x, v[2 * q + 1]);
-              }
-          }
-        if (!reduce(v)) return;
-        double2 c[TT];
-#pragma unroll
-        for (int q = 0; q < TT; ++q) c[q] = red_out[q];
-        const bool last = pass == S.passes - 1;
-        nrm = 0;
-        if (active)
-          for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
             double2 wv = w[g];
 #pragma unroll
             for (int q = 0; q < TT - 1; ++q)
-              if (q < acc) wv = csub(wv, cmul(c[q], Vr[q * D + g]));
+              if (q < acc) wv = csub(wv, cmul(cur[q], Vr[q * D + g]));
             w[g] = wv;
-            if (last) nrm += cabs2(wv);
+#pragma unroll
+            for (int q = 0; q < TT - 1; ++q)
+              if (q < acc) {
+                double2 x = make_double2(v[2 * q], v[2 * q + 1]);
+                cfma_conj(x, Vr[q * D + g], wv);
+                v[2 * q] = x.x;
+                v[2 * q + 1] = x.y;
+              }
           }
-        if (writer && active)
+        if (!reduce(v)) return;
 #pragma unroll
-          for (int q = 0; q < TT - 1; ++q)
-            if (q < acc) {
-              double2* p = S.Rnew + (size_t)r * TT * TT + q * TT + j;
-              *p = cadd(*p, c[q]);
-            }
+        for (int q = 0; q < TT; ++q) {
+          cur[q] = q < acc ? red_out[q] : make_double2(0, 0);
+          tot[q] = cadd(tot[q], cur[q]);
+        }
       }
-    } else if (active) {
-      for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) nrm += cabs2(w[g]);
-    }
-    double v[2 * TT];
+      // phase C
+      const bool next = j + 1 < TT;
+      double v[2 * TT];
 #pragma unroll
-    for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
-    v[0] = nrm;
-    if (!reduce(v)) return;
-    const double rjj = sqrt(red_out[0].x);
+      for (int q = 0; q < 2 * TT; ++q) v[q] = 0;
+      if (active)
+        for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+          double2 wv = w[g];
+          if (acc > 0) {
+#pragma unroll
+            for (int q = 0; q < TT - 1; ++q)
+              if (q < acc) wv = csub(wv, cmul(cur[q], Vr[q * D + g]));
+            w[g] = wv;
+          }
+          v[0] += cabs2(wv);
+          if (next) {
+            // slot q + 1: <q_q, w_{j+1}> for q < acc, then <w_j, w_{j+1}> (static indices: the
+            // slots stay in registers)
+            const double2 wn = Wr[(j + 1) * D + g];
+#pragma unroll
+            for (int q = 0; q < TT - 1; ++q)
+              if (q <= acc) {
+                double2 x = make_double2(v[2 * (q + 1)], v[2 * (q + 1) + 1]);
+                cfma_conj(x, q < acc ? Vr[q * D + g] : wv, wn);
+                v[2 * (q + 1)] = x.x;
+                v[2 * (q + 1) + 1] = x.y;
+              }
+          }
+        }
+      if (!reduce(v)) return;
+      rj = sqrt(ro[0]);
+#pragma unroll
+      for (int q = 0; q < TT; ++q) dn[q] = (next && q < acc) ? red_out[q + 1] : make_double2(0, 0);
+      if (next) xn = red_out[acc + 1];
+      if (writer && active)
+#pragma unroll
+        for (int q = 0; q < TT - 1; ++q)
+          if (q < acc) {
+            double2* p = S.Rnew + (size_t)r * TT * TT + q * TT + j;
+            *p = cadd(*p, tot[q]);
+          }
+    }
     amap[j] = -1;
-    if (active && rjj > S.eta * nu[j] && rjj > 0 && isfinite(rjj)) {
-      const double inv = 1.0 / rjj;
+    if (active && rj > S.eta * nu[j] && rj > 0 && isfinite(rj)) {
+      const double inv = 1.0 / rj;
       double2* vo = Vr + acc * D;
       for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) vo[g] = cscale(w[g], inv);
-      if (writer) S.Rnew[(size_t)r * TT * TT + acc * TT + j] = make_double2(rjj, 0);
+      if (writer) S.Rnew[(size_t)r * TT * TT + acc * TT + j] = make_double2(rj, 0);
+      if (j + 1 < TT)
+#pragma unroll
+        for (int q = 0; q < TT; ++q)
+          if (q == acc) dn[q] = cscale(xn, inv);  // <q_acc, w_{j+1}>, r_jj real
       amap[j] = acc;
       ++acc;
     }
@@ -1032,7 +1095,7 @@ struct SlotSolver::Impl {
       // one complex multiply-add (8 real flops) per basis element and new column; the basis
       // (16 bytes per element) is read once, the column planes (24 bytes) once per 4 vectors
       if (tick) E.tick_end(Engine::K_GSDOT, nv * D * 16.0 + (double)t * D * 24.0 * nv / 4.0, 8.0 * nv * t * D);
-      gs_reduce_kernel<<<S, 256, 0, E.stream>>>(K, pass == 0);
+      gs_reduce_kernel<<<dim3((K.maxV * t + 7) / 8, S), 256, 0, E.stream>>>(K, pass == 0);
       const size_t smem = (size_t)K.maxV * TT * 3 * sizeof(double) + (size_t)K.maxV * sizeof(void*);
       cudaFuncSetAttribute((const void*)gs_update_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       gs_update_kernel<TT><<<gsgrid, 256, smem, E.stream>>>(K, W, pass + 1 < K.passes ? 1 : 0);
