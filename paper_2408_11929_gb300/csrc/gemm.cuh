@@ -218,6 +218,11 @@ template <typename R>
 __global__ void split_reduce_kernel(const typename Cx<R>::T* __restrict__ partial, int nsplit, int m,
                                     LineOperand<typename Cx<R>::T> op) {
   using T = typename Cx<R>::T;
+  // Launched with programmatic dependent launch after a tensor-core step: the next step may
+  // start its prologue at once, and this grid waits until the step that wrote the slices has
+  // completed (both are no-ops for a plain launch).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int ncols = op.ns * op.C;
   const size_t total = (size_t)m * ncols;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {

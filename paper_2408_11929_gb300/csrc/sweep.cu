@@ -567,8 +567,20 @@ static cudaError_t launch_tc_step(Engine& E, const LineOperand<float2>& op, int 
   E.count_launch();
   if (ce != cudaSuccess) return ce;
   if (nsplit > 1) {
-    split_reduce_kernel<float><<<E.grid_for((size_t)E.m * ncols), 256, 0, E.stream>>>(partial, nsplit, E.m, op);
+    // also with programmatic dependent launch: its CTAs wait, resident, for the step to
+    // complete, and the next step's CTAs start their prologue while it runs
+    cudaLaunchConfig_t rc{};
+    rc.gridDim = dim3(E.grid_for((size_t)E.m * ncols));
+    rc.blockDim = dim3(256);
+    rc.stream = E.stream;
+    cudaLaunchAttribute ra[1];
+    ra[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    ra[0].val.programmaticStreamSerializationAllowed = 1;
+    rc.attrs = ra;
+    rc.numAttrs = E.opts.overlap_steps ? 1 : 0;
+    const cudaError_t re = cudaLaunchKernelEx(&rc, split_reduce_kernel<float>, (const float2*)partial, nsplit, E.m, op);
     E.count_launch();
+    if (re != cudaSuccess) return re;
   }
   return cudaSuccess;
 }
