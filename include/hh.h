@@ -73,7 +73,9 @@ typedef struct {
                              Givens update, next sources) is captured once per number of active
                              right-hand sides and replayed as a CUDA graph; sweeps run on their own
                              (hh_apply_preconditioner) are captured the same way */
-  int profile;            /* 1: time every kernel class with CUDA events (hh_get_stats) */
+  int profile;            /* 0: off; 1: time every kernel class with CUDA events (hh_get_stats), with
+                             graphs on in every 8th Arnoldi step and sweep, which then run eagerly;
+                             p > 1: the same in every p-th step and sweep */
   int gs_passes;          /* Gram-Schmidt passes against the basis and within the new block:
                              2 (default, CGS2) or 1 (the single pass whose inner products
                              Section 3 counts, (k - 1/2) t^2 + 3t/2 at iteration k) */
@@ -119,8 +121,8 @@ typedef struct {
   int factor_blocks;       /* distinct m x m blocks stored (R + 1) */
   int m, ldf, columns;     /* nodes per line, padded leading dimension, sweep columns of last solve */
   int64_t sweep_steps;     /* dependent block steps of one sweep launch */
-  /* the wide GEMM steps of the sweeps, timed one by one in every 8th sweep when
-     opts.profile is set: sampled launches, their device time (ms) and their complex
+  /* the wide GEMM steps of the sweeps, timed one by one in every sampled sweep (see
+     opts.profile): sampled launches, their device time (ms) and their complex
      multiply-add flops (8 m^2 per column) */
   int64_t gemm_launches;   double gemm_ms;   double gemm_flops;
   int tensor_cores;        /* 1 when the wide sweep steps run on the tensor cores */
@@ -136,7 +138,7 @@ typedef struct {
   int tc_cluster;          /* 1 when its K slices are summed in a thread-block cluster */
   double tc_us;            /* its time per step when tuned (us) */
   int64_t iterations_total; /* Arnoldi steps run, timed or replayed from their graph (with
-                               opts.profile the classes above time every 8th step) */
+                               opts.profile the classes above time the sampled steps) */
   int step_graphs;          /* Arnoldi-step graphs captured by the handle's solvers */
   int step_graph_fallback;  /* 1 if a step could not be captured and ran eagerly */
 } hh_stats;

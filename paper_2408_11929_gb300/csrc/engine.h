@@ -131,6 +131,8 @@ class Engine {
   double bytes[K_NCLASS] = {0, 0, 0, 0, 0, 0};
   double flops[K_NCLASS] = {0, 0, 0, 0, 0, 0};
   int64_t kernel_launches = 0;
+  // with opts.profile, every sample_every-th Arnoldi step and sweep runs eagerly and timed
+  int sample_every() const { return opts.profile > 1 ? opts.profile : 8; }
   double setup_ms_total = 0;
   int last_columns = 0;
   int64_t sweep_calls = 0;

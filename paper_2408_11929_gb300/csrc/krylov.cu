@@ -1133,9 +1133,9 @@ struct SlotSolver::Impl {
       cudaMemcpyAsync(d_act, h_act, sizeof(int) * nact, cudaMemcpyHostToDevice, E.stream);
       double nv = 0;  // basis vectors of the active slots before this iteration's block
       for (int a = 0; a < nact; ++a) nv += 1.0 + (double)(slots[h_act[a]].blocks.size() / 2 - 1) * t;
-      // Every 8th iteration of a profiled handle runs eagerly with its kernels timed one class
+      // Every sample_every()-th iteration of a profiled handle runs eagerly with its kernels timed one class
       // at a time; the others replay the captured step for this number of active slots.
-      const bool timed = !E.opts.use_graph || step_graph_broken || (E.opts.profile && iter_calls % 8 == 0);
+      const bool timed = !E.opts.use_graph || step_graph_broken || (E.opts.profile && iter_calls % E.sample_every() == 0);
       ++iter_calls;
       ++E.iterations_total;
       int rc = HH_OK;

@@ -736,13 +736,13 @@ int Engine::run_sweep(const void* Rin, void* V, void* W, int C, bool single) {
 
 int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool single, void* partial,
                               size_t partial_bytes, bool allow_graph) {
-  // Every 8th sweep of a profiled handle, and the sweep of every timed Arnoldi step, times
+  // Every sample_every()-th sweep of a profiled handle, and the sweep of every timed Arnoldi step, times
   // its GEMM steps one by one and so runs eagerly; the others replay a captured graph.
   if (precision == HH_PREC_FP32 && tc_ready && allow_graph && C % 2 == 0 && !tc_tuned.count(C)) {
     const int rc = tune_tc(C, Rin, V, W, partial, partial_bytes);
     if (rc) return rc;
   }
-  const bool sampled = opts.profile && ((sweep_calls++ % 8 == 0) || sample_next_sweep);
+  const bool sampled = opts.profile && ((sweep_calls++ % sample_every() == 0) || sample_next_sweep);
   sample_next_sweep = false;
   auto launch = [&](bool tick) {
     return precision == HH_PREC_FP32
