@@ -301,6 +301,52 @@ static void setup_gemm(Engine& E, const typename Cx<R>::T* A, const typename Cx<
   E.count_launch();
 }
 
+// Starting points of Newton-Schulz when the previous block is no good start.
+// Jacobi: X = diag(1 / S_ii); contractive for the diagonally dominant line blocks (the first
+// block of a strip is one line block, tridiagonal, ||I - S X|| about 0.5 at k = 400).
+template <typename R>
+__global__ void jacobi_start_kernel(const typename Cx<R>::T* __restrict__ S, int ld, int m,
+                                    typename Cx<R>::T* __restrict__ X) {
+  using T = typename Cx<R>::T;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)m * m;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / m), c = (int)(idx % m);
+    T v = mk<T>(0, 0);
+    if (i == c) {
+      const T d = S[(size_t)i * ld + i];
+      const R dd = d.x * d.x + d.y * d.y;
+      v.x = d.x / dd;
+      v.y = -d.y / dd;
+    }
+    X[(size_t)i * ld + c] = v;
+  }
+}
+// Absolute row sums (sums[i]) and column sums (sums[m + c]) of S, for the scaled adjoint start.
+template <typename R>
+__global__ void abs_sums_kernel(const typename Cx<R>::T* __restrict__ S, int ld, int m, double* __restrict__ sums) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * m) return;
+  double s = 0;
+  if (t < m)
+    for (int c = 0; c < m; ++c) { const auto v = S[(size_t)t * ld + c]; s += sqrt((double)v.x * v.x + (double)v.y * v.y); }
+  else
+    for (int i = 0; i < m; ++i) { const auto v = S[(size_t)i * ld + (t - m)]; s += sqrt((double)v.x * v.x + (double)v.y * v.y); }
+  sums[t] = s;
+}
+// X = alpha S^H, alpha = 1 / (||S||_1 ||S||_inf): the eigenvalues of S X lie in (0, 1], so
+// Newton-Schulz converges from it for any nonsingular S (slowly at first).
+template <typename R>
+__global__ void scaled_adjoint_kernel(const typename Cx<R>::T* __restrict__ S, int ld, int m, double alpha,
+                                      typename Cx<R>::T* __restrict__ X) {
+  using T = typename Cx<R>::T;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)m * m;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / m), c = (int)(idx % m);
+    const T v = S[(size_t)c * ld + i];
+    X[(size_t)i * ld + c] = mk<T>(alpha * v.x, -alpha * v.y);
+  }
+}
+
 // F_j = S^-1 by Newton-Schulz from X_0 = F_{j-1}.  Successive Schur complements of the strip
 // recursion are close (||I - S_j F_{j-1}||_2 between 0.04 and 0.14 from j = 2 on at k = 100
 // and 200, cond(S_j) about 6), so a few iterations of two GEMMs replace the pivoted
@@ -312,7 +358,7 @@ static void setup_gemm(Engine& E, const typename Cx<R>::T* A, const typename Cx<
 template <typename R>
 static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename Cx<R>::T* X0, typename Cx<R>::T* Fj,
                           typename Cx<R>::T* Tb, typename Cx<R>::T* Xb, double* part_dev, double* part_host,
-                          int& iters) {
+                          int& iters, bool from_adjoint = false) {
   using T = typename Cx<R>::T;
   const int m = E.m, ld = E.ldf;
   const int nblk = 2 * E.num_sms;
@@ -320,7 +366,10 @@ static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename 
   T* bufs[2] = {Fj, Xb};
   double prev = 1e300;
   iters = 0;
-  for (int it = 0; it < 16; ++it) {
+  // from the scaled adjoint the residual need not shrink at first (its eigenvalues start near
+  // 1): no contraction test, more iterations
+  const int max_it = from_adjoint ? 48 : 16;
+  for (int it = 0; it < max_it; ++it) {
     setup_gemm<R>(E, S, X, Tb);
     ns_residual_kernel<R><<<nblk, 256, 0, E.stream>>>(Tb, ld, m, part_dev);
     E.count_launch();
@@ -330,7 +379,7 @@ static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename 
     for (int b = 0; b < nblk; ++b) s += part_host[b];
     const double rms = std::sqrt(s / ((double)m * m));
     const bool done = rms <= 2e-7 || (rms < 1e-4 && rms > 0.5 * prev);
-    if (it == 0 && std::sqrt(s) >= 0.9 * std::sqrt((double)m)) return false;  // not contractive
+    if (!from_adjoint && it == 0 && std::sqrt(s) >= 0.9 * std::sqrt((double)m)) return false;  // not contractive
     if (done) {
       if (X != Fj) cudaMemcpyAsync(Fj, X, sizeof(T) * (size_t)m * ld, cudaMemcpyDeviceToDevice, E.stream);
       if constexpr (sizeof(R) == 4) {
@@ -348,7 +397,7 @@ static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename 
       }
       return true;
     }
-    if (it > 2 && rms > prev) return false;  // diverging
+    if (it > 2 && rms > prev && !(from_adjoint && rms > 1e-2)) return false;  // diverging
     prev = rms;
     T* Xn = bufs[it & 1];
     setup_gemm<R>(E, X, Tb, Xn);  // X (2I - S X)
@@ -378,14 +427,17 @@ int factor_impl(Engine& E) {
   // and the residual partials)
   const bool use_ns = sizeof(R) == 4;
   T *bufC = nullptr, *bufD = nullptr;
-  double *part_dev = nullptr, *part_host = nullptr;
+  double *part_dev = nullptr, *part_host = nullptr, *sums_dev = nullptr, *sums_host = nullptr;
   if (use_ns) {
     if (E.dmalloc((void**)&bufC, mat) || E.dmalloc((void**)&bufD, mat) ||
         E.dmalloc((void**)&part_dev, sizeof(double) * 2 * E.num_sms) ||
-        cudaMallocHost((void**)&part_host, sizeof(double) * 2 * E.num_sms) != cudaSuccess) {
+        E.dmalloc((void**)&sums_dev, sizeof(double) * 2 * m) ||
+        cudaMallocHost((void**)&part_host, sizeof(double) * 2 * E.num_sms) != cudaSuccess ||
+        cudaMallocHost((void**)&sums_host, sizeof(double) * 2 * m) != cudaSuccess) {
       E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
-      E.dfree(bufC); E.dfree(bufD); E.dfree(part_dev);
+      E.dfree(bufC); E.dfree(bufD); E.dfree(part_dev); E.dfree(sums_dev);
       if (part_host) cudaFreeHost(part_host);
+      if (sums_host) cudaFreeHost(sums_host);
       return HH_ENOMEM;
     }
   }
@@ -397,11 +449,46 @@ int factor_impl(Engine& E) {
     E.tick_begin(Engine::K_SETUP);
     schur_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(X, ld, j ? 1 : 0, type, E.coef, bufA, ld, m, col);
     E.count_launch();
-    if (use_ns && j >= (E.tc_dense_ok() ? 1 : 2)) {
+    if (use_ns && E.tc_dense_ok()) {
+      // Newton-Schulz from the previous block, else from the Jacobi start (the first block is a
+      // single line block), else from the scaled adjoint; pivoted elimination is the last resort
+      int iters = 0, tried = 0;
+      bool ok = false;
+      for (int start = (j == 0 ? 1 : 0); start < 3 && !ok; ++start) {
+        const T* X0 = X;
+        if (start == 1) {
+          jacobi_start_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(bufA, ld, m, bufB);
+          E.count_launch();
+          X0 = bufB;
+        } else if (start == 2) {
+          abs_sums_kernel<R><<<(2 * m + 255) / 256, 256, 0, E.stream>>>(bufA, ld, m, sums_dev);
+          E.count_launch();
+          cudaMemcpyAsync(sums_host, sums_dev, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, E.stream);
+          if (cudaStreamSynchronize(E.stream) != cudaSuccess) break;
+          double r1 = 0, ri = 0;
+          for (int q = 0; q < m; ++q) { ri = std::max(ri, sums_host[q]); r1 = std::max(r1, sums_host[m + q]); }
+          if (!(r1 > 0 && ri > 0)) break;
+          scaled_adjoint_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(bufA, ld, m, 1.0 / (r1 * ri), bufB);
+          E.count_launch();
+          X0 = bufB;
+        }
+        int it_here = 0;
+        ok = newton_schulz<R>(E, bufA, X0, F + (size_t)j * m * ld, bufC, bufD, part_dev, part_host, it_here, start == 2);
+        iters += it_here;
+        ++tried;
+      }
+      if (ok) {
+        // 2 GEMMs per iteration, one residual GEMM per attempt, and the two of the refinement step
+        E.tick_end(Engine::K_SETUP, 0.0, (2.0 * iters + tried + 2) * 8.0 * m * (double)m * m);
+        ++E.ns_blocks;
+        E.ns_iterations += iters;
+        status = E.check_device_error("strip setup");
+        continue;
+      }
+    } else if (use_ns && j >= 2) {
       int iters = 0;
       if (newton_schulz<R>(E, bufA, X, F + (size_t)j * m * ld, bufC, bufD, part_dev, part_host, iters)) {
-        // 2 GEMMs per iteration, the final residual GEMM, and the two of the refinement step
-        E.tick_end(Engine::K_SETUP, 0.0, (2.0 * iters + 1 + (E.tc_dense_ok() ? 2 : 0)) * 8.0 * m * (double)m * m);
+        E.tick_end(Engine::K_SETUP, 0.0, (2.0 * iters + 1) * 8.0 * m * (double)m * m);
         ++E.ns_blocks;
         E.ns_iterations += iters;
         status = E.check_device_error("strip setup");
@@ -426,8 +513,9 @@ int factor_impl(Engine& E) {
   if (status == HH_OK) status = E.check_device_error("strip setup");
   if (status == HH_OK) status = interface_blocks<R>(E, bufA, bufB);
   E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
-  E.dfree(bufC); E.dfree(bufD); E.dfree(part_dev);
+  E.dfree(bufC); E.dfree(bufD); E.dfree(part_dev); E.dfree(sums_dev);
   if (part_host) cudaFreeHost(part_host);
+  if (sums_host) cudaFreeHost(sums_host);
   return status;
 }
 
