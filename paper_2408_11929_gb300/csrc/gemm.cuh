@@ -245,6 +245,8 @@ constexpr size_t line_gemm_smem() {
 }
 
 // Setup GEMM: C = alpha * A * B (all m x m, row-major, leading dimensions lda / ldb / ldc).
+// The next K tile is copied into the other shared-memory buffer by cp.async while the current
+// one is multiplied (two buffers, one copy group in flight).
 template <typename R, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256) dense_gemm_kernel(const typename Cx<R>::T* __restrict__ A, int lda,
                                                          const typename Cx<R>::T* __restrict__ B, int ldb,
@@ -263,13 +265,16 @@ __global__ void __launch_bounds__(256) dense_gemm_kernel(const typename Cx<R>::T
     for (int e = tid; e < BK * BM; e += 256) {
       const int r = e / BK, kk = e % BK;  // consecutive threads walk along a row of A
       const int gr = row0 + r, gk = k0 + kk;
-      As[buf][kk][r] = (gr < m && gk < m) ? __ldg(A + (size_t)gr * lda + gk) : mk<T>(0, 0);
+      const bool ok = gr < m && gk < m;
+      cp_async_elem(&As[buf][kk][r], ok ? A + (size_t)gr * lda + gk : A, ok);
     }
     for (int e = tid; e < BK * BN; e += 256) {
       const int kk = e / BN, cc = e % BN;
       const int gk = k0 + kk, gc = col0 + cc;
-      Bs[buf][kk][cc] = (gk < m && gc < m) ? __ldg(B + (size_t)gk * ldb + gc) : mk<T>(0, 0);
+      const bool ok = gk < m && gc < m;
+      cp_async_elem(&Bs[buf][kk][cc], ok ? B + (size_t)gk * ldb + gc : B, ok);
     }
+    cp_async_commit();
   };
   R acc[TM][TN][2];
 #pragma unroll
@@ -278,9 +283,11 @@ __global__ void __launch_bounds__(256) dense_gemm_kernel(const typename Cx<R>::T
     for (int b = 0; b < TN; ++b) acc[a][b][0] = acc[a][b][1] = 0;
   const int nk = (m + BK - 1) / BK;
   load_tile(0, 0);
-  __syncthreads();
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
+    // tile kt has landed, and every thread is done with tile kt - 1, whose buffer is refilled
+    cp_async_wait<0>();
+    __syncthreads();
     if (kt + 1 < nk) load_tile(cur ^ 1, (kt + 1) * BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
@@ -299,7 +306,6 @@ __global__ void __launch_bounds__(256) dense_gemm_kernel(const typename Cx<R>::T
           acc[p][q][1] = fma(a[p].y, x[q].x, acc[p][q][1]);
         }
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int p = 0; p < TM; ++p) {
