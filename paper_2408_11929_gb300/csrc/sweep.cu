@@ -587,7 +587,6 @@ static cudaError_t launch_tc_step(Engine& E, const LineOperand<float2>& op, int 
 
 // tile shapes of the autotuner: 0 = 64, 1 = 32, 2 = 128 complex columns per CTA
 static constexpr int kTcShapes = 3;
-static int tc_shape_columns(int shape) { return shape == 1 ? 32 : (shape == 2 ? 128 : 64); }
 static cudaError_t launch_tc_shape(Engine& E, int shape, const LineOperand<float2>& op, int fblock, int C,
                                    int nsplit_req, const void* Rin, void* partial_buf, size_t partial_bytes,
                                    bool cluster) {
