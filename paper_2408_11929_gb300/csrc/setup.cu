@@ -321,17 +321,32 @@ __global__ void jacobi_start_kernel(const typename Cx<R>::T* __restrict__ S, int
     X[(size_t)i * ld + c] = v;
   }
 }
-// Absolute row sums (sums[i]) and column sums (sums[m + c]) of S, for the scaled adjoint start.
+// Absolute row sums (sums[i]) and column sums (sums[m + c]) of S, for the scaled adjoint start
+// (only a bound is needed: moduli in the element precision, sums in FP64).  Warp w < m sums row
+// w with its lanes along the row; the threads of the remaining blocks take one column each.
 template <typename R>
-__global__ void abs_sums_kernel(const typename Cx<R>::T* __restrict__ S, int ld, int m, double* __restrict__ sums) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * m) return;
+__global__ void abs_sums_kernel(const typename Cx<R>::T* __restrict__ S, int ld, int m, double* __restrict__ sums,
+                                int row_blocks) {
+  if ((int)blockIdx.x < row_blocks) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= m) return;
+    double s = 0;
+    for (int c = lane; c < m; c += 32) {
+      const auto v = S[(size_t)w * ld + c];
+      s += (double)sqrt(v.x * v.x + v.y * v.y);
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sums[w] = s;
+    return;
+  }
+  const int c = ((int)blockIdx.x - row_blocks) * blockDim.x + threadIdx.x;
+  if (c >= m) return;
   double s = 0;
-  if (t < m)
-    for (int c = 0; c < m; ++c) { const auto v = S[(size_t)t * ld + c]; s += sqrt((double)v.x * v.x + (double)v.y * v.y); }
-  else
-    for (int i = 0; i < m; ++i) { const auto v = S[(size_t)i * ld + (t - m)]; s += sqrt((double)v.x * v.x + (double)v.y * v.y); }
-  sums[t] = s;
+  for (int i = 0; i < m; ++i) {
+    const auto v = S[(size_t)i * ld + c];
+    s += (double)sqrt(v.x * v.x + v.y * v.y);
+  }
+  sums[m + c] = s;
 }
 // X = alpha S^H, alpha = 1 / (||S||_1 ||S||_inf): the eigenvalues of S X lie in (0, 1], so
 // Newton-Schulz converges from it for any nonsingular S (slowly at first).
@@ -461,7 +476,8 @@ int factor_impl(Engine& E) {
           E.count_launch();
           X0 = bufB;
         } else if (start == 2) {
-          abs_sums_kernel<R><<<(2 * m + 255) / 256, 256, 0, E.stream>>>(bufA, ld, m, sums_dev);
+          const int row_blocks = (m + 7) / 8;  // 8 warps (rows) per block of 256 threads
+          abs_sums_kernel<R><<<row_blocks + (m + 255) / 256, 256, 0, E.stream>>>(bufA, ld, m, sums_dev, row_blocks);
           E.count_launch();
           cudaMemcpyAsync(sums_host, sums_dev, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, E.stream);
           if (cudaStreamSynchronize(E.stream) != cudaSuccess) break;
