@@ -875,18 +875,21 @@ void Engine::free_dense_scratch() {
 // Rows [r0, m) of C = (+/-) A B (+ C), on the CUDA cores in FP32: the few rows below the last
 // full 128-row tile, so that the tensor-core grid fits in one wave (at m = 1025 a full grid
 // is 9 x 17 = 153 CTAs of one per SM: the 153rd would run alone).  A is read as hi + lo (its
-// exact split), since C may be A itself.  Grid (columns / 32, rows); 8 warps split K.
-__global__ void __launch_bounds__(256) dense_tail_rows_kernel(const float2* __restrict__ Ahi,
-                                                              const float2* __restrict__ Alo,
-                                                              const float2* __restrict__ B, float2* Cm, int ld,
-                                                              int m, int r0, int neg, int add) {
-  __shared__ float2 part[8][32];
+// exact split), since C may be A itself.  Grid (columns / 32, rows); 32 warps split K.  It
+// lets the tensor-core kernel (launched next, with programmatic dependent launch) start at
+// once: the two run side by side, on disjoint rows of C.
+__global__ void __launch_bounds__(1024) dense_tail_rows_kernel(const float2* __restrict__ Ahi,
+                                                               const float2* __restrict__ Alo,
+                                                               const float2* __restrict__ B, float2* Cm, int ld,
+                                                               int m, int r0, int neg, int add) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  __shared__ float2 part[32][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane, r = r0 + blockIdx.y;
   float2 acc = make_float2(0.f, 0.f);
   if (c < m) {
 #pragma unroll 4
-    for (int k = w; k < m; k += 8) {
+    for (int k = w; k < m; k += 32) {
       const float2 h = Ahi[(size_t)r * ld + k], l = Alo[(size_t)r * ld + k];
       cfma(acc, make_float2(h.x + l.x, h.y + l.y), B[(size_t)k * ld + c]);
     }
@@ -896,7 +899,7 @@ __global__ void __launch_bounds__(256) dense_tail_rows_kernel(const float2* __re
   if (w == 0 && c < m) {
     float2 z = part[0][lane];
 #pragma unroll
-    for (int q = 1; q < 8; ++q) z = cadd(z, part[q][lane]);
+    for (int q = 1; q < 32; ++q) z = cadd(z, part[q][lane]);
     if (neg) z = make_float2(-z.x, -z.y);
     float2* o = Cm + (size_t)r * ld + c;
     *o = add ? cadd(*o, z) : z;
@@ -963,15 +966,30 @@ int Engine::tc_dense_gemm(const void* A, const void* B, void* C, bool negate_b, 
   const int full = m / tc::BM, tail = m - full * tc::BM;
   const bool split_tail = gx * gy > num_sms && full >= 1 && tail > 0 && tail <= 8 && full * gy <= num_sms;
   if (split_tail) {
-    dense_tail_rows_kernel<<<dim3((m + 31) / 32, tail), 256, 0, stream>>>(
+    dense_tail_rows_kernel<<<dim3((m + 31) / 32, tail), 1024, 0, stream>>>(
         reinterpret_cast<const float2*>(dense_hi), reinterpret_cast<const float2*>(dense_lo),
         reinterpret_cast<const float2*>(B), reinterpret_cast<float2*>(C), ldf, m, full * tc::BM, negate_b ? 1 : 0,
         add ? 1 : 0);
     count_launch();
   }
-  tc_line_gemm_kernel<tc::Wide><<<dim3(split_tail ? full : gx, gy, 1), tc::THREADS, tc::Wide::SMEM, stream>>>(
-      dense_map_hi, dense_map_lo, dm->base, dm->src, 0, m, op, coef, kchunk, nullptr, err, opts.timeout_cycles);
+  // after the tail kernel: programmatic dependent launch, so that the two overlap (the
+  // tensor-core kernel waits for it only before writing its output)
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(split_tail ? full : gx, gy, 1);
+  cfg.blockDim = dim3(tc::THREADS);
+  cfg.dynamicSmemBytes = tc::Wide::SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = split_tail ? 1 : 0;
+  float2* nopartial = nullptr;
+  const cudaError_t ce = cudaLaunchKernelEx(&cfg, tc_line_gemm_kernel<tc::Wide, false>, dense_map_hi, dense_map_lo,
+                                            dm->base, dm->src, 0, m, op, coef, kchunk, nopartial, err,
+                                            opts.timeout_cycles);
   count_launch(2);
+  if (ce != cudaSuccess) return (set_cuda_error(ce, "tensor-core setup GEMM launch"), HH_ECUDA);
   return HH_OK;
 }
 
