@@ -10,6 +10,9 @@
 // F_j = S_j^{-1} (m x m, m = n+1) are the stored factors.  L couples a line to the line
 // below (vertical edge + cell diagonal), U = L^T.
 //
+// The inverses: complex64 blocks by Newton-Schulz (GEMMs on the tensor cores, started from the
+// previous block, the Jacobi start or the scaled adjoint), pivoted Gauss-Jordan otherwise.
+//
 // For the sweep's interface chains (sweep.cu) setup also forms, for the strips visited
 // before the last one, the first-line response of the strip inverse at its last line,
 //     Y_0 = F_0,  Y_j = -F_j L Y_{j-1}   (j = 1..R-1),   Y_{R-1} = D^{-1}[R-1, 0],
@@ -438,8 +441,9 @@ int factor_impl(Engine& E) {
   int grid = E.num_sms < m ? E.num_sms : m;
   const size_t smem = 0;
   int status = HH_OK;
-  // Newton-Schulz for complex64 factors from the third block on (scratch: two more matrices
-  // and the residual partials)
+  // Newton-Schulz for complex64 factors (every block with the tensor cores, from the third
+  // block on without; scratch: two more matrices, the residual partials and the absolute row
+  // and column sums of the scaled adjoint start)
   const bool use_ns = sizeof(R) == 4;
   T *bufC = nullptr, *bufD = nullptr;
   double *part_dev = nullptr, *part_host = nullptr, *sums_dev = nullptr, *sums_host = nullptr;
