@@ -19,6 +19,7 @@ import hashlib
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -76,7 +77,10 @@ class ClockSampler:
     def __init__(self, index: int = 0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples: HH_CLOCKS_DIR if set, else the temporary directory (the JSON line carries
+        # the summary)
+        out_dir = os.environ.get("HH_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
