@@ -134,9 +134,9 @@ typedef struct {
   int ns_blocks;           /* strip inverses computed by Newton-Schulz from the previous one */
   int ns_iterations;       /* their iterations (two GEMMs each) */
   int tc_bnc, tc_nsplit;   /* autotuned tensor-core step for the last column count: complex
-                              columns per CTA (64 or 32) and K split (0 = fill the SMs) */
+                              columns per CTA (64, 32 or 128) and K split (0 = fill the SMs) */
   int tc_cluster;          /* 1 when its K slices are summed in a thread-block cluster */
-  double tc_us;            /* its time per step when tuned (us) */
+  double tc_us;            /* its time per step when tuned (us; a run of consecutive steps) */
   int64_t iterations_total; /* Arnoldi steps run, timed or replayed from their graph (with
                                opts.profile the classes above time the sampled steps) */
   int step_graphs;          /* Arnoldi-step graphs captured by the handle's solvers */
