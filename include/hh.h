@@ -198,8 +198,9 @@ hh_status hh_apply_preconditioner(hh_handle* h, uint32_t dir, int ncols, const d
  *   - r and z must be DEVICE pointers (ncols complex128 columns); host pointers -> HH_EINVAL;
  *   - a grid / column count whose packed sweep arrays exceed the 32 MiB -> HH_EINVAL
  *     (roughly: complex64 factors up to n = 512 with 4 columns, n = 1024 not at all);
- *   - the first call on a device resolves the array's device address (once per device);
- *     make that first call before any stream capture;
+ *   - hh_setup resolves the array's device address once per device (which also loads the
+ *     module holding it, so that the array is reserved on the device from then on); this
+ *     entry point itself only reads that address;
  *   - every call shares the one array and leaves its contents behind; nothing in it needs to
  *     start at zero; calls whose GPU work overlaps (other handles, other streams, other
  *     threads) race on it and must be serialised by the caller.

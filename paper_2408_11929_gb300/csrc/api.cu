@@ -19,6 +19,7 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 int qr_blocks_per_sm();
+int noalloc_scratch_address(int device, void** out);
 
 // ------------------------------------------------------------------ engine helpers
 int Engine::dmalloc(void** p, size_t nbytes) {
@@ -158,6 +159,13 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
     own_stream = true;
   }
   coop_per_sm = std::max(1, qr_blocks_per_sm());
+  {
+    // loads the module of the no-allocation entry point on this device, which reserves its
+    // fixed scratch array now rather than at that entry point's first call
+    void* scratch = nullptr;
+    const int rc = noalloc_scratch_address(device, &scratch);
+    if (rc) return rc;
+  }
 
   const size_t fbytes = (size_t)factor_blocks() * m * ldf * sweep_elem();
   size_t free_b = 0, total_b = 0;

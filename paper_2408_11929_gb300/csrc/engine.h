@@ -87,7 +87,7 @@ class Engine {
     int C = -1, bnc = 0;
     CUtensorMap base{}, src{};
   };
-  LineMaps line_maps[8];
+  LineMaps line_maps[16];
   int line_maps_next = 0;
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
   const LineMaps* line_maps_for(const void* buf, int C, int bnc);

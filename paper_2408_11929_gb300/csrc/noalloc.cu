@@ -5,8 +5,11 @@
 // cudaMalloc / cudaFree (which can synchronise the whole device).  The kernels are the
 // same as hh_apply_preconditioner's; only their scratch moves: the packed input, the
 // sweep output, the correction array, the column tables and the split-K slices live in one
-// file-scope device array of fixed size, reserved in every GPU's memory by the loader
-// when the library is loaded and held until the process exits.
+// file-scope device array of fixed size.  The array is reserved on a device when this file's
+// module is loaded there, which CUDA's lazy module loading does at the first use of one of its
+// symbols; hh_setup makes that use (it resolves the array's device address), so the array is
+// reserved on the handle's device before any call of this entry point, and held until the
+// process exits.
 //
 // Scratch contents: nothing in the array has to start at zero.  Each call rewrites the
 // whole packed input (padding entries included) and the column tables, and every sweep step
@@ -33,12 +36,12 @@ constexpr size_t kNoAllocScratchBytes = 32ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of g_noalloc_scratch for each device, resolved once per device (with that
-// device current) by the first call that runs on it.
+// device current) by the first hh_setup on it.
 constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[kMaxDevices] = {};
 
-static int noalloc_scratch_address(int device, void** out) {
+int noalloc_scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) {
     set_error("device index out of range for the no-allocation scratch");
     return HH_EINVAL;

@@ -522,9 +522,16 @@ static cudaError_t launch_tc_step(Engine& E, const LineOperand<float2>& op, int 
     while (nsplit > 1 && (size_t)nsplit * E.m * ncols * sizeof(float2) > partial_bytes) --nsplit;
   const int kchunk = ((E.m + nsplit - 1) / nsplit + tc::BKC - 1) / tc::BKC * tc::BKC;
   nsplit = (E.m + kchunk - 1) / kchunk;  // no empty split
-  const Engine::LineMaps* mb = E.line_maps_for(op.base ? op.base : Rin, C, CF::BNC);
-  const Engine::LineMaps* ms = E.line_maps_for(op.src ? op.src : Rin, C, CF::BNC);
-  if (!mb || !ms) return cudaErrorInvalidValue;
+  // the maps are copied out at once: the second lookup may evict the first one's ring slot
+  CUtensorMap map_base, map_src;
+  {
+    const Engine::LineMaps* mb = E.line_maps_for(op.base ? op.base : Rin, C, CF::BNC);
+    if (!mb) return cudaErrorInvalidValue;
+    map_base = mb->base;
+    const Engine::LineMaps* ms = E.line_maps_for(op.src ? op.src : Rin, C, CF::BNC);
+    if (!ms) return cudaErrorInvalidValue;
+    map_src = ms->src;
+  }
   // launch attributes: the K slices of a tile as one cluster (they meet in distributed shared
   // memory), and programmatic dependent launch (the step's prologue and first factor tiles
   // overlap the end of the preceding kernel; the kernel waits for it before touching the
@@ -555,14 +562,14 @@ static cudaError_t launch_tc_step(Engine& E, const LineOperand<float2>& op, int 
   if (in_cluster) {
     float2* nopartial = nullptr;
     const cudaError_t ce =
-        cudaLaunchKernelEx(&cfg, tc_line_gemm_kernel<CF, true>, E.tmap_hi, E.tmap_lo, mb->base, ms->src, fblock, E.m,
+        cudaLaunchKernelEx(&cfg, tc_line_gemm_kernel<CF, true>, E.tmap_hi, E.tmap_lo, map_base, map_src, fblock, E.m,
                            op, E.coef, kchunk, nopartial, E.err, E.opts.timeout_cycles);
     E.count_launch();
     return ce;
   }
   float2* partial = nsplit > 1 ? reinterpret_cast<float2*>(partial_buf) : nullptr;
   const cudaError_t ce =
-      cudaLaunchKernelEx(&cfg, tc_line_gemm_kernel<CF, false>, E.tmap_hi, E.tmap_lo, mb->base, ms->src, fblock, E.m,
+      cudaLaunchKernelEx(&cfg, tc_line_gemm_kernel<CF, false>, E.tmap_hi, E.tmap_lo, map_base, map_src, fblock, E.m,
                          op, E.coef, kchunk, partial, E.err, E.opts.timeout_cycles);
   E.count_launch();
   if (ce != cudaSuccess) return ce;
@@ -1120,7 +1127,7 @@ const Engine::LineMaps* Engine::line_maps_for(const void* buf, int C, int bnc) {
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(encode_fn);
   if (!encode || C % 2) return nullptr;
   LineMaps& lm = line_maps[line_maps_next];
-  line_maps_next = (line_maps_next + 1) % 8;
+  line_maps_next = (line_maps_next + 1) % 16;
   const cuuint64_t dims[3] = {(cuuint64_t)2 * N * C, (cuuint64_t)m, (cuuint64_t)(R + 1)};
   const cuuint64_t strides[2] = {(cuuint64_t)2 * N * C * sizeof(float), (cuuint64_t)m * 2 * N * C * sizeof(float)};
   const cuuint32_t estr[3] = {1, 1, 1};

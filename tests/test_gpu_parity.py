@@ -399,8 +399,10 @@ def test_fused_interface_chains(precision, ncols, single):
     r = hh_inputs.random_vector(A.shape[0], ncols, seed=11)
     rr = np.ascontiguousarray(r.ravel())
     bar = 1e-10 if precision == "fp64" else 2e-4
-    with hh.Handle(k, n, N, precision=precision, single_sweep=single) as hf, \
-            hh.Handle(k, n, N, precision=precision, single_sweep=single, fuse_chains=0) as hu:
+    # both handles run the same tensor-core candidate (the autotuner could give them forms
+    # with different launches per wide step), so the launch counts differ by the fusion only
+    with hh.Handle(k, n, N, precision=precision, single_sweep=single, autotune=0) as hf, \
+            hh.Handle(k, n, N, precision=precision, single_sweep=single, fuse_chains=0, autotune=0) as hu:
         for d in sweep.DIRECTIONS:
             hf.apply_preconditioner(d, rr, ncols)
             hu.apply_preconditioner(d, rr, ncols)
@@ -447,3 +449,19 @@ def test_overlapped_tensor_core_steps_equal_plain_order(autotune):
         xo, ro = ho.solve(b, tol=1e-6)
         xp, rp = hp.solve(b, tol=1e-6)
     assert ro.iterations == rp.iterations and rel(xo, xp) < 1e-12
+
+
+def test_tensor_map_cache_turnover():
+    """The tensor maps of the sweep arrays are cached in a ring keyed by (array, columns,
+    tile shape); sweeps over many column counts on one handle turn the ring over several
+    times, and every sweep still equals the oracle's (a step whose two maps were looked up
+    across an eviction would read the wrong array)."""
+    k, n, N = 20.0, 64, 4
+    A, *_ = fem.global_system(k, n)
+    sw = sweep.Sweeper(A, k, n, N, "LR")
+    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + 7 + 5)) as h:
+        for ncols in (2, 4, 6, 8, 10, 12, 14, 16, 2, 4):
+            r = hh_inputs.random_vector(A.shape[0], ncols, seed=20 + ncols)
+            z = h.apply_preconditioner("LR", np.ascontiguousarray(r.ravel()), ncols).reshape(ncols, -1)
+            for c in range(ncols):
+                assert rel(z[c], sw.apply(r[c])) < 2e-4, (ncols, c)

@@ -33,23 +33,44 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_noalloc_matches_allocating_entry_point(precision):
+def noalloc(h, d, ncols, r, torch):
+    z = torch.full_like(r, complex(np.nan, np.nan))
+    st = h.lib.hh_apply_preconditioner_noalloc(h.h, hh.DIR_BITS[d], ncols, ctypes.c_void_p(r.data_ptr()),
+                                               ctypes.c_void_p(z.data_ptr()))
+    torch.cuda.synchronize()
+    assert st == hh.HH_OK, h.lib.hh_last_error()
+    return z
+
+
+# complex64 with an even column count runs the tensor-core step (tensor maps over the fixed
+# array, split-K slices in what is left of it); an odd count and complex128 the CUDA-core one
+@pytest.mark.parametrize("precision,ncols", [("fp64", 3), ("fp32", 2), ("fp32", 3), ("fp32", 4)])
+def test_noalloc_matches_allocating_entry_point(precision, ncols):
     torch = pytest.importorskip("torch")
-    k, n, N, ncols = 30.0, 64, 4, 3
+    k, n, N = 30.0, 64, 4
     dofs = (n + 1) ** 2
     r = torch.from_numpy(np.ascontiguousarray(hh_inputs.random_vector(dofs, ncols, seed=5).ravel())).cuda()
     with hh.Handle(k, n, N, precision=precision) as h:
-        lib = h.lib
         for d in ("LR", "TB", "BT", "RL"):
             z_ref = h.apply_preconditioner(d, r, ncols)
             for call in range(2):  # two calls in a row reuse the scratch left by the previous one
-                z = torch.full_like(r, complex(np.nan, np.nan))
-                st = lib.hh_apply_preconditioner_noalloc(h.h, hh.DIR_BITS[d], ncols, ctypes.c_void_p(r.data_ptr()),
-                                                         ctypes.c_void_p(z.data_ptr()))
-                torch.cuda.synchronize()
-                assert st == hh.HH_OK, lib.hh_last_error()
+                z = noalloc(h, d, ncols, r, torch)
                 assert rel(z, z_ref) <= TOL[precision], (d, call)
+
+
+def test_noalloc_before_any_allocating_call():
+    """The first calls on a fresh handle, before the allocating entry point has run (so no
+    tensor-core candidate has been tuned for the column count), agree with a later
+    allocating call."""
+    torch = pytest.importorskip("torch")
+    k, n, N, ncols = 30.0, 64, 4, 4
+    dofs = (n + 1) ** 2
+    r = torch.from_numpy(np.ascontiguousarray(hh_inputs.random_vector(dofs, ncols, seed=7).ravel())).cuda()
+    with hh.Handle(k, n, N, precision="fp32") as h:
+        z = [noalloc(h, "BT", ncols, r, torch) for _ in range(2)]
+        z_ref = h.apply_preconditioner("BT", r, ncols)
+        for call in range(2):
+            assert rel(z[call], z_ref) <= TOL["fp32"], call
 
 
 def test_noalloc_rejects_what_it_cannot_serve():
