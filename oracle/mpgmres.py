@@ -12,7 +12,12 @@ One iteration:
   3. The t columns of W are then orthonormalised one after the other, in preconditioner
      order, each by classical Gram-Schmidt against the new vectors already accepted in this
      iteration (again twice), giving a real positive diagonal r_jj.  Column j is DEFLATED (its Z column dropped)
-     when r_jj <= eta * ||w_j||, ||w_j|| taken after step 2.
+     when r_jj <= eta * ||A z_j||, the norm of the new column before any Gram-Schmidt: the
+     part of A z_j outside the span of everything before it is then below eta of its size,
+     so the direction is numerically dependent.  (Section 3 gives no threshold.  Measuring
+     r_jj against the norm left after step 2 instead keeps a direction that coincides with
+     an earlier one to 1e-13 whenever step 2 already removed most of it: the triangular
+     factor becomes ill-conditioned and x = Z y loses digits.)
   4. The Hessenberg matrix stays scalar upper Hessenberg; the previous complex Givens
      rotations are applied to each new column and one new rotation zeroes its
      sub-diagonal entry.  The residual estimate is |g_last|.
@@ -91,6 +96,7 @@ def solve(A, precs, b: np.ndarray, tol: float = 1e-8, maxit: int = 200, scheme: 
         nip = 0
         Zk = [precs[i](src[i]) for i in range(t)]
         W = [A @ z for z in Zk]
+        az = [np.linalg.norm(w) for w in W]        # deflation reference: ||A z_j||
         nold = len(V)
         Vm = np.array(V).T                           # dofs x nold
         Hold = np.zeros((nold, t), dtype=np.complex128)
@@ -100,7 +106,6 @@ def solve(A, precs, b: np.ndarray, tol: float = 1e-8, maxit: int = 200, scheme: 
                 nip += nold
                 W[j] = W[j] - Vm @ c
                 Hold[:, j] += c
-        nu = [np.linalg.norm(w) for w in W]
         new_v, new_from = [], []
         Rnew = np.zeros((t, t), dtype=np.complex128)
         accepted = []
@@ -115,7 +120,7 @@ def solve(A, precs, b: np.ndarray, tol: float = 1e-8, maxit: int = 200, scheme: 
                     Rnew[:len(new_v), j] += c
             rjj = np.linalg.norm(w)
             nip += 1
-            if rjj <= eta * nu[j] or rjj == 0.0:
+            if rjj <= eta * az[j] or rjj == 0.0:
                 continue                             # deflated: Z_j dropped
             Rnew[len(new_v), j] = rjj
             new_v.append(w / rjj)

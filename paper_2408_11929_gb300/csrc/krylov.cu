@@ -4,7 +4,8 @@
 //   W   = A Z_k            (matrix-free P1 stencil)
 //   block CGS: H = V^H W, W -= V H, twice by default (opts.gs_passes), coefficients summed
 //   block QR of W in preconditioner order (the same number of passes against the new vectors),
-//     column j deflated when r_jj <= eta * ||w_j|| (norm after CGS2)
+//     column j deflated when r_jj <= eta * ||A z_j|| (the norm of the new column before any
+//     Gram-Schmidt)
 //   Givens update of the scalar upper Hessenberg matrix, rho = |g_last|, converged when
 //     rho / ||b|| <= tol (tested once per iteration)
 //   next sources: t = 1 the new vector, t = 2 the other preconditioner's new vector
@@ -38,6 +39,7 @@ struct KState {
   double* beta;
   int *done, *status, *nV, *nZ, *iters, *nacc, *amap;
   double *rho, *nu, *cs, *hist, *npart;
+  double* azpart;          // per slot, new column j, CTA c of gs_wprep_kernel: its part of ||A z_j||^2
   double2 **Vptr, **Zptr;
   double2 *Hacc, *Hthis, *Hpart, *Rnew, *sn, *g, *Rrot, *y, *qpart, *sbuf, *V0;
   const double2** srcptr;
@@ -296,6 +298,10 @@ __global__ void __launch_bounds__(256) gs_wprep_kernel(KState S, const double2* 
   const size_t D = S.D;
   const double2* Wr = W + (size_t)r * TT * D;
   double* P = S.Wp + (size_t)r * TT * 3 * D;
+  __shared__ double sh[32 * TT];
+  double n2[TT];
+#pragma unroll
+  for (int b = 0; b < TT; ++b) n2[b] = 0;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < D; g += (size_t)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int b = 0; b < TT; ++b) {
@@ -303,8 +309,14 @@ __global__ void __launch_bounds__(256) gs_wprep_kernel(KState S, const double2* 
       P[(b * 3 + 0) * D + g] = w.x;
       P[(b * 3 + 1) * D + g] = w.y - w.x;
       P[(b * 3 + 2) * D + g] = w.x + w.y;
+      n2[b] += cabs2(w);
     }
   }
+  // this CTA's part of ||A z_j||^2 (W = A Z before Gram-Schmidt): the deflation reference
+  block_sum<TT>(n2, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int b = 0; b < TT; ++b) S.azpart[((size_t)r * TT + b) * gridDim.x + blockIdx.x] = n2[b];
 }
 
 template <int TT, int AB>
@@ -540,6 +552,25 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
     return qr_reduce<TT>(v, S, r, parity, bar, target, err, budget, sh, red_out);
   };
 
+  // deflation reference ||A z_j||: the GX parts of gs_wprep_kernel, summed in the same order by
+  // every CTA (so that all of them take the same decisions)
+  double az[TT];
+  {
+#pragma unroll
+    for (int j = 0; j < TT; ++j) az[j] = 0;
+    if (active)
+      for (int c = threadIdx.x; c < S.GX; c += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < TT; ++j) az[j] += __ldcg(S.azpart + ((size_t)r * TT + j) * S.GX + c);
+    block_sum<TT>(az, sh);
+    __shared__ double az_s[TT];
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int j = 0; j < TT; ++j) az_s[j] = sqrt(az[j]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < TT; ++j) az[j] = az_s[j];
+  }
   // R1: norms in doubles 0..TT-1, <w_0, w_1> in slot NS
   constexpr int NS = (TT + 1) / 2;
   double nu[TT];
@@ -652,7 +683,7 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
           }
     }
     amap[j] = -1;
-    if (active && rj > S.eta * nu[j] && rj > 0 && isfinite(rj)) {
+    if (active && rj > S.eta * az[j] && rj > 0 && isfinite(rj)) {
       const double inv = 1.0 / rj;
       double2* vo = Vr + acc * D;
       for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) vo[g] = cscale(w[g], inv);
@@ -995,6 +1026,7 @@ struct SlotSolver::Impl {
     K.amap = dev<int>((size_t)S * t); K.rho = dev<double>(S); K.nu = dev<double>((size_t)S * t);
     K.cs = dev<double>((size_t)S * K.maxZ); K.sn = dev<double2>((size_t)S * K.maxZ);
     K.hist = dev<double>((size_t)S * maxit); K.npart = dev<double>((size_t)S * K.GX);
+    K.azpart = dev<double>((size_t)S * t * K.GX);
     K.Vptr = dev<double2*>((size_t)S * K.maxV); K.Zptr = dev<double2*>((size_t)S * K.maxZ);
     K.Hacc = dev<double2>((size_t)S * K.maxV * t); K.Hthis = dev<double2>((size_t)S * K.maxV * t);
     K.Hpart = dev<double2>((size_t)S * K.maxV * t * K.GX); K.Rnew = dev<double2>((size_t)S * t * t);

@@ -7,7 +7,9 @@
 * the inner-product count of a single Gram-Schmidt pass is (k - 1/2) t^2 + (3/2) t
   (Section 3);
 * Arnoldi relation A Z = V H, orthonormal V, monotone residuals;
-* duplicated preconditioners deflate and reproduce the t = 1 iterates;
+* duplicated preconditioners deflate and reproduce the t = 1 iterates; a direction that
+  agrees with another to 1e-11 of its size is deflated even when Gram-Schmidt against the
+  basis has already removed most of it, and the explicit residual follows the implicit one;
 * the converged solution agrees with the banded direct solve.
 """
 import numpy as np
@@ -101,6 +103,29 @@ def test_duplicate_preconditioners_deflate_to_t1():
     assert two.iterations == one.iterations
     np.testing.assert_allclose(two.history, one.history, rtol=1e-6)
     assert np.linalg.norm(two.x - one.x) / np.linalg.norm(one.x) < 1e-9
+
+
+def test_nearly_dependent_direction_is_deflated():
+    """Two preconditioners of the form A^{-1}(I + 1e-3 E1), the second perturbed by 1e-11: the
+    new columns A z_1, A z_2 agree to 1e-11 of their size, while projecting them on the
+    basis (b) leaves only 1e-3 of it.  Measured against ||A z_j|| (the deflation reading) the
+    second column is dependent and is dropped; kept (measured against the 1e-3 remainder it
+    would pass a 1e-10 test), it makes the rotated triangular factor ill-conditioned and the
+    explicit residual of x = Z y stalls near 1e-9 while the implicit one reaches 1e-14."""
+    A, *_ = fem.global_system(10.0, 16)
+    Ad = A.toarray()
+    Ai = np.linalg.inv(Ad)
+    rng = np.random.default_rng(3)
+    n = Ad.shape[0]
+    E1 = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    E2 = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    p1 = lambda r: Ai @ (r + 1e-3 * (E1 @ r))
+    p2 = lambda r: p1(r) + 1e-11 * (Ai @ (E2 @ r))
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    res = mpgmres.solve(A, [p1, p2], b, tol=1e-12, maxit=30, keep_basis=True)
+    assert res.status == "ok"
+    assert res.Z.shape[1] == res.iterations  # one accepted direction per iteration
+    assert res.rel_res_explicit < 10 * max(res.rel_res_implicit, 1e-14)
 
 
 def test_zero_rhs():
