@@ -12,12 +12,16 @@ One iteration:
   3. The t columns of W are then orthonormalised one after the other, in preconditioner
      order, each by classical Gram-Schmidt against the new vectors already accepted in this
      iteration (again twice), giving a real positive diagonal r_jj.  Column j is DEFLATED (its Z column dropped)
-     when r_jj <= eta * ||A z_j||, the norm of the new column before any Gram-Schmidt: the
-     part of A z_j outside the span of everything before it is then below eta of its size,
-     so the direction is numerically dependent.  (Section 3 gives no threshold.  Measuring
-     r_jj against the norm left after step 2 instead keeps a direction that coincides with
-     an earlier one to 1e-13 whenever step 2 already removed most of it: the triangular
-     factor becomes ill-conditioned and x = Z y loses digits.)
+     when r_jj == 0, or when another column of this block has been accepted already and
+     r_jj <= eta * ||A z_j||, the norm of the new column before any Gram-Schmidt: the part of
+     A z_j outside the span of the basis and of the block's accepted vectors is then below
+     eta of its size, so the direction duplicates one already taken.  The first accepted
+     column of a block is kept whenever r_jj > 0: when A z lies in the span of the basis
+     (one strip, where the sweep is A^{-1}) it completes the least-squares problem (a lucky
+     breakdown) even though its new basis vector is rounding noise.  (Section 3 gives no
+     threshold.  Measuring r_jj against the norm left after step 2 instead keeps a direction
+     that coincides with another new one to 1e-13 whenever step 2 already removed most of
+     both: the triangular factor becomes ill-conditioned and x = Z y loses digits.)
   4. The Hessenberg matrix stays scalar upper Hessenberg; the previous complex Givens
      rotations are applied to each new column and one new rotation zeroes its
      sub-diagonal entry.  The residual estimate is |g_last|.
@@ -120,7 +124,7 @@ def solve(A, precs, b: np.ndarray, tol: float = 1e-8, maxit: int = 200, scheme: 
                     Rnew[:len(new_v), j] += c
             rjj = np.linalg.norm(w)
             nip += 1
-            if rjj <= eta * az[j] or rjj == 0.0:
+            if rjj == 0.0 or (new_v and rjj <= eta * az[j]):
                 continue                             # deflated: Z_j dropped
             Rnew[len(new_v), j] = rjj
             new_v.append(w / rjj)

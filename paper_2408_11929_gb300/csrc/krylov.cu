@@ -4,8 +4,8 @@
 //   W   = A Z_k            (matrix-free P1 stencil)
 //   block CGS: H = V^H W, W -= V H, twice by default (opts.gs_passes), coefficients summed
 //   block QR of W in preconditioner order (the same number of passes against the new vectors),
-//     column j deflated when r_jj <= eta * ||A z_j|| (the norm of the new column before any
-//     Gram-Schmidt)
+//     column j deflated when r_jj = 0, or when an earlier column of the block was accepted and
+//     r_jj <= eta * ||A z_j|| (the norm of the new column before any Gram-Schmidt)
 //   Givens update of the scalar upper Hessenberg matrix, rho = |g_last|, converged when
 //     rho / ||b|| <= tol (tested once per iteration)
 //   next sources: t = 1 the new vector, t = 2 the other preconditioner's new vector
@@ -683,7 +683,9 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
           }
     }
     amap[j] = -1;
-    if (active && rj > S.eta * az[j] && rj > 0 && isfinite(rj)) {
+    // the first accepted column of the block is kept whenever r_jj > 0 (a lucky breakdown when
+    // A z lies in the basis' span); later ones must exceed eta ||A z_j||
+    if (active && rj > (acc > 0 ? S.eta * az[j] : 0.0) && isfinite(rj)) {
       const double inv = 1.0 / rj;
       double2* vo = Vr + acc * D;
       for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) vo[g] = cscale(w[g], inv);
