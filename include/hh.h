@@ -99,6 +99,15 @@ typedef struct {
                              dependent launch, so that its prologue and first factor tiles overlap
                              the end of the preceding kernel (it waits for that kernel before it
                              reads the line data); 0: plain stream order */
+  int interface_form;     /* how a sweep passes interface data from strip to strip (Section 2's
+                             block forward / backward substitution, reorganised exactly):
+                             1 (default): the interface recurrences of the forward and backward
+                             passes as prefix-doubling scans (log2 N grouped steps over all
+                             strips, with the powers G^(2^l), K^(2^l) of the strip transfer
+                             blocks) and each pass's correction of the strips' interior lines as
+                             ONE grouped step with stored block columns of the strip inverse;
+                             0: chains of N-2 and N-1 dependent steps and block-Thomas corrections
+                             (2R+1 and R-1 dependent steps) */
 } hh_opts;
 
 typedef struct {

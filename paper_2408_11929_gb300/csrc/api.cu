@@ -133,11 +133,13 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   if (opts.bcr_depth != 0) return (set_error("only bcr_depth = 0 (block Thomas strip solves) is implemented"), HH_EINVAL);
   if (opts.gs_passes != 1 && opts.gs_passes != 2) return (set_error("gs_passes must be 1 or 2"), HH_EINVAL);
   if (opts.serve_slots < 1 || opts.serve_slots > 256) return (set_error("serve_slots must be in 1..256"), HH_EINVAL);
+  if (opts.interface_form != 0 && opts.interface_form != 1) return (set_error("interface_form must be 0 or 1"), HH_EINVAL);
   if (opts.timeout_cycles <= 0) opts.timeout_cycles = 4000000000LL;
   k = k_; n = n_; N = strips; m = n + 1; R = n / N;
   precision = opts.precision;
   ldf = (m + 3) & ~3;
   coef.init(k, n);
+  bdir = block_directory(R, N, opts.interface_form);
   static const int bitcode[4] = {DC_LR, DC_RL, DC_BT, DC_TB};
   dir_codes.clear();
   for (int b = 0; b < 4; ++b)
@@ -179,6 +181,9 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   cudaMemsetAsync(err, 0, 64, stream);
   steps_double = build_steps(n, N, true);
   steps_single = build_steps(n, N, false);
+  prog_double = build_program(n, N, true, opts.interface_form, bdir);
+  prog_single = build_program(n, N, false, opts.interface_form, bdir);
+  if (upload_programs()) return HH_ENOMEM;
   cudaStreamSynchronize(stream);
 
   cudaEvent_t a, b;
@@ -215,7 +220,8 @@ Engine::~Engine() {
   collect_ticks();
   for (auto ev : event_pool) cudaEventDestroy(ev);
   dfree(factors); dfree(bar); dfree(err);
-  dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial);
+  dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial); dfree(w_t0); dfree(w_t1);
+  dfree(prog_tasks);
   dfree(factors_hi); dfree(factors_lo);
   free_dense_scratch();
   if (own_stream && stream) cudaStreamDestroy(stream);
@@ -410,6 +416,7 @@ void hh_default_opts(hh_opts* o) {
   o->autotune = 1;
   o->fuse_chains = 1;
   o->overlap_steps = 1;
+  o->interface_form = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {
@@ -541,7 +548,7 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->m = E.m;
   st->ldf = E.ldf;
   st->columns = E.last_columns;
-  st->sweep_steps = (int64_t)(E.opts.single_sweep ? E.steps_single.size() : E.steps_double.size());
+  st->sweep_steps = (int64_t)(E.opts.single_sweep ? E.prog_single.size() : E.prog_double.size());
   st->gemm_launches = E.launches[Engine::K_GEMM];
   st->gemm_ms = E.ms[Engine::K_GEMM];
   st->gemm_flops = E.flops[Engine::K_GEMM];
@@ -564,8 +571,8 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
       st->tc_us = it->second.us;
     }
   }
-  for (const SweepStep& sp : E.opts.single_sweep ? E.steps_single : E.steps_double)
-    st->wide_steps += (int64_t)(sp.ns * E.last_columns > 8);
+  for (const SweepPhase& ph : E.opts.single_sweep ? E.prog_single : E.prog_double)
+    st->wide_steps += (int64_t)(ph.kind == PH_GROUP || (ph.kind == PH_STEP && ph.step.ns * E.last_columns > 8));
   return HH_OK;
 }
 

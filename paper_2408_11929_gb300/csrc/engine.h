@@ -25,7 +25,7 @@ void set_error(const std::string& msg);
 // with C the identity or the coupling to the line below (L) / above (U), and optionally the
 // result also accumulated into acc[acc_j].  Buffers: SB_RIN (packed right-hand sides), SB_V
 // (sweep result), SB_W (corrections).
-enum SweepBuf { SB_NONE = 0, SB_RIN = 1, SB_V = 2, SB_W = 3 };
+enum SweepBuf { SB_NONE = 0, SB_RIN = 1, SB_V = 2, SB_W = 3, SB_T0 = 4, SB_T1 = 5, SB_COUNT = 6 };
 struct SweepStep {
   int f, s0, ns;
   int base, base_j;
@@ -35,6 +35,45 @@ struct SweepStep {
 };
 
 std::vector<SweepStep> build_steps(int n, int N, bool double_sweep);
+
+// A grouped step (sweep.cu, group.cu): independent output lines ("tasks"), each
+//   out[out_line] = (base[base_line] or, with OUT_ADD, out itself, else 0) + sum_q (-1)^neg_q F_{f_q} x_q
+// over strips s0 .. s0+ns-1, x_q = line `line` of array `arr` (a SweepBuf) at strip s + ds
+// (zero outside 0..N-1).  The terms' K ranges are concatenated.  T0 and T1 hold one line.
+struct GTerm {
+  int f, arr, line, ds, neg;
+};
+constexpr int GMAX_TERMS = 3;
+struct GTask {
+  int nterm;
+  GTerm term[GMAX_TERMS];
+  int out_arr, out_line, base_arr, base_line, mode, s0, ns;
+};
+// One phase of a sweep program: a step of the line-coupled block-Thomas form, a grouped step,
+// or a copy of one line (strips s0 .. s0+ns-1) from task 0's term 0 line to its output line.
+enum PhaseKind { PH_STEP = 0, PH_GROUP = 1, PH_COPY = 2 };
+struct SweepPhase {
+  int kind;
+  SweepStep step;
+  std::vector<GTask> tasks;
+  size_t dev_off = 0;  // first task in the engine's device task table
+};
+// Device addresses of the sweep arrays, by SweepBuf.  Rin, V, W hold R+1 lines, T0 and T1 one.
+struct GArrays {
+  void* p[SB_COUNT];
+};
+// Block directory of the factor store beyond F_0..F_R, G, K (see setup.cu).
+struct BlockDir {
+  int iY = -1;   // D_int^{-1}[j, 0] L, j = 0..R-1 (strips visited before the last)
+  int iYL = -1;  // D_last^{-1}[j, 0] L, j = 0..R (the last strip)
+  int iZ = -1;   // D_int^{-1}[j, R-1] U, j = 1..R-1 at iZ + j - 1
+  int iGp = -1;  // G^(2^l), l = 1..LF-1 at iGp + l - 1
+  int iKp = -1;  // K^(2^l), l = 1..LB-1 at iKp + l - 1
+  int LF = 0, LB = 0;  // levels of the forward / backward interface scans
+  int total = 0;       // blocks in the store
+};
+BlockDir block_directory(int R, int N, int form);
+std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form, const BlockDir& bd);
 
 // Direction codes of the BT frame mapping (node of the BT frame -> node of the grid).
 enum DirCode { DC_BT = 0, DC_TB = 1, DC_LR = 2, DC_RL = 3 };
@@ -84,13 +123,14 @@ class Engine {
   // boxes of the tensor-core step (16 and 18 rows), cached per (array, columns per strip)
   struct LineMaps {
     const void* ptr = nullptr;
-    int C = -1, bnc = 0;
+    int C = -1, bnc = 0, lines = 0;
     CUtensorMap base{}, src{};
   };
-  LineMaps line_maps[16];
+  LineMaps line_maps[24];
   int line_maps_next = 0;
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
-  const LineMaps* line_maps_for(const void* buf, int C, int bnc);
+  // lines: lines held by the array (0: R + 1, the sweep arrays; 1: the interface arrays)
+  const LineMaps* line_maps_for(const void* buf, int C, int bnc, int lines = 0);
   // autotuned tensor-core step per column count: tile shape (0: 64 columns x 3 stages,
   // 1: 32 columns x 4 stages) and K split (0 = fill the SMs)
   struct TcChoice {
@@ -115,7 +155,13 @@ class Engine {
   static constexpr size_t BAR_BYTES = (size_t)BAR_COUNT * 64 * sizeof(unsigned);
   unsigned* bar = nullptr;
   int* err = nullptr;       // device error word
-  std::vector<SweepStep> steps_double, steps_single;  // sweep schedules
+  std::vector<SweepStep> steps_double, steps_single;  // sweep schedules (block-Thomas form)
+  // sweep programs (opts.interface_form): phases of a double and of a single sweep, their
+  // grouped tasks in one device table
+  BlockDir bdir;
+  std::vector<SweepPhase> prog_double, prog_single;
+  GTask* prog_tasks = nullptr;
+  int upload_programs();
   size_t bytes_allocated = 0;
 
   // statistics
@@ -181,8 +227,9 @@ class Engine {
   int run_sweep(const void* Rin, void* V, void* W, int C, bool single);
   // partial: split-K slices (or nullptr); allow_graph = false keeps the sweep eager (graph
   // instantiation may allocate, which the no-allocation entry point must not)
+  // T0, T1: one-line interface arrays (nullptr: the handle's own)
   int run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool single, void* partial,
-                        size_t partial_bytes, bool allow_graph = true);
+                        size_t partial_bytes, bool allow_graph = true, void* T0 = nullptr, void* T1 = nullptr);
   int apply_preconditioner_noalloc(int dcode, int ncols, const double2* r, double2* z, bool single);
   // the launches of one sweep, untimed and without a graph of their own (for captures)
   int sweep_inline(const void* Rin, void* V, void* W, int C, bool single);
@@ -192,13 +239,16 @@ class Engine {
   size_t sweep_ws_bytes(int C) const;          // bytes of one packed sweep array
   double sweep_flops(int C, bool single) const;
   double sweep_bytes(int C, bool single) const;
-  int factor_blocks() const { return R + 3; }
+  int factor_blocks() const { return bdir.total > 0 ? bdir.total : R + 3; }
+  int inverse_columns();  // setup.cu: the blocks of bdir beyond G and K
 
   // sweep workspaces (grown on demand)
   void* w_rin = nullptr;
   void* w_v = nullptr;
   void* w_w = nullptr;
   void* w_partial = nullptr;   // split-K slices of the sweep GEMM steps
+  void* w_t0 = nullptr;        // one-line arrays of the interface scans
+  void* w_t1 = nullptr;
   size_t w_partial_bytes = 0;
   size_t sweep_partial_bytes(int C) const;
   size_t w_cap_cols = 0;

@@ -244,14 +244,15 @@ constexpr size_t line_gemm_smem() {
   return ((size_t)STAGES * (BM * BK + BK * BN + (BK + 2) * BN) + BK * BN) * sizeof(typename Cx<R>::T);
 }
 
-// Setup GEMM: C = alpha * A * B (all m x m, row-major, leading dimensions lda / ldb / ldc).
+// Setup GEMM: C = E + alpha * A * B (all m x m, row-major, leading dimensions lda / ldb / ldc;
+// E optional, with leading dimension ldc, and it may be C itself).
 // The next K tile is copied into the other shared-memory buffer by cp.async while the current
 // one is multiplied (two buffers, one copy group in flight).
 template <typename R, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256) dense_gemm_kernel(const typename Cx<R>::T* __restrict__ A, int lda,
                                                          const typename Cx<R>::T* __restrict__ B, int ldb,
-                                                         typename Cx<R>::T* __restrict__ Cm, int ldc, int m,
-                                                         double alpha) {
+                                                         typename Cx<R>::T* Cm, int ldc, int m,
+                                                         double alpha, const typename Cx<R>::T* E = nullptr) {
   using T = typename Cx<R>::T;
   constexpr int BK = 16;
   constexpr int NTX = BN / TN;
@@ -315,7 +316,9 @@ __global__ void __launch_bounds__(256) dense_gemm_kernel(const typename Cx<R>::T
     for (int q = 0; q < TN; ++q) {
       const int gc = col0 + tx * TN + q;
       if (gc >= m) continue;
-      Cm[(size_t)gr * ldc + gc] = mk<T>(alpha * acc[p][q][0], alpha * acc[p][q][1]);
+      T z = mk<T>(alpha * acc[p][q][0], alpha * acc[p][q][1]);
+      if (E) z = cadd(E[(size_t)gr * ldc + gc], z);
+      Cm[(size_t)gr * ldc + gc] = z;
     }
   }
 }

@@ -4,7 +4,8 @@
 // allocator owns every byte of the device, or real-time paths that must not pay for
 // cudaMalloc / cudaFree (which can synchronise the whole device).  The kernels are the
 // same as hh_apply_preconditioner's; only their scratch moves: the packed input, the
-// sweep output, the correction array, the column tables and the split-K slices live in one
+// sweep output, the correction array, the interface arrays, the column tables and the split-K
+// slices live in one
 // file-scope device array of fixed size.  The array is reserved on a device when this file's
 // module is loaded there, which CUDA's lazy module loading does at the first use of one of its
 // symbols; hh_setup makes that use (it resolves the array's device address), so the array is
@@ -87,7 +88,10 @@ int Engine::apply_preconditioner_noalloc(int dcode, int ncols, const double2* r,
   const size_t off_w = off_v + align256(arr);
   const size_t off_ptr = off_w + align256(arr);
   const size_t off_scale = off_ptr + align256(sizeof(void*) * ncols);
-  const size_t need = off_scale + align256(sizeof(double) * ncols);
+  const size_t tline = (size_t)m * N * ncols * sweep_elem();  // one-line interface arrays
+  const size_t off_t0 = off_scale + align256(sizeof(double) * ncols);
+  const size_t off_t1 = off_t0 + align256(tline);
+  const size_t need = off_t1 + align256(tline);
   // whatever is left of the array holds split-K slices of the GEMM steps (fewer slices, or
   // none, when it is small)
   const size_t off_part = need;
@@ -110,7 +114,8 @@ int Engine::apply_preconditioner_noalloc(int dcode, int ncols, const double2* r,
   int4 codes = make_int4(dcode, dcode, dcode, dcode);
   launch_pack(*this, tab, scale, ncols, 1, codes, rin);
   const size_t part_bytes = kNoAllocScratchBytes > off_part ? kNoAllocScratchBytes - off_part : 0;
-  rc = run_sweep_untimed(rin, v, w, ncols, single, part_bytes ? s + off_part : nullptr, part_bytes, false);
+  rc = run_sweep_untimed(rin, v, w, ncols, single, part_bytes ? s + off_part : nullptr, part_bytes, false, s + off_t0,
+                         s + off_t1);
   if (rc == HH_OK) launch_unpack(*this, v, ncols, 1, codes, z, D);
   cudaError_t e = cudaStreamSynchronize(stream);
   if (rc) return rc;

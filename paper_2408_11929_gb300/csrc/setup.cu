@@ -257,6 +257,142 @@ int interface_blocks(Engine& E, typename Cx<R>::T* bufA, typename Cx<R>::T* bufB
   return HH_OK;
 }
 
+// Z = alpha X L (upper = 0) or alpha X U (upper = 1), with L[p][p] = vert(p), L[p][p-1] = diag,
+// U[p][p] = vert(p), U[p][p+1] = diag (the couplings of a line to the line below / above);
+// the padding columns of Z are zeroed.
+template <typename R>
+__global__ void rmul_kernel(const typename Cx<R>::T* __restrict__ X, typename Cx<R>::T* __restrict__ Z, int m, int ld,
+                            Coef cf, int upper, double alpha) {
+  using T = typename Cx<R>::T;
+  const R dg = (R)cf.diag();
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)m * ld; idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / ld), b = (int)(idx % ld);
+    if (b >= m) { Z[idx] = mk<T>(0, 0); continue; }
+    const double2 vb = cf.vert(b);
+    T v = cmul(X[(size_t)a * ld + b], mk<T>(vb.x, vb.y));
+    const int nb = upper ? b - 1 : b + 1;
+    if (nb >= 0 && nb < m) { const T y = X[(size_t)a * ld + nb]; v.x += dg * y.x; v.y += dg * y.y; }
+    Z[idx] = mk<T>(alpha * v.x, alpha * v.y);
+  }
+}
+
+// C = Eadd + alpha A B on the exact GEMM of the setup (complex64 FMA or complex128)
+template <typename R>
+static void exact_gemm(Engine& E, const typename Cx<R>::T* A, const typename Cx<R>::T* B, typename Cx<R>::T* C,
+                       double alpha, const typename Cx<R>::T* Eadd = nullptr) {
+  const int m = E.m, ld = E.ldf;
+  if constexpr (sizeof(R) == 4) {
+    dim3 grid((m + 63) / 64, (m + 63) / 64);
+    dense_gemm_kernel<R, 64, 64, 4, 4><<<grid, 256, 0, E.stream>>>(A, ld, B, ld, C, ld, m, alpha, Eadd);
+  } else {
+    dim3 grid((m + 31) / 32, (m + 31) / 32);
+    dense_gemm_kernel<R, 32, 32, 2, 2><<<grid, 256, 0, E.stream>>>(A, ld, B, ld, C, ld, m, alpha, Eadd);
+  }
+  E.count_launch();
+}
+
+// Block columns of the strip inverses and powers of the transfer blocks (the blocks of the
+// sweep's interface form 1, see build_program in sweep.cu), from the stored F_j = S_j^{-1}:
+//   first block column X = D^{-1} E_0 by block Thomas on the identity of line 0:
+//     forward   y_0 = F_0,  y_j = -F_j L y_{j-1};
+//     backward  X_top = y_top,  X_j = y_j - (F_j U) X_{j+1};
+//   Y_j = X_j L for the strips visited before the last (top = R-1) and for the last (top = R);
+//   last block column of the strips before the last, X = D^{-1} E_{R-1}:
+//     X_{R-1} = F_{R-1},  X_j = -(F_j U) X_{j+1},  Z_j = X_j U  (j = 1..R-1);
+//   G^(2^l) and K^(2^l) by repeated squaring.
+// The products chain up to R factors, so they run on the exact GEMM (as the interface blocks).
+template <typename R>
+int inverse_columns_impl(Engine& E) {
+  using T = typename Cx<R>::T;
+  const BlockDir& bd = E.bdir;
+  if (bd.iY < 0) return HH_OK;
+  const int m = E.m, ld = E.ldf, Rr = E.R;
+  const size_t blk = (size_t)m * ld;
+  T* F = reinterpret_cast<T*>(E.factors);
+  auto B = [&](int i) { return F + (size_t)i * blk; };
+  T *FU = nullptr, *P[2] = {nullptr, nullptr}, *Zs = nullptr;
+  if (E.dmalloc((void**)&FU, blk * sizeof(T)) || E.dmalloc((void**)&P[0], blk * sizeof(T)) ||
+      E.dmalloc((void**)&P[1], blk * sizeof(T)) || E.dmalloc((void**)&Zs, blk * sizeof(T))) {
+    E.dfree(FU); E.dfree(P[0]); E.dfree(P[1]); E.dfree(Zs);
+    return HH_ENOMEM;
+  }
+  const unsigned g = E.grid_for(blk);
+  auto rmul = [&](const T* X, T* Z, int upper, double alpha = 1.0) {
+    rmul_kernel<R><<<g, 256, 0, E.stream>>>(X, Z, m, ld, E.coef, upper, alpha);
+    E.count_launch();
+  };
+  int products = 0;
+  E.tick_begin(Engine::K_SETUP);
+  // forward: y_j in the slots of the last strip's columns
+  cudaMemcpyAsync(B(bd.iYL), B(0), blk * sizeof(T), cudaMemcpyDeviceToDevice, E.stream);
+  for (int j = 1; j <= Rr; ++j) {
+    lmul_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(B(bd.iYL + j - 1), Zs, m, ld, E.coef);
+    E.count_launch();
+    exact_gemm<R>(E, B(j), Zs, B(bd.iYL + j), -1.0);
+    ++products;
+  }
+  // strips before the last: X_{R-1} = y_{R-1}
+  const T* X = B(bd.iYL + Rr - 1);
+  rmul(X, B(bd.iY + Rr - 1), 0);
+  int pp = 0;
+  for (int j = Rr - 2; j >= 0; --j) {
+    rmul(B(j), FU, 1);
+    T* Xn = P[pp];
+    pp ^= 1;
+    exact_gemm<R>(E, FU, X, Xn, -1.0, B(bd.iYL + j));
+    rmul(Xn, B(bd.iY + j), 0);
+    X = Xn;
+    ++products;
+  }
+  // the last strip: X_R = y_R
+  cudaMemcpyAsync(P[0], B(bd.iYL + Rr), blk * sizeof(T), cudaMemcpyDeviceToDevice, E.stream);
+  X = P[0];
+  pp = 1;
+  rmul(X, B(bd.iYL + Rr), 0);
+  for (int j = Rr - 1; j >= 0; --j) {
+    rmul(B(j), FU, 1);
+    T* Xn = P[pp];
+    pp ^= 1;
+    exact_gemm<R>(E, FU, X, Xn, -1.0, B(bd.iYL + j));
+    rmul(Xn, B(bd.iYL + j), 0);
+    X = Xn;
+    ++products;
+  }
+  // last block column of the strips before the last
+  X = B(Rr - 1);
+  rmul(X, B(bd.iZ + Rr - 2), 1);
+  pp = 0;
+  for (int j = Rr - 2; j >= 1; --j) {
+    rmul(B(j), FU, 1);
+    T* Xn = P[pp];
+    pp ^= 1;
+    exact_gemm<R>(E, FU, X, Xn, -1.0);
+    rmul(Xn, B(bd.iZ + j - 1), 1);
+    X = Xn;
+    ++products;
+  }
+  // powers of the transfer blocks
+  for (int l = 1; l < bd.LF; ++l) {
+    const T* prev = l == 1 ? B(Rr + 1) : B(bd.iGp + l - 2);
+    exact_gemm<R>(E, prev, prev, B(bd.iGp + l - 1), 1.0);
+    ++products;
+  }
+  for (int l = 1; l < bd.LB; ++l) {
+    const T* prev = l == 1 ? B(Rr + 2) : B(bd.iKp + l - 2);
+    exact_gemm<R>(E, prev, prev, B(bd.iKp + l - 1), 1.0);
+    ++products;
+  }
+  E.tick_end(Engine::K_SETUP, 0.0, products * 8.0 * m * (double)m * m);
+  const cudaError_t ce = cudaStreamSynchronize(E.stream);
+  E.dfree(FU); E.dfree(P[0]); E.dfree(P[1]); E.dfree(Zs);
+  if (ce != cudaSuccess) { E.set_cuda_error(ce, "strip inverse columns"); return HH_ECUDA; }
+  return E.check_device_error("strip inverse columns");
+}
+
+int Engine::inverse_columns() {
+  return precision == HH_PREC_FP32 ? inverse_columns_impl<float>(*this) : inverse_columns_impl<double>(*this);
+}
+
 // Newton-Schulz step of an approximate inverse X of S (X <- X (2I - S X), quadratically
 // convergent while ||I - S X||_2 < 1): with T = S X given, T is replaced by 2I - T and every
 // block writes its part of ||I - T||_F^2 to part[blockIdx.x] (summed on the host in a fixed
@@ -532,6 +668,7 @@ int factor_impl(Engine& E) {
   cudaStreamSynchronize(E.stream);
   if (status == HH_OK) status = E.check_device_error("strip setup");
   if (status == HH_OK) status = interface_blocks<R>(E, bufA, bufB);
+  if (status == HH_OK) status = inverse_columns_impl<R>(E);
   E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
   E.dfree(bufC); E.dfree(bufD); E.dfree(part_dev); E.dfree(sums_dev);
   if (part_host) cudaFreeHost(part_host);

@@ -117,6 +117,119 @@ std::vector<SweepStep> build_steps(int n, int N, bool double_sweep) {
   return st;
 }
 
+static int ceil_log2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+BlockDir block_directory(int R, int N, int form) {
+  BlockDir bd;
+  bd.total = R + 3;
+  if (form == 0 || N < 2) return bd;
+  bd.LF = N >= 3 ? ceil_log2(N - 1) : 0;
+  bd.LB = ceil_log2(N);
+  bd.iY = R + 3;
+  bd.iYL = bd.iY + R;
+  bd.iZ = bd.iYL + R + 1;
+  bd.iGp = bd.iZ + (R - 1);
+  bd.iKp = bd.iGp + std::max(0, bd.LF - 1);
+  bd.total = bd.iKp + std::max(0, bd.LB - 1);
+  return bd;
+}
+
+// The double sweep with the interface data passed by scans and the interior corrections as
+// single grouped steps (form 1):
+//   F1  w_s = D^{-1} r_s, every strip at once (block Thomas steps, as in build_steps);
+//   F2  t_s = w_s[R-1] - G t_{s-1} (s = 0..N-2, t_{-1} = 0) as a prefix-doubling scan:
+//       a^0_s = w_s[R-1], a^{l+1}_s = a^l_s + (-G)^(2^l) a^l_{s-2^l} (ceil(log2(N-1)) steps,
+//       every strip in each step, ping-pong between T0 and T1);
+//   F3  v_s[j] = w_s[j] - Y_j t_{s-1}, every line j of strips 1..N-1 in one step, with the block
+//       columns Y_j = D^{-1}[j, 0] L of the strip inverse (D of the strips before the last,
+//       or of the last one); v_s[R-1] = t_s follows for the strips before the last;
+//   B1  u_s[0] = v_s[0] - K u_{s+1}[0] (s = N-2..0, u_{N-1}[0] = v_{N-1}[0]) as a scan with
+//       (-K)^(2^l) and strip offsets +2^l (ceil(log2 N) steps), then copied into V's line 0;
+//   B2  u_s[j] = v_s[j] - Z_j u_{s+1}[0], lines j = 1..R-1 of strips 0..N-2 in one step,
+//       Z_j = D^{-1}[j, R-1] U.
+// Every step is exact algebra on the block-Thomas form; only the order of the sums differs.
+std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form, const BlockDir& bd) {
+  std::vector<SweepPhase> prog;
+  const int R = n / N;
+  auto as_step = [](const SweepStep& x) {
+    SweepPhase p;
+    p.kind = PH_STEP;
+    p.step = x;
+    return p;
+  };
+  if (form == 0 || N < 2) {
+    for (const SweepStep& x : build_steps(n, N, double_sweep)) prog.push_back(as_step(x));
+    return prog;
+  }
+  const std::vector<SweepStep> legacy = build_steps(n, N, false);
+  for (int q = 0; q < 2 * R + 1; ++q) prog.push_back(as_step(legacy[q]));  // F1
+  auto task1 = [](int f, int arr, int line, int ds, int neg, int out_arr, int out_line, int base_arr, int base_line,
+                  int mode, int s0, int ns) {
+    GTask t{};
+    t.nterm = 1;
+    t.term[0] = GTerm{f, arr, line, ds, neg};
+    t.out_arr = out_arr; t.out_line = out_line;
+    t.base_arr = base_arr; t.base_line = base_line;
+    t.mode = mode; t.s0 = s0; t.ns = ns;
+    return t;
+  };
+  const int FG = R + 1, FK = R + 2;
+  // F2
+  int src_arr = SB_V, src_line = R - 1;
+  for (int l = 0; l < bd.LF; ++l) {
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    const int dst = (l & 1) ? SB_T1 : SB_T0;
+    p.tasks.push_back(task1(l == 0 ? FG : bd.iGp + l - 1, src_arr, src_line, -(1 << l), l == 0 ? 1 : 0, dst, 0,
+                            src_arr, src_line, OUT_SET, 0, N - 1));
+    prog.push_back(p);
+    src_arr = dst;
+    src_line = 0;
+  }
+  // F3
+  {
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    if (N >= 3)
+      for (int j = 0; j < R; ++j)
+        p.tasks.push_back(task1(bd.iY + j, src_arr, src_line, -1, 1, SB_V, j, SB_NONE, 0, OUT_ADD, 1, N - 2));
+    for (int j = 0; j <= R; ++j)
+      p.tasks.push_back(task1(bd.iYL + j, src_arr, src_line, -1, 1, SB_V, j, SB_NONE, 0, OUT_ADD, N - 1, 1));
+    prog.push_back(p);
+  }
+  if (!double_sweep) return prog;
+  // B1
+  src_arr = SB_V;
+  src_line = 0;
+  for (int l = 0; l < bd.LB; ++l) {
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    const int dst = (l & 1) ? SB_T1 : SB_T0;
+    p.tasks.push_back(task1(l == 0 ? FK : bd.iKp + l - 1, src_arr, src_line, 1 << l, l == 0 ? 1 : 0, dst, 0, src_arr,
+                            src_line, OUT_SET, 0, N));
+    prog.push_back(p);
+    src_arr = dst;
+    src_line = 0;
+  }
+  // B2, then u_s[0] into V's line 0
+  {
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    for (int j = 1; j < R; ++j)
+      p.tasks.push_back(task1(bd.iZ + j - 1, src_arr, 0, 1, 1, SB_V, j, SB_NONE, 0, OUT_ADD, 0, N - 1));
+    if (!p.tasks.empty()) prog.push_back(p);
+    SweepPhase c;
+    c.kind = PH_COPY;
+    c.tasks.push_back(task1(0, src_arr, 0, 0, 0, SB_V, 0, SB_NONE, 0, OUT_SET, 0, N - 1));
+    prog.push_back(c);
+  }
+  return prog;
+}
+
 // BT-frame node (i, l) of a column with direction code c -> grid node (io, jo)
 __device__ __forceinline__ void frame_map(int code, int i, int l, int n, int& io, int& jo) {
   switch (code) {
@@ -483,18 +596,34 @@ __global__ void __launch_bounds__(1024) chain_kernel(const typename Cx<R>::T* __
   }
 }
 
+int Engine::upload_programs() {
+  std::vector<GTask> all;
+  for (std::vector<SweepPhase>* prog : {&prog_double, &prog_single})
+    for (SweepPhase& ph : *prog) {
+      ph.dev_off = all.size();
+      for (const GTask& t : ph.tasks) all.push_back(t);
+    }
+  dfree(prog_tasks);
+  prog_tasks = nullptr;
+  if (all.empty()) return HH_OK;
+  if (dmalloc((void**)&prog_tasks, all.size() * sizeof(GTask))) return HH_ENOMEM;
+  cudaMemcpy(prog_tasks, all.data(), all.size() * sizeof(GTask), cudaMemcpyHostToDevice);
+  return HH_OK;
+}
+
 size_t Engine::sweep_ws_bytes(int C) const { return (size_t)(R + 1) * m * N * C * sweep_elem(); }
 
 size_t Engine::sweep_partial_bytes(int C) const { return (size_t)8 * m * N * C * sweep_elem(); }
 
 int Engine::ensure_sweep_ws(int C) {
   if ((size_t)C <= w_cap_cols) return HH_OK;
-  dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial);
-  w_rin = w_v = w_w = w_partial = nullptr;
+  dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial); dfree(w_t0); dfree(w_t1);
+  w_rin = w_v = w_w = w_partial = w_t0 = w_t1 = nullptr;
   w_cap_cols = 0;
   w_partial_bytes = 0;
-  const size_t b = sweep_ws_bytes(C);
-  if (dmalloc(&w_rin, b) || dmalloc(&w_v, b) || dmalloc(&w_w, b) || dmalloc(&w_partial, sweep_partial_bytes(C)))
+  const size_t b = sweep_ws_bytes(C), bt = (size_t)m * N * C * sweep_elem();
+  if (dmalloc(&w_rin, b) || dmalloc(&w_v, b) || dmalloc(&w_w, b) || dmalloc(&w_partial, sweep_partial_bytes(C)) ||
+      dmalloc(&w_t0, bt) || dmalloc(&w_t1, bt))
     return HH_ENOMEM;
   w_partial_bytes = sweep_partial_bytes(C);
   w_cap_cols = C;
@@ -603,15 +732,13 @@ static cudaError_t launch_tc_shape(Engine& E, int shape, const LineOperand<float
 }
 
 template <typename R>
-static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, int C, bool single, void* partial_buf,
-                                  size_t partial_bytes, bool allow_tick) {
+static cudaError_t run_steps_t(Engine& E, const std::vector<SweepStep>& steps, const GArrays& arrs, int C,
+                               void* partial_buf, size_t partial_bytes, bool allow_tick) {
   using T = typename Cx<R>::T;
-  const std::vector<SweepStep>& steps = single ? E.steps_single : E.steps_double;
+  const void* Rin = arrs.p[SB_RIN];
   const T* Fb = reinterpret_cast<const T*>(E.factors);
   const size_t blk = (size_t)E.m * E.ldf;
-  auto buf = [&](int b) -> T* {
-    return b == SB_RIN ? (T*)Rin : (b == SB_V ? (T*)V : (b == SB_W ? (T*)W : nullptr));
-  };
+  auto buf = [&](int b) -> T* { return b == SB_NONE ? nullptr : reinterpret_cast<T*>(arrs.p[b]); };
   const size_t gemv_cap = 200 * 1024;  // the narrow kernel keeps x (m x ncols) in shared memory
   constexpr int BM = 64, BN = 64, BK = 16, STG = 3;
   constexpr size_t gemm_smem = line_gemm_smem<R, BM, BN, BK, STG>();
@@ -718,17 +845,82 @@ static cudaError_t launch_steps_t(Engine& E, const void* Rin, void* V, void* W, 
   return cudaGetLastError();
 }
 
-double Engine::sweep_flops(int C, bool single) const {
-  const std::vector<SweepStep>& steps = single ? steps_single : steps_double;
+template <typename R>
+cudaError_t launch_group_simt(Engine& E, const SweepPhase& ph, const GArrays& arrs, int C, void* partial_buf,
+                              size_t partial_bytes);
+template <typename R>
+cudaError_t launch_copy_phase(Engine& E, const SweepPhase& ph, const GArrays& arrs, int C);
+cudaError_t launch_tc_group(Engine& E, int shape, const SweepPhase& ph, const GArrays& arrs, int C);
+
+// Algorithmic work of a grouped step: every task reads its terms' blocks and input lines once,
+// writes its output line (and reads its base, or the output itself when it adds to it).
+static double group_bytes(const Engine& E, const SweepPhase& ph, int C) {
+  const double e = (double)E.sweep_elem(), blkb = (double)E.m * E.m * e;
+  double b = 0;
+  for (const GTask& t : ph.tasks) {
+    const double line = (double)E.m * t.ns * C * e;
+    b += t.nterm * (blkb + line) + line * (1 + (t.base_arr != SB_NONE || t.mode == OUT_ADD));
+  }
+  return b;
+}
+static double group_flops(const Engine& E, const SweepPhase& ph, int C) {
   double f = 0;
-  for (const SweepStep& s : steps) f += 8.0 * m * m * (double)s.ns * C;
+  for (const GTask& t : ph.tasks) f += 8.0 * E.m * E.m * (double)t.ns * C * t.nterm;
+  return f;
+}
+
+// The phases of a sweep program in order: runs of block-Thomas steps, grouped steps (on the
+// tensor cores for complex64 with an even column count) and line copies.
+template <typename R>
+static cudaError_t launch_steps_t(Engine& E, const GArrays& arrs, int C, bool single, void* partial_buf,
+                                  size_t partial_bytes, bool allow_tick) {
+  const std::vector<SweepPhase>& prog = single ? E.prog_single : E.prog_double;
+  const bool tick_gemm = allow_tick && E.opts.profile;
+  for (size_t pi = 0; pi < prog.size();) {
+    const SweepPhase& ph = prog[pi];
+    if (ph.kind == PH_STEP) {
+      std::vector<SweepStep> run;
+      while (pi < prog.size() && prog[pi].kind == PH_STEP) run.push_back(prog[pi++].step);
+      const cudaError_t ce = run_steps_t<R>(E, run, arrs, C, partial_buf, partial_bytes, allow_tick);
+      if (ce != cudaSuccess) return ce;
+      continue;
+    }
+    cudaError_t ce;
+    if (ph.kind == PH_COPY) {
+      ce = launch_copy_phase<R>(E, ph, arrs, C);
+    } else if (std::is_same<R, float>::value && E.tc_ready && C % 2 == 0) {
+      const auto it = E.tc_tuned.find(C);
+      const int shape = it != E.tc_tuned.end() ? it->second.shape : 0;
+      if (tick_gemm) E.tick_begin(Engine::K_GEMM);
+      ce = launch_tc_group(E, shape, ph, arrs, C);
+      if (tick_gemm) E.tick_end(Engine::K_GEMM, group_bytes(E, ph, C), group_flops(E, ph, C));
+    } else {
+      ce = launch_group_simt<R>(E, ph, arrs, C, partial_buf, partial_bytes);
+    }
+    if (ce != cudaSuccess) return ce;
+    ++pi;
+  }
+  return cudaGetLastError();
+}
+
+double Engine::sweep_flops(int C, bool single) const {
+  const std::vector<SweepPhase>& prog = single ? prog_single : prog_double;
+  double f = 0;
+  for (const SweepPhase& p : prog) {
+    if (p.kind == PH_STEP) f += 8.0 * m * m * (double)p.step.ns * C;
+    else if (p.kind == PH_GROUP) f += group_flops(*this, p, C);
+  }
   return f;
 }
 
 double Engine::sweep_bytes(int C, bool single) const {
-  const std::vector<SweepStep>& steps = single ? steps_single : steps_double;
+  const std::vector<SweepPhase>& prog = single ? prog_single : prog_double;
   double b = 0;
-  for (const SweepStep& s : steps) b += step_bytes(*this, s, C);
+  for (const SweepPhase& p : prog) {
+    if (p.kind == PH_STEP) b += step_bytes(*this, p.step, C);
+    else if (p.kind == PH_GROUP) b += group_bytes(*this, p, C);
+    else b += 2.0 * m * p.tasks[0].ns * C * sweep_elem();
+  }
   return b;
 }
 
@@ -741,7 +933,7 @@ int Engine::run_sweep(const void* Rin, void* V, void* W, int C, bool single) {
 }
 
 int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool single, void* partial,
-                              size_t partial_bytes, bool allow_graph) {
+                              size_t partial_bytes, bool allow_graph, void* T0, void* T1) {
   // Every sample_every()-th sweep of a profiled handle, and the sweep of every timed Arnoldi step, times
   // its GEMM steps one by one and so runs eagerly; the others replay a captured graph.
   if (precision == HH_PREC_FP32 && tc_ready && allow_graph && C % 2 == 0 && !tc_tuned.count(C)) {
@@ -750,10 +942,15 @@ int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool sin
   }
   const bool sampled = opts.profile && ((sweep_calls++ % sample_every() == 0) || sample_next_sweep);
   sample_next_sweep = false;
+  GArrays arrs{};
+  arrs.p[SB_RIN] = const_cast<void*>(Rin);
+  arrs.p[SB_V] = V;
+  arrs.p[SB_W] = W;
+  arrs.p[SB_T0] = T0 ? T0 : w_t0;
+  arrs.p[SB_T1] = T1 ? T1 : w_t1;
   auto launch = [&](bool tick) {
-    return precision == HH_PREC_FP32
-               ? launch_steps_t<float>(*this, Rin, V, W, C, single, partial, partial_bytes, tick)
-               : launch_steps_t<double>(*this, Rin, V, W, C, single, partial, partial_bytes, tick);
+    return precision == HH_PREC_FP32 ? launch_steps_t<float>(*this, arrs, C, single, partial, partial_bytes, tick)
+                                     : launch_steps_t<double>(*this, arrs, C, single, partial, partial_bytes, tick);
   };
   if (!opts.use_graph || !allow_graph || sampled) {
     cudaError_t ce = launch(sampled);
@@ -794,9 +991,15 @@ int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool sin
 }
 
 int Engine::sweep_inline(const void* Rin, void* V, void* W, int C, bool single) {
+  GArrays arrs{};
+  arrs.p[SB_RIN] = const_cast<void*>(Rin);
+  arrs.p[SB_V] = V;
+  arrs.p[SB_W] = W;
+  arrs.p[SB_T0] = w_t0;
+  arrs.p[SB_T1] = w_t1;
   cudaError_t ce = precision == HH_PREC_FP32
-                       ? launch_steps_t<float>(*this, Rin, V, W, C, single, w_partial, w_partial_bytes, false)
-                       : launch_steps_t<double>(*this, Rin, V, W, C, single, w_partial, w_partial_bytes, false);
+                       ? launch_steps_t<float>(*this, arrs, C, single, w_partial, w_partial_bytes, false)
+                       : launch_steps_t<double>(*this, arrs, C, single, w_partial, w_partial_bytes, false);
   if (ce != cudaSuccess) { set_cuda_error(ce, "sweep launch"); return HH_ECUDA; }
   return HH_OK;
 }
@@ -845,6 +1048,8 @@ __global__ void tf32_split_kernel(const float* __restrict__ F, float* __restrict
   }
 }
 
+void set_tc_group_attributes();
+
 int Engine::load_encoder() {
   if (precision != HH_PREC_FP32 || !opts.tensor_cores) return HH_OK;
   if (encode_fn) return HH_OK;
@@ -869,6 +1074,7 @@ int Engine::load_encoder() {
                        (int)tc::Huge::SMEM);
   cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Huge, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)tc::Huge::SMEM);
+  set_tc_group_attributes();
   return HH_OK;
 }
 
@@ -1121,14 +1327,15 @@ int Engine::tune_tc(int C, const void* Rin, void* V, void* W, void* partial, siz
   return check_device_error("tensor-core autotune");
 }
 
-const Engine::LineMaps* Engine::line_maps_for(const void* buf, int C, int bnc) {
+const Engine::LineMaps* Engine::line_maps_for(const void* buf, int C, int bnc, int lines) {
+  if (lines <= 0) lines = R + 1;
   for (const LineMaps& lm : line_maps)
-    if (lm.ptr == buf && lm.C == C && lm.bnc == bnc) return &lm;
+    if (lm.ptr == buf && lm.C == C && lm.bnc == bnc && lm.lines == lines) return &lm;
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(encode_fn);
   if (!encode || C % 2) return nullptr;
   LineMaps& lm = line_maps[line_maps_next];
-  line_maps_next = (line_maps_next + 1) % 16;
-  const cuuint64_t dims[3] = {(cuuint64_t)2 * N * C, (cuuint64_t)m, (cuuint64_t)(R + 1)};
+  line_maps_next = (line_maps_next + 1) % 24;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * N * C, (cuuint64_t)m, (cuuint64_t)lines};
   const cuuint64_t strides[2] = {(cuuint64_t)2 * N * C * sizeof(float), (cuuint64_t)m * 2 * N * C * sizeof(float)};
   const cuuint32_t estr[3] = {1, 1, 1};
   const cuuint32_t box_b[3] = {(cuuint32_t)(2 * bnc), (cuuint32_t)tc::RAW_BASE_ROWS, 1};
@@ -1147,6 +1354,7 @@ const Engine::LineMaps* Engine::line_maps_for(const void* buf, int C, int bnc) {
   lm.ptr = buf;
   lm.C = C;
   lm.bnc = bnc;
+  lm.lines = lines;
   return &lm;
 }
 

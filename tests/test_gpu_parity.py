@@ -401,8 +401,10 @@ def test_fused_interface_chains(precision, ncols, single):
     bar = 1e-10 if precision == "fp64" else 2e-4
     # both handles run the same tensor-core candidate (the autotuner could give them forms
     # with different launches per wide step), so the launch counts differ by the fusion only
-    with hh.Handle(k, n, N, precision=precision, single_sweep=single, autotune=0) as hf, \
-            hh.Handle(k, n, N, precision=precision, single_sweep=single, fuse_chains=0, autotune=0) as hu:
+    # the chains exist in interface form 0 (form 1 replaces them by scans)
+    with hh.Handle(k, n, N, precision=precision, single_sweep=single, autotune=0, interface_form=0) as hf, \
+            hh.Handle(k, n, N, precision=precision, single_sweep=single, fuse_chains=0, autotune=0,
+                      interface_form=0) as hu:
         for d in sweep.DIRECTIONS:
             hf.apply_preconditioner(d, rr, ncols)
             hu.apply_preconditioner(d, rr, ncols)
@@ -423,8 +425,8 @@ def test_fused_interface_chain_many_rows():
     (each warp takes several rows); the fused chains equal the per-step form to rounding."""
     k, n, N = 600.0, 1536, 16
     rr = np.ascontiguousarray(hh_inputs.random_vector((n + 1) ** 2, 4, seed=12).ravel())
-    with hh.Handle(k, n, N, precision="fp32", autotune=0) as hf, \
-            hh.Handle(k, n, N, precision="fp32", autotune=0, fuse_chains=0) as hu:
+    with hh.Handle(k, n, N, precision="fp32", autotune=0, interface_form=0) as hf, \
+            hh.Handle(k, n, N, precision="fp32", autotune=0, fuse_chains=0, interface_form=0) as hu:
         for d in ("BT", "LR"):
             zf = hf.apply_preconditioner(d, rr, 4)
             zu = hu.apply_preconditioner(d, rr, 4)
@@ -465,3 +467,29 @@ def test_tensor_map_cache_turnover():
             z = h.apply_preconditioner("LR", np.ascontiguousarray(r.ravel()), ncols).reshape(ncols, -1)
             for c in range(ncols):
                 assert rel(z[c], sw.apply(r[c])) < 2e-4, (ncols, c)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,n,N", CASES + [(10.0, 16, 2), (25.0, 64, 16), (20.0, 36, 6)])
+@pytest.mark.parametrize("double", [True, False])
+def test_interface_scans_and_block_column_corrections(precision, k, n, N, double):
+    """Interface form 1 (prefix-doubling scans of the strip-to-strip recurrences, interior
+    corrections as one grouped step with stored block columns of the strip inverse) against
+    the oracle's sweep and against interface form 0 (chains and block-Thomas corrections):
+    the same sweep up to rounding.  N = 2, 3, 5, 6 strips cover scans of 0, 1 and ragged
+    numbers of levels; 4 columns (the tensor cores for complex64) and 3 (the CUDA cores)."""
+    A, *_ = fem.global_system(k, n)
+    for ncols in (4, 3):
+        r = hh_inputs.random_vector(A.shape[0], ncols, seed=30 + ncols)
+        rr = np.ascontiguousarray(r.ravel())
+        bar = 1e-10 if precision == "fp64" else 2e-4
+        with hh.Handle(k, n, N, precision=precision, single_sweep=0 if double else 1) as h1, \
+                hh.Handle(k, n, N, precision=precision, single_sweep=0 if double else 1, interface_form=0) as h0:
+            assert h1.stats()["sweep_steps"] < h0.stats()["sweep_steps"] or N <= 2
+            for d in sweep.DIRECTIONS:
+                z1 = h1.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                z0 = h0.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                assert rel(z1, z0) < (1e-11 if precision == "fp64" else 1e-4), (d, ncols)
+                sw = sweep.Sweeper(A, k, n, N, d)
+                for c in range(ncols):
+                    assert rel(z1[c], sw.apply(r[c], double)) < bar, (d, c, ncols)
