@@ -65,7 +65,13 @@ typedef struct {
   int single_sweep;       /* 1: forward sweeps only (LR, RL, BT, TB of Section 4) */
   int maxit;              /* iteration limit (default 200) */
   double deflate_eta;     /* deflation threshold r_jj <= eta * ||w_j|| (default 1e-10) */
-  int bcr_depth;          /* reserved: 0 = block Thomas strip solves (the only value accepted) */
+  int bcr_depth;          /* the strip solves with a full right-hand side (w = D^{-1} r, every strip):
+                             0 (default): block Thomas, 2R+1 dependent steps; d >= 1 (n / strips
+                             divisible by 2^d): d levels of block cyclic (odd-even) reduction, then
+                             block Thomas on the reduced system of R / 2^d lines, 2d + 2R/2^d + 1
+                             dependent steps, every level one grouped step over its lines and all
+                             strips; -1: the blocks of every usable depth are stored and the
+                             fastest depth is picked by timing whole sweeps, per column count */
   int64_t timeout_cycles; /* SM clock budget of every device-side wait (default 4e9) */
   void* stream;           /* cudaStream_t to run on, or NULL for the handle's own stream */
   int use_graph;          /* 1 (default): every Arnoldi step (table gather, pack, the sweep's
@@ -150,6 +156,8 @@ typedef struct {
                                opts.profile the classes above time the sampled steps) */
   int step_graphs;          /* Arnoldi-step graphs captured by the handle's solvers */
   int step_graph_fallback;  /* 1 if a step could not be captured and ran eagerly */
+  int bcr_depth;            /* cyclic-reduction depth of the strip solves for the last column
+                               count (fixed by opts.bcr_depth or autotuned) */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -55,7 +55,7 @@ class hh_stats(ctypes.Structure):
                 ("gsdot_flops", ctypes.c_double), ("gs_flops", ctypes.c_double), ("wide_steps", ctypes.c_int64),
                 ("ns_blocks", ctypes.c_int), ("ns_iterations", ctypes.c_int), ("tc_bnc", ctypes.c_int),
                 ("tc_nsplit", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_us", ctypes.c_double), ("iterations_total", ctypes.c_int64),
-                ("step_graphs", ctypes.c_int), ("step_graph_fallback", ctypes.c_int)]
+                ("step_graphs", ctypes.c_int), ("step_graph_fallback", ctypes.c_int), ("bcr_depth", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -130,7 +130,9 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   if ((dirs & 15u) == 0 || (dirs & ~15u)) return (set_error("dirs must be a non-empty subset of HH_DIR_*"), HH_EINVAL);
   if (opts.precision != HH_PREC_FP32 && opts.precision != HH_PREC_FP64) return (set_error("bad precision"), HH_EINVAL);
   if (opts.maxit < 1 || opts.maxit > 2000) return (set_error("maxit must be in [1, 2000]"), HH_EINVAL);
-  if (opts.bcr_depth != 0) return (set_error("only bcr_depth = 0 (block Thomas strip solves) is implemented"), HH_EINVAL);
+  if (opts.bcr_depth < -1 || (opts.bcr_depth > 0 && (n_ % strips != 0 || opts.bcr_depth > max_bcr_depth(n_ / strips))))
+    return (set_error("bcr_depth must be -1 (autotune), 0 (block Thomas) or d >= 1 with n / strips divisible by 2^d"),
+            HH_EINVAL);
   if (opts.gs_passes != 1 && opts.gs_passes != 2) return (set_error("gs_passes must be 1 or 2"), HH_EINVAL);
   if (opts.serve_slots < 1 || opts.serve_slots > 256) return (set_error("serve_slots must be in 1..256"), HH_EINVAL);
   if (opts.interface_form != 0 && opts.interface_form != 1) return (set_error("interface_form must be 0 or 1"), HH_EINVAL);
@@ -139,7 +141,15 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   precision = opts.precision;
   ldf = (m + 3) & ~3;
   coef.init(k, n);
-  bdir = block_directory(R, N, opts.interface_form);
+  {
+    // cyclic-reduction blocks: the requested depth, or every usable depth for the autotuner
+    unsigned depths = 0;
+    const int dl = max_bcr_depth(R);
+    if (opts.bcr_depth > 0) depths = 1u << opts.bcr_depth;
+    else if (opts.bcr_depth < 0)
+      for (int d = 1; d <= dl; ++d) depths |= 1u << d;
+    bdir = block_directory(R, N, opts.interface_form, depths);
+  }
   static const int bitcode[4] = {DC_LR, DC_RL, DC_BT, DC_TB};
   dir_codes.clear();
   for (int b = 0; b < 4; ++b)
@@ -181,8 +191,11 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   cudaMemsetAsync(err, 0, 64, stream);
   steps_double = build_steps(n, N, true);
   steps_single = build_steps(n, N, false);
-  prog_double = build_program(n, N, true, opts.interface_form, bdir);
-  prog_single = build_program(n, N, false, opts.interface_form, bdir);
+  for (int d = 0; d <= bdir.dmax; ++d)
+    if (d == 0 || bdir.iDeep[d] >= 0) {
+      prog_double_d[d] = build_program(n, N, true, opts.interface_form, bdir, d);
+      prog_single_d[d] = build_program(n, N, false, opts.interface_form, bdir, d);
+    }
   if (upload_programs()) return HH_ENOMEM;
   cudaStreamSynchronize(stream);
 
@@ -548,7 +561,8 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->m = E.m;
   st->ldf = E.ldf;
   st->columns = E.last_columns;
-  st->sweep_steps = (int64_t)(E.opts.single_sweep ? E.prog_single.size() : E.prog_double.size());
+  st->sweep_steps = (int64_t)E.program(E.last_columns, E.opts.single_sweep != 0).size();
+  st->bcr_depth = E.depth_for(E.last_columns);
   st->gemm_launches = E.launches[Engine::K_GEMM];
   st->gemm_ms = E.ms[Engine::K_GEMM];
   st->gemm_flops = E.flops[Engine::K_GEMM];
@@ -571,7 +585,7 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
       st->tc_us = it->second.us;
     }
   }
-  for (const SweepPhase& ph : E.opts.single_sweep ? E.prog_single : E.prog_double)
+  for (const SweepPhase& ph : E.program(E.last_columns, E.opts.single_sweep != 0))
     st->wide_steps += (int64_t)(ph.kind == PH_GROUP || (ph.kind == PH_STEP && ph.step.ns * E.last_columns > 8));
   return HH_OK;
 }

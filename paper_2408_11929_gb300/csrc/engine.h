@@ -70,10 +70,21 @@ struct BlockDir {
   int iGp = -1;  // G^(2^l), l = 1..LF-1 at iGp + l - 1
   int iKp = -1;  // K^(2^l), l = 1..LB-1 at iKp + l - 1
   int LF = 0, LB = 0;  // levels of the forward / backward interface scans
-  int total = 0;       // blocks in the store
+  // block cyclic reduction of the strip solves (levels 1..dmax): at level l the odd lines of
+  // the level-(l-1) system are eliminated; its blocks are Dinv = D_int^{-1}, L Dinv, U Dinv,
+  // Dinv L, Dinv U at iLev + 5 (l - 1) + 0..4.  For each depth d in 1..dmax the block-Thomas
+  // factors of the reduced system (nd = R / 2^d lines, the last strip one more): F_0..F_{nd-1},
+  // F_top, G_1..G_{nd-1} (F_i L), G_top, H_0..H_{nd-1} (F_i U) from iDeep[d].
+  int dmax = 0, iLev = -1;
+  int iDeep[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  int total = 0;  // blocks in the store
 };
-BlockDir block_directory(int R, int N, int form);
-std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form, const BlockDir& bd);
+// form: interface form (0, 1); depths: bit d set = the blocks of cyclic-reduction depth d
+BlockDir block_directory(int R, int N, int form, unsigned depths = 0);
+// depth: cyclic-reduction levels of the full-right-hand-side strip solves (0: block Thomas)
+std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form, const BlockDir& bd, int depth = 0);
+// largest usable depth: R divisible by 2^d (at most 7)
+int max_bcr_depth(int R);
 
 // Direction codes of the BT frame mapping (node of the BT frame -> node of the grid).
 enum DirCode { DC_BT = 0, DC_TB = 1, DC_LR = 2, DC_RL = 3 };
@@ -159,7 +170,13 @@ class Engine {
   // sweep programs (opts.interface_form): phases of a double and of a single sweep, their
   // grouped tasks in one device table
   BlockDir bdir;
-  std::vector<SweepPhase> prog_double, prog_single;
+  // programs of every cyclic-reduction depth whose blocks are stored (index = depth)
+  std::vector<SweepPhase> prog_double_d[8], prog_single_d[8];
+  int bcr_blocks();                          // setup.cu: the cyclic-reduction blocks of bdir
+  std::map<int, int> bcr_tuned;              // depth per column count (fixed or autotuned)
+  int depth_for(int C) const;                // the depth a sweep of C columns uses
+  const std::vector<SweepPhase>& program(int C, bool single) const;
+  int tune_depth(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes);
   GTask* prog_tasks = nullptr;
   int upload_programs();
   size_t bytes_allocated = 0;

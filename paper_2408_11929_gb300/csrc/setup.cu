@@ -561,6 +561,199 @@ static bool newton_schulz(Engine& E, const typename Cx<R>::T* S, const typename 
   return false;
 }
 
+// Dense m x m line blocks for the cyclic-reduction setup: which = 0..2 the diagonal block of a
+// line of type BOT / INT / TOP (tridiagonal), 3 the coupling L to the line below
+// (L[a][a] = vert(a), L[a][a-1] = diag), 4 the coupling U = L^T to the line above.
+template <typename R>
+__global__ void line_block_kernel(typename Cx<R>::T* __restrict__ Z, int m, int ld, Coef cf, int which) {
+  using T = typename Cx<R>::T;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < (size_t)m * ld; idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / ld), b = (int)(idx % ld);
+    double2 v = make_double2(0.0, 0.0);
+    if (b < m) {
+      if (which <= 2) {
+        if (a == b) v = cf.centre(a, which);
+        else if (a - b == 1 || b - a == 1) v = cf.horiz(which);
+      } else {
+        if (a == b) v = cf.vert(a);
+        else if ((which == 3 && b == a - 1) || (which == 4 && b == a + 1)) v = make_double2(cf.diag(), 0.0);
+      }
+    }
+    Z[idx] = mk<T>(v.x, v.y);
+  }
+}
+
+// column 0 of S, contiguous (the first pivot column of the Gauss-Jordan inversion)
+template <typename R>
+__global__ void col0_kernel(const typename Cx<R>::T* __restrict__ S, int ld, int m, typename Cx<R>::T* __restrict__ col) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x) col[a] = S[(size_t)a * ld];
+}
+
+// Inverse of one dense m x m block for the cyclic-reduction setup: complex64 by Newton-Schulz
+// (from a given start, else the Jacobi start, else the scaled adjoint), then pivoted
+// Gauss-Jordan as the last resort; complex128 by Gauss-Jordan.
+template <typename R>
+struct BlockInverter {
+  using T = typename Cx<R>::T;
+  Engine& E;
+  T *A = nullptr, *B = nullptr, *col = nullptr, *Tb = nullptr, *Xb = nullptr, *Xs = nullptr;
+  int *piv = nullptr, *srcidx = nullptr;
+  double *part_dev = nullptr, *part_host = nullptr, *sums_dev = nullptr, *sums_host = nullptr;
+  int inversions = 0, ns_iters = 0;
+  explicit BlockInverter(Engine& e) : E(e) {}
+  int alloc() {
+    const size_t mat = (size_t)E.m * E.ldf * sizeof(T);
+    if (E.dmalloc((void**)&A, mat) || E.dmalloc((void**)&B, mat) || E.dmalloc((void**)&col, 2 * E.m * sizeof(T)) ||
+        E.dmalloc((void**)&Tb, mat) || E.dmalloc((void**)&Xb, mat) || E.dmalloc((void**)&Xs, mat) ||
+        E.dmalloc((void**)&piv, E.m * sizeof(int)) || E.dmalloc((void**)&srcidx, E.m * sizeof(int)) ||
+        E.dmalloc((void**)&part_dev, sizeof(double) * 2 * E.num_sms) ||
+        E.dmalloc((void**)&sums_dev, sizeof(double) * 2 * E.m) ||
+        cudaMallocHost((void**)&part_host, sizeof(double) * 2 * E.num_sms) != cudaSuccess ||
+        cudaMallocHost((void**)&sums_host, sizeof(double) * 2 * E.m) != cudaSuccess)
+      return HH_ENOMEM;
+    return HH_OK;
+  }
+  ~BlockInverter() {
+    cudaStreamSynchronize(E.stream);
+    E.dfree(A); E.dfree(B); E.dfree(col); E.dfree(Tb); E.dfree(Xb); E.dfree(Xs);
+    E.dfree(piv); E.dfree(srcidx); E.dfree(part_dev); E.dfree(sums_dev);
+    if (part_host) cudaFreeHost(part_host);
+    if (sums_host) cudaFreeHost(sums_host);
+  }
+  // out = S^{-1}; S is left unchanged; X0 (optional) a start close to the inverse
+  int invert(const T* S, const T* X0, T* out) {
+    const int m = E.m, ld = E.ldf;
+    ++inversions;
+    if constexpr (sizeof(R) == 4) {
+      for (int start = X0 ? 0 : 1; start < 3; ++start) {
+        const T* X = X0;
+        if (start == 1) {
+          jacobi_start_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(S, ld, m, Xs);
+          E.count_launch();
+          X = Xs;
+        } else if (start == 2) {
+          const int row_blocks = (m + 7) / 8;
+          abs_sums_kernel<R><<<row_blocks + (m + 255) / 256, 256, 0, E.stream>>>(S, ld, m, sums_dev, row_blocks);
+          E.count_launch();
+          cudaMemcpyAsync(sums_host, sums_dev, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, E.stream);
+          if (cudaStreamSynchronize(E.stream) != cudaSuccess) break;
+          double r1 = 0, ri = 0;
+          for (int q = 0; q < m; ++q) { ri = std::max(ri, sums_host[q]); r1 = std::max(r1, sums_host[m + q]); }
+          if (!(r1 > 0 && ri > 0)) break;
+          scaled_adjoint_kernel<R><<<E.grid_for((size_t)m * m), 256, 0, E.stream>>>(S, ld, m, 1.0 / (r1 * ri), Xs);
+          E.count_launch();
+          X = Xs;
+        }
+        int it = 0;
+        const bool ok = newton_schulz<R>(E, S, X, out, Tb, Xb, part_dev, part_host, it, start == 2);
+        ns_iters += it;
+        if (ok) return E.check_device_error("cyclic-reduction setup");
+      }
+    }
+    cudaMemcpyAsync(A, S, sizeof(T) * (size_t)m * ld, cudaMemcpyDeviceToDevice, E.stream);
+    col0_kernel<R><<<(m + 255) / 256, 256, 0, E.stream>>>(S, ld, m, col);
+    cudaMemsetAsync(E.bar + Engine::BAR_SETUP * GRID_BAR_WORDS, 0, GRID_BAR_WORDS * sizeof(unsigned), E.stream);
+    cudaMemsetAsync(piv, 0, m * sizeof(int), E.stream);
+    int mm = m, ldd = ld;
+    void* args[] = {(void*)&A, (void*)&B, (void*)&col, (void*)&piv, (void*)&mm, (void*)&ldd,
+                    (void*)&E.bar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
+    const int grid = E.num_sms < m ? E.num_sms : m;
+    cudaError_t ce = E.launch_coop((const void*)gj_kernel<R>, grid, 1024, 0, args);
+    if (ce != cudaSuccess) { E.set_cuda_error(ce, "gj_kernel launch"); return HH_ECUDA; }
+    const T* W = ((m - 1) & 1) ? A : B;
+    gj_perm_index<<<1, 1, 0, E.stream>>>(piv, srcidx, m);
+    gj_permute<R><<<E.grid_for((size_t)m * ld), 256, 0, E.stream>>>(W, ld, srcidx, out, ld, m);
+    E.count_launch(3);
+    return E.check_device_error("cyclic-reduction setup");
+  }
+};
+
+// Blocks of block cyclic reduction of the strip solves (see append_bcr_f1 in sweep.cu).  The
+// level-0 system of a strip is block tridiagonal over its node lines: diagonal blocks D_BOT
+// (line 0), D_INT, D_TOP (the last strip's line R), couplings L (to the line below) and U.
+// Eliminating the odd lines of a level-(l-1) system (all of type INT) with Dinv = D_INT^{-1}
+// leaves, on the even lines, the level-l system
+//   D_INT' = D_INT - L Dinv U - U Dinv L,  D_BOT' = D_BOT - U Dinv L,  D_TOP' = D_TOP - L Dinv U,
+//   L' = -L Dinv L,  U' = -U Dinv U;
+// stored per level: Dinv, L Dinv, U Dinv (forward), Dinv L, Dinv U (back substitution).  For
+// each depth d, block Thomas on the reduced system: S_0 = D_BOT^(d),
+// S_i = D_INT^(d) - L^(d) F_{i-1} U^(d), S_top = D_TOP^(d) - L^(d) F_{nd-1} U^(d), F = S^{-1},
+// G = F L^(d), H = F U^(d).  Products on the exact GEMM, inverses as above.
+template <typename R>
+int bcr_blocks_impl(Engine& E) {
+  using T = typename Cx<R>::T;
+  const BlockDir& bd = E.bdir;
+  if (bd.dmax == 0) return HH_OK;
+  const int m = E.m, ld = E.ldf;
+  const size_t blk = (size_t)m * ld;
+  T* F = reinterpret_cast<T*>(E.factors);
+  auto B = [&](int i) { return F + (size_t)i * blk; };
+  T* sc[7] = {};
+  for (T*& p : sc)
+    if (E.dmalloc((void**)&p, blk * sizeof(T))) {
+      for (T* q : sc) E.dfree(q);
+      return HH_ENOMEM;
+    }
+  T *Db = sc[0], *Di = sc[1], *Dt = sc[2], *Lc = sc[3], *Uc = sc[4], *T1 = sc[5], *T2 = sc[6];
+  int rc = HH_OK;
+  {
+    BlockInverter<R> inv(E);
+    rc = inv.alloc();
+    const unsigned g = E.grid_for(blk);
+    T* lb[5] = {Db, Di, Dt, Lc, Uc};
+    for (int w = 0; w < 5 && rc == HH_OK; ++w) {
+      line_block_kernel<R><<<g, 256, 0, E.stream>>>(lb[w], m, ld, E.coef, w);
+      E.count_launch();
+    }
+    int products = 0;
+    E.tick_begin(Engine::K_SETUP);
+    for (int l = 1; l <= bd.dmax && rc == HH_OK; ++l) {
+      const int lev = bd.iLev + 5 * (l - 1);
+      T *Dinv = B(lev), *AF = B(lev + 1), *BF = B(lev + 2), *P = B(lev + 3), *Q = B(lev + 4);
+      rc = inv.invert(Di, nullptr, Dinv);
+      if (rc) break;
+      exact_gemm<R>(E, Lc, Dinv, AF, 1.0);
+      exact_gemm<R>(E, Uc, Dinv, BF, 1.0);
+      exact_gemm<R>(E, Dinv, Lc, P, 1.0);
+      exact_gemm<R>(E, Dinv, Uc, Q, 1.0);
+      exact_gemm<R>(E, AF, Uc, Di, -1.0, Di);
+      exact_gemm<R>(E, BF, Lc, Di, -1.0, Di);
+      exact_gemm<R>(E, BF, Lc, Db, -1.0, Db);
+      exact_gemm<R>(E, AF, Uc, Dt, -1.0, Dt);
+      exact_gemm<R>(E, AF, Lc, T1, -1.0);
+      exact_gemm<R>(E, BF, Uc, T2, -1.0);
+      std::swap(Lc, T1);
+      std::swap(Uc, T2);
+      products += 10;
+      if (bd.iDeep[l] < 0) continue;
+      // block Thomas on the level-l system
+      const int nd = E.R >> l, b = bd.iDeep[l];
+      const int iF = b, iFtop = b + nd, iGtop = b + 2 * nd, iH = b + 2 * nd + 1;
+      rc = inv.invert(Db, nullptr, B(iF));
+      for (int i = 1; i <= nd && rc == HH_OK; ++i) {
+        exact_gemm<R>(E, Lc, B(iF + i - 1), T1, 1.0);
+        exact_gemm<R>(E, T1, Uc, T2, -1.0, i < nd ? Di : Dt);
+        rc = inv.invert(T2, B(iF + i - 1), B(i < nd ? iF + i : iFtop));
+        products += 2;
+      }
+      for (int i = 1; i < nd && rc == HH_OK; ++i) exact_gemm<R>(E, B(iF + i), Lc, B(b + nd + i), 1.0);
+      if (rc == HH_OK) exact_gemm<R>(E, B(iFtop), Lc, B(iGtop), 1.0);
+      for (int i = 0; i < nd && rc == HH_OK; ++i) exact_gemm<R>(E, B(iF + i), Uc, B(iH + i), 1.0);
+      products += 2 * nd;
+    }
+    E.tick_end(Engine::K_SETUP, 0.0, products * 8.0 * m * (double)m * m);
+  }
+  const cudaError_t ce = cudaStreamSynchronize(E.stream);
+  for (T* q : sc) E.dfree(q);
+  if (rc) return rc;
+  if (ce != cudaSuccess) { E.set_cuda_error(ce, "cyclic-reduction setup"); return HH_ECUDA; }
+  return E.check_device_error("cyclic-reduction setup");
+}
+
+int Engine::bcr_blocks() {
+  return precision == HH_PREC_FP32 ? bcr_blocks_impl<float>(*this) : bcr_blocks_impl<double>(*this);
+}
+
 template <typename R>
 int factor_impl(Engine& E) {
   using T = typename Cx<R>::T;
@@ -669,6 +862,7 @@ int factor_impl(Engine& E) {
   if (status == HH_OK) status = E.check_device_error("strip setup");
   if (status == HH_OK) status = interface_blocks<R>(E, bufA, bufB);
   if (status == HH_OK) status = inverse_columns_impl<R>(E);
+  if (status == HH_OK) status = bcr_blocks_impl<R>(E);
   E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
   E.dfree(bufC); E.dfree(bufD); E.dfree(part_dev); E.dfree(sums_dev);
   if (part_host) cudaFreeHost(part_host);

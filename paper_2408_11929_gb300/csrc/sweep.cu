@@ -123,19 +123,116 @@ static int ceil_log2(int v) {
   return l;
 }
 
-BlockDir block_directory(int R, int N, int form) {
+int max_bcr_depth(int R) {
+  int d = 0;
+  while (d < 7 && R % (2 << d) == 0) ++d;
+  return d;
+}
+
+BlockDir block_directory(int R, int N, int form, unsigned depths) {
   BlockDir bd;
   bd.total = R + 3;
-  if (form == 0 || N < 2) return bd;
-  bd.LF = N >= 3 ? ceil_log2(N - 1) : 0;
-  bd.LB = ceil_log2(N);
-  bd.iY = R + 3;
-  bd.iYL = bd.iY + R;
-  bd.iZ = bd.iYL + R + 1;
-  bd.iGp = bd.iZ + (R - 1);
-  bd.iKp = bd.iGp + std::max(0, bd.LF - 1);
-  bd.total = bd.iKp + std::max(0, bd.LB - 1);
+  if (form != 0 && N >= 2) {
+    bd.LF = N >= 3 ? ceil_log2(N - 1) : 0;
+    bd.LB = ceil_log2(N);
+    bd.iY = R + 3;
+    bd.iYL = bd.iY + R;
+    bd.iZ = bd.iYL + R + 1;
+    bd.iGp = bd.iZ + (R - 1);
+    bd.iKp = bd.iGp + std::max(0, bd.LF - 1);
+    bd.total = bd.iKp + std::max(0, bd.LB - 1);
+  }
+  const int dlim = max_bcr_depth(R);
+  for (int d = 1; d <= dlim; ++d)
+    if (depths & (1u << d)) bd.dmax = d;
+  if (bd.dmax > 0) {
+    bd.iLev = bd.total;
+    bd.total += 5 * bd.dmax;
+    for (int d = 1; d <= bd.dmax; ++d)
+      if (depths & (1u << d)) {
+        bd.iDeep[d] = bd.total;
+        bd.total += 3 * (R >> d) + 1;
+      }
+  }
   return bd;
+}
+
+// F1 (w_s = D^{-1} r_s for every strip) by block cyclic reduction of depth d >= 1 (Section 2's
+// strip solve is block LU of a block-tridiagonal matrix; odd-even reduction orders it so
+// that every level is one grouped step over all its lines and strips):
+//   forward, level l = 1..d (h = 2^(l-1), source Rin at l = 1, else W): the kept lines
+//     p = 0, 2h, 4h, .. (and R in the last strip) get
+//     r^l_p = r^(l-1)_p - (L Dinv) r^(l-1)_{p-h} - (U Dinv) r^(l-1)_{p+h}   (into W);
+//   the reduced system (lines p = i 2^d) by block Thomas with dense couplings:
+//     y_i = F_i r_i for every line at once, then y_i -= G_i y_{i-1} (chain), the last strip's
+//     top line y_top -= G_top y_{nd-1}, then u_i = y_i - H_i u_{i+1} (chain; the strips before
+//     the last start one line lower: their top line has nothing above it);
+//   back substitution, level l = d..1: the eliminated lines p = h, 3h, .. get
+//     u_p = Dinv r^(l-1)_p - (Dinv L) u_{p-h} - (Dinv U) u_{p+h}   (into V),
+//   the top eliminated line of the strips before the last without the last term.
+static void append_bcr_f1(std::vector<SweepPhase>& prog, int R, int N, int d, const BlockDir& bd) {
+  auto term = [](int f, int arr, int line, int neg) { return GTerm{f, arr, line, 0, neg}; };
+  auto task = [](std::initializer_list<GTerm> terms, int out_arr, int out_line, int base_arr, int base_line,
+                 int mode, int s0, int ns) {
+    GTask t{};
+    t.nterm = 0;
+    for (const GTerm& g : terms) t.term[t.nterm++] = g;
+    t.out_arr = out_arr; t.out_line = out_line;
+    t.base_arr = base_arr; t.base_line = base_line;
+    t.mode = mode; t.s0 = s0; t.ns = ns;
+    return t;
+  };
+  auto group = [](std::vector<GTask> ts) {
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    for (const GTask& t : ts)
+      if (t.ns > 0) p.tasks.push_back(t);
+    return p;
+  };
+  const int last = N - 1, nl = N - 1;  // the last strip; the strips before it
+  for (int l = 1; l <= d; ++l) {
+    const int h = 1 << (l - 1), src = l == 1 ? SB_RIN : SB_W;
+    const int lev = bd.iLev + 5 * (l - 1), AF = lev + 1, BF = lev + 2;
+    std::vector<GTask> ts;
+    ts.push_back(task({term(BF, src, h, 1)}, SB_W, 0, src, 0, OUT_SET, 0, N));
+    for (int p = 2 * h; p < R; p += 2 * h)
+      ts.push_back(task({term(AF, src, p - h, 1), term(BF, src, p + h, 1)}, SB_W, p, src, p, OUT_SET, 0, N));
+    ts.push_back(task({term(AF, src, R - h, 1)}, SB_W, R, src, R, OUT_SET, last, 1));
+    prog.push_back(group(ts));
+  }
+  const int nd = R >> d, S = 1 << d, b = bd.iDeep[d];
+  const int iF = b, iFtop = b + nd, iGtop = b + 2 * nd, iH = b + 2 * nd + 1;
+  auto iG = [&](int i) { return b + nd + i; };
+  {
+    std::vector<GTask> ts;
+    for (int i = 0; i < nd; ++i) ts.push_back(task({term(iF + i, SB_W, i * S, 0)}, SB_V, i * S, SB_NONE, 0, OUT_SET, 0, N));
+    ts.push_back(task({term(iFtop, SB_W, R, 0)}, SB_V, R, SB_NONE, 0, OUT_SET, last, 1));
+    prog.push_back(group(ts));
+  }
+  for (int i = 1; i < nd; ++i)
+    prog.push_back(group({task({term(iG(i), SB_V, (i - 1) * S, 1)}, SB_V, i * S, SB_NONE, 0, OUT_ADD, 0, N)}));
+  prog.push_back(group({task({term(iGtop, SB_V, R - S, 1)}, SB_V, R, SB_NONE, 0, OUT_ADD, last, 1)}));
+  for (int q = 0; q < nd; ++q) {
+    std::vector<GTask> ts;
+    const int il = nd - 1 - q;  // the last strip's line
+    ts.push_back(task({term(iH + il, SB_V, (il + 1) * S, 1)}, SB_V, il * S, SB_NONE, 0, OUT_ADD, last, 1));
+    const int io = nd - 2 - q;  // the other strips' line
+    if (io >= 0) ts.push_back(task({term(iH + io, SB_V, (io + 1) * S, 1)}, SB_V, io * S, SB_NONE, 0, OUT_ADD, 0, nl));
+    prog.push_back(group(ts));
+  }
+  for (int l = d; l >= 1; --l) {
+    const int h = 1 << (l - 1), src = l == 1 ? SB_RIN : SB_W;
+    const int lev = bd.iLev + 5 * (l - 1), Dinv = lev, P = lev + 3, Q = lev + 4;
+    std::vector<GTask> ts;
+    for (int p = h; p < R - h; p += 2 * h)
+      ts.push_back(task({term(Dinv, src, p, 0), term(P, SB_V, p - h, 1), term(Q, SB_V, p + h, 1)}, SB_V, p,
+                        SB_NONE, 0, OUT_SET, 0, N));
+    ts.push_back(task({term(Dinv, src, R - h, 0), term(P, SB_V, R - 2 * h, 1)}, SB_V, R - h, SB_NONE, 0, OUT_SET, 0,
+                      nl));
+    ts.push_back(task({term(Dinv, src, R - h, 0), term(P, SB_V, R - 2 * h, 1), term(Q, SB_V, R, 1)}, SB_V, R - h,
+                      SB_NONE, 0, OUT_SET, last, 1));
+    prog.push_back(group(ts));
+  }
 }
 
 // The double sweep with the interface data passed by scans and the interior corrections as
@@ -152,7 +249,7 @@ BlockDir block_directory(int R, int N, int form) {
 //   B2  u_s[j] = v_s[j] - Z_j u_{s+1}[0], lines j = 1..R-1 of strips 0..N-2 in one step,
 //       Z_j = D^{-1}[j, R-1] U.
 // Every step is exact algebra on the block-Thomas form; only the order of the sums differs.
-std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form, const BlockDir& bd) {
+std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form, const BlockDir& bd, int depth) {
   std::vector<SweepPhase> prog;
   const int R = n / N;
   auto as_step = [](const SweepStep& x) {
@@ -161,12 +258,14 @@ std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form,
     p.step = x;
     return p;
   };
+  const std::vector<SweepStep> legacy = build_steps(n, N, double_sweep);
+  if (depth > 0) append_bcr_f1(prog, R, N, depth, bd);
+  else
+    for (int q = 0; q < 2 * R + 1; ++q) prog.push_back(as_step(legacy[q]));  // F1
   if (form == 0 || N < 2) {
-    for (const SweepStep& x : build_steps(n, N, double_sweep)) prog.push_back(as_step(x));
+    for (size_t q = 2 * R + 1; q < legacy.size(); ++q) prog.push_back(as_step(legacy[q]));
     return prog;
   }
-  const std::vector<SweepStep> legacy = build_steps(n, N, false);
-  for (int q = 0; q < 2 * R + 1; ++q) prog.push_back(as_step(legacy[q]));  // F1
   auto task1 = [](int f, int arr, int line, int ds, int neg, int out_arr, int out_line, int base_arr, int base_line,
                   int mode, int s0, int ns) {
     GTask t{};
@@ -596,13 +695,25 @@ __global__ void __launch_bounds__(1024) chain_kernel(const typename Cx<R>::T* __
   }
 }
 
+int Engine::depth_for(int C) const {
+  const auto it = bcr_tuned.find(C);
+  if (it != bcr_tuned.end()) return it->second;
+  return opts.bcr_depth > 0 ? opts.bcr_depth : 0;
+}
+
+const std::vector<SweepPhase>& Engine::program(int C, bool single) const {
+  const int d = depth_for(C);
+  return single ? prog_single_d[d] : prog_double_d[d];
+}
+
 int Engine::upload_programs() {
   std::vector<GTask> all;
-  for (std::vector<SweepPhase>* prog : {&prog_double, &prog_single})
-    for (SweepPhase& ph : *prog) {
-      ph.dev_off = all.size();
-      for (const GTask& t : ph.tasks) all.push_back(t);
-    }
+  for (int d = 0; d < 8; ++d)
+    for (std::vector<SweepPhase>* prog : {&prog_double_d[d], &prog_single_d[d]})
+      for (SweepPhase& ph : *prog) {
+        ph.dev_off = all.size();
+        for (const GTask& t : ph.tasks) all.push_back(t);
+      }
   dfree(prog_tasks);
   prog_tasks = nullptr;
   if (all.empty()) return HH_OK;
@@ -874,7 +985,7 @@ static double group_flops(const Engine& E, const SweepPhase& ph, int C) {
 template <typename R>
 static cudaError_t launch_steps_t(Engine& E, const GArrays& arrs, int C, bool single, void* partial_buf,
                                   size_t partial_bytes, bool allow_tick) {
-  const std::vector<SweepPhase>& prog = single ? E.prog_single : E.prog_double;
+  const std::vector<SweepPhase>& prog = E.program(C, single);
   const bool tick_gemm = allow_tick && E.opts.profile;
   for (size_t pi = 0; pi < prog.size();) {
     const SweepPhase& ph = prog[pi];
@@ -904,7 +1015,7 @@ static cudaError_t launch_steps_t(Engine& E, const GArrays& arrs, int C, bool si
 }
 
 double Engine::sweep_flops(int C, bool single) const {
-  const std::vector<SweepPhase>& prog = single ? prog_single : prog_double;
+  const std::vector<SweepPhase>& prog = program(C, single);
   double f = 0;
   for (const SweepPhase& p : prog) {
     if (p.kind == PH_STEP) f += 8.0 * m * m * (double)p.step.ns * C;
@@ -914,7 +1025,7 @@ double Engine::sweep_flops(int C, bool single) const {
 }
 
 double Engine::sweep_bytes(int C, bool single) const {
-  const std::vector<SweepPhase>& prog = single ? prog_single : prog_double;
+  const std::vector<SweepPhase>& prog = program(C, single);
   double b = 0;
   for (const SweepPhase& p : prog) {
     if (p.kind == PH_STEP) b += step_bytes(*this, p.step, C);
@@ -938,6 +1049,10 @@ int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool sin
   // its GEMM steps one by one and so runs eagerly; the others replay a captured graph.
   if (precision == HH_PREC_FP32 && tc_ready && allow_graph && C % 2 == 0 && !tc_tuned.count(C)) {
     const int rc = tune_tc(C, Rin, V, W, partial, partial_bytes);
+    if (rc) return rc;
+  }
+  if (opts.bcr_depth < 0 && allow_graph && !bcr_tuned.count(C)) {
+    const int rc = tune_depth(C, Rin, V, W, partial, partial_bytes);
     if (rc) return rc;
   }
   const bool sampled = opts.profile && ((sweep_calls++ % sample_every() == 0) || sample_next_sweep);
@@ -1005,8 +1120,62 @@ int Engine::sweep_inline(const void* Rin, void* V, void* W, int C, bool single) 
 }
 
 int Engine::ensure_tuned(int C) {
-  if (precision != HH_PREC_FP32 || !tc_ready || C % 2 || tc_tuned.count(C)) return HH_OK;
-  return tune_tc(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
+  if (precision == HH_PREC_FP32 && tc_ready && C % 2 == 0 && !tc_tuned.count(C)) {
+    const int rc = tune_tc(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
+    if (rc) return rc;
+  }
+  if (opts.bcr_depth < 0 && !bcr_tuned.count(C)) return tune_depth(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
+  return HH_OK;
+}
+
+// Autotuner of the cyclic-reduction depth for C columns per strip: every depth whose blocks
+// are stored runs whole sweeps (one warm-up, three timed with CUDA events, on the arrays of the
+// call, whose outputs the real sweep overwrites next) and the fastest is kept.
+int Engine::tune_depth(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes) {
+  std::vector<int> cand = {0};
+  for (int d = 1; d <= bdir.dmax; ++d)
+    if (bdir.iDeep[d] >= 0) cand.push_back(d);
+  if (cand.size() == 1) {
+    bcr_tuned[C] = 0;
+    return HH_OK;
+  }
+  GArrays arrs{};
+  arrs.p[SB_RIN] = const_cast<void*>(Rin);
+  arrs.p[SB_V] = V;
+  arrs.p[SB_W] = W;
+  arrs.p[SB_T0] = w_t0;
+  arrs.p[SB_T1] = w_t1;
+  const bool single = opts.single_sweep != 0;
+  auto sweep = [&]() {
+    return precision == HH_PREC_FP32 ? launch_steps_t<float>(*this, arrs, C, single, partial, partial_bytes, false)
+                                     : launch_steps_t<double>(*this, arrs, C, single, partial, partial_bytes, false);
+  };
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int d : cand) {
+    bcr_tuned[C] = d;
+    if (sweep() != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(a, stream);
+    for (int r = 0; r < 3; ++r) sweep();
+    cudaEventRecord(b, stream);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = d;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  bcr_tuned[C] = best;
+  return check_device_error("cyclic-reduction depth autotune");
 }
 
 // launch helpers used by krylov.cu / api.cu / noalloc.cu

@@ -67,7 +67,10 @@ def test_default_opts(lib):
     (10.0, 32, 4, 0, {}),           # no direction
     (10.0, 32, 4, 16, {}),          # unknown direction bit
     (10.0, 32, 4, 15, {"maxit": 0}),
-    (10.0, 32, 4, 15, {"bcr_depth": 2}),
+    (10.0, 32, 4, 15, {"bcr_depth": 4}),   # R = 8 allows at most 3 levels of cyclic reduction
+    (10.0, 32, 4, 15, {"interface_form": 2}),
+    (10.0, 36, 4, 15, {"bcr_depth": 2}),   # R = 9 is odd: no cyclic reduction
+    (10.0, 32, 4, 15, {"bcr_depth": -2}),
     (10.0, 32, 4, 15, {"gs_passes": 3}),
     (10.0, 32, 4, 15, {"serve_slots": 0}),
     (10.0, 32, 4, 15, {"serve_slots": 257}),

@@ -493,3 +493,95 @@ def test_interface_scans_and_block_column_corrections(precision, k, n, N, double
                 sw = sweep.Sweeper(A, k, n, N, d)
                 for c in range(ncols):
                     assert rel(z1[c], sw.apply(r[c], double)) < bar, (d, c, ncols)
+
+
+BCR_CASES = [(20.0, 32, 4), (30.0, 48, 3), (25.0, 64, 16), (20.0, 36, 6), (12.0, 16, 8)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,n,N", BCR_CASES)
+def test_cyclic_reduction_depths(precision, k, n, N):
+    """Strip solves by block cyclic reduction of every usable depth d (R divisible by 2^d):
+    the double and the single sweep equal the oracle's (banded LU strip solves) and the
+    block-Thomas form (d = 0) up to rounding; fewer dependent steps for d >= 1 when R >= 4.
+    Columns 4 (tensor cores for complex64) and 3 (CUDA cores)."""
+    R = n // N
+    dmax = 0
+    while R % (2 << dmax) == 0:
+        dmax += 1
+    A, *_ = fem.global_system(k, n)
+    bar = 1e-10 if precision == "fp64" else 2e-4
+    for d in range(1, dmax + 1):
+        for ncols in (4, 3):
+            r = hh_inputs.random_vector(A.shape[0], ncols, seed=40 + d + ncols)
+            rr = np.ascontiguousarray(r.ravel())
+            for single in (0, 1):
+                with hh.Handle(k, n, N, precision=precision, bcr_depth=d, single_sweep=single) as hd, \
+                        hh.Handle(k, n, N, precision=precision, bcr_depth=0, single_sweep=single) as h0:
+                    for dd in ("BT", "LR", "TB", "RL"):
+                        zd = hd.apply_preconditioner(dd, rr, ncols).reshape(ncols, -1)
+                        z0 = h0.apply_preconditioner(dd, rr, ncols).reshape(ncols, -1)
+                        assert hd.stats()["bcr_depth"] == d
+                        assert rel(zd, z0) < (1e-11 if precision == "fp64" else 1e-4), (d, dd, ncols, single)
+                        sw = sweep.Sweeper(A, k, n, N, dd)
+                        for c in range(ncols):
+                            assert rel(zd[c], sw.apply(r[c], not single)) < bar, (d, dd, c, single)
+                    if R >= 4:
+                        assert hd.stats()["sweep_steps"] < h0.stats()["sweep_steps"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cyclic_reduction_autotuned_solve(precision):
+    """bcr_depth = -1: every usable depth is stored and the fastest is picked by timing whole
+    sweeps; the solve equals the oracle's (FP64: same iterations, 1e-10; FP32: within the
+    oracle's iterations + 2)."""
+    k, n, N = 30.0, 64, 4
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    ref = P.solve(b, tol=tol)
+    with hh.Handle(k, n, N, precision=precision, bcr_depth=-1) as h:
+        x, res = h.solve(b, tol=tol)
+        st = h.stats()
+    assert 0 <= st["bcr_depth"] <= 4
+    assert res.status == hh.HH_OK
+    if precision == "fp64":
+        assert res.iterations == ref.iterations and rel(x, ref.x) < 1e-10
+    else:
+        assert res.iterations <= ref.iterations + 2 and res.rel_res_explicit < 1.5e-6
+
+
+def test_cyclic_reduction_solve_fp64_matches_oracle():
+    """A whole FP64 solve with depth-3 cyclic reduction (R = 8): the oracle's iteration count
+    and solution to 1e-10."""
+    k, n, N = 20.0, 32, 4
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    ref = P.solve(b, tol=1e-8)
+    with hh.Handle(k, n, N, precision="fp64", bcr_depth=3) as h:
+        x, res = h.solve(b, tol=1e-8)
+    assert res.status == hh.HH_OK and res.iterations == ref.iterations
+    assert rel(x, ref.x) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dirs", ["LR+RL", "LR+RL+BT+TB"])
+def test_single_sweep_combinations_solve(precision, dirs):
+    """Table 1's single-sweep combinations LR+RL and LR+BT+RL+TB (forward sweeps only) as whole
+    solves against the oracle's MPGMRES with the same forward-only preconditioners: FP64 the
+    same iteration count and the solution to 1e-10; complex64 sweeps within the oracle's
+    iterations + 2 at tol 1e-6."""
+    k, n, N = 30.0, 64, 8
+    P = solver.Problem(k, n, N, dirs, double=False)
+    b = P.rhs(hh_inputs.centre_source())
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    ref = P.solve(b, tol=tol)
+    with hh.Handle(k, n, N, dirs, precision=precision, single_sweep=1) as h:
+        x, res = h.solve(b, tol=tol)
+    assert res.status == hh.HH_OK
+    if precision == "fp64":
+        assert res.iterations == ref.iterations
+        assert rel(x, ref.x) < 1e-10
+    else:
+        assert res.iterations <= ref.iterations + 2 and res.rel_res_explicit < 1.5e-6
+        assert rel(x, ref.x) < 1e-4
