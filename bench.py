@@ -253,7 +253,8 @@ def run_gpu(args, ws, rank, local):
     peaks = measured_peaks()
 
     with torch.cuda.stream(stream):
-        h = hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", profile=PROFILE_SAMPLE, stream=stream.cuda_stream)
+        h = hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", profile=PROFILE_SAMPLE, stream=stream.cuda_stream,
+                      bcr_depth=args.bcr_depth)
         setup_ms = h.stats()["setup_ms"]
         b = torch.from_numpy(h.assemble_rhs(src)).to(f"cuda:{local}")
         x = torch.zeros_like(b)
@@ -436,17 +437,21 @@ def run_fp64(w, local):
             "rel_res_explicit": res.rel_res_explicit}
 
 
-def run_serving(nreq: int, rate_hz: float, seed: int = 0) -> dict:
+SERVE_MAXIT = 100  # iteration cap of a served request (the server reserves memory for it)
+
+
+def run_serving(nreq: int, rate_hz, seed: int = 0) -> dict:
     """The mixed-k request stream: nreq requests (k uniform in [50, 400], n = ceil(2.5k/32)*32,
     strips of 32 node lines, one Gaussian each, tol 1e-6) arriving as a Poisson stream of
-    rate_hz, through one hh_server (complex64 sweeps on the tensor cores, 2 slots per
-    problem).  Latency = submission to completion (queueing, setup of an uncached problem and
-    the solve); throughput = requests / (last completion - first arrival)."""
+    rate_hz (None: all at once, which measures the capacity), through one hh_server (complex64
+    sweeps on the tensor cores, 2 slots per problem, iteration cap SERVE_MAXIT).  Latency =
+    submission to completion (queueing, setup of an uncached problem and the solve);
+    throughput = requests / (last completion - first arrival)."""
     import paper_2408_11929_gb300 as hh
-    reqs = hh_inputs.serving_stream(nreq, seed=seed, rate_hz=rate_hz)
+    reqs = hh_inputs.serving_stream(nreq, seed=seed, rate_hz=rate_hz if rate_hz else 1e12)
     xs = [np.zeros((q["n"] + 1) ** 2, dtype=np.complex128) for q in reqs]
     done, tickets = {}, []
-    with hh.Server(precision="fp32", serve_slots=2) as srv:
+    with hh.Server(precision="fp32", serve_slots=2, maxit=SERVE_MAXIT) as srv:
         t0 = time.perf_counter()
         i = 0
         while len(done) < len(reqs):
@@ -465,13 +470,15 @@ def run_serving(nreq: int, rate_hz: float, seed: int = 0) -> dict:
     lat = [done[j][1].t_solve_ms for j in range(len(reqs))]
     t_end = max(done[j][2] for j in range(len(reqs)))
     return {
-        "nreq": nreq, "rate_hz": rate_hz, "seed": seed,
+        "nreq": nreq, "rate_hz": rate_hz if rate_hz else "all at t=0 (capacity)", "seed": seed,
         "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99), "mean_ms": float(np.mean(lat)),
         "solves_per_s": nreq / (t_end - reqs[0]["t_arrive"]),
         "all_ok": all(done[j][0] == hh.HH_OK for j in range(len(reqs))),
         "max_rel_res_explicit": max(done[j][1].rel_res_explicit for j in range(len(reqs))),
         "iterations_mean": float(np.mean([done[j][1].iterations for j in range(len(reqs))])),
         "setups": stats["setups"], "cache_hits": stats["cache_hits"], "evictions": stats["evictions"],
+        "cache_hit_rate": stats["cache_hits"] / max(1, stats["cache_hits"] + stats["setups"]),
+        "maxit": SERVE_MAXIT, "makespan_s": t_end - reqs[0]["t_arrive"],
         "setup_ms_total": stats["setup_ms"], "k_range": [50, 400], "n_range": [128, 1024],
         "kind": "open loop, Poisson arrivals, mixed k; latency includes queueing and the setup of uncached problems"}
 
@@ -561,7 +568,7 @@ def run_sweep_only(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         h = hh.Handle(k, args.n, args.strips, "LR+RL+BT+TB", precision=args.precision, profile=1,
-                      autotune=args.autotune,
+                      autotune=args.autotune, bcr_depth=args.bcr_depth,
                       stream=stream.cuda_stream)
         dofs = (args.n + 1) ** 2
         r = torch.from_numpy(np.ascontiguousarray(hh_inputs.random_vector(dofs, 4, seed=1).ravel())).cuda()
@@ -580,6 +587,7 @@ def run_sweep_only(args):
         h.close()
     ms = st["sweep_ms"] / max(1, st["sweep_launches"])
     print(json.dumps({"mode": "sweep", "n": args.n, "strips": args.strips, "precision": args.precision,
+                      "bcr_depth": st["bcr_depth"], "setup_ms": st["setup_ms"],
                       "sweep_ms": ms, "steps_per_launch": st["sweep_steps"],
                       "us_per_step": ms * 1e3 / st["sweep_steps"],
                       "GBps": st["sweep_bytes"] / max(1, st["sweep_launches"]) / (ms / 1e3) / 1e9,
@@ -600,13 +608,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-right-hand-side batch")
-    ap.add_argument("--serve-nreq", type=int, default=40, help="requests of the mixed-k serving stream (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=4.0, help="Poisson arrival rate of the serving stream (1/s)")
+    ap.add_argument("--serve-nreq", type=int, default=500, help="requests of the mixed-k serving stream (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="--mode serve: Poisson arrival rate (1/s); 0: all at once (capacity)")
     ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "solve1", "candidates"],
                     help="sweep: time hh_apply_preconditioner alone (4 columns) -- the profiling case")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--strips", type=int, default=32)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--bcr-depth", type=int, default=-1,
+                    help="cyclic-reduction depth of the strip solves (-1: autotuned, 0: block Thomas)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="--mode solve1/sweep: hh_opts.autotune (0: the default tile; -(1 + 7 shape + variant): "
                          "one candidate, e.g. -13 = 32 columns, 4 K slices summed in a cluster)")
@@ -679,9 +690,14 @@ def main():
         if not args.no_batch:
             out["batch"] = run_batch()
         if args.serve_nreq > 0:
-            out["serving"] = run_serving(args.serve_nreq, args.serve_rate)
-            out["latency_ms"]["serving_p50"] = out["serving"]["p50_ms"]
-            out["latency_ms"]["serving_p99"] = out["serving"]["p99_ms"]
+            # capacity (every request at t = 0), then Poisson streams at 0.7 and 0.9 of it
+            cap = run_serving(args.serve_nreq, None)
+            runs = {"capacity": cap}
+            for f in (0.7, 0.9):
+                runs[f"poisson_{f:.1f}x_capacity"] = run_serving(args.serve_nreq, f * cap["solves_per_s"])
+            out["serving"] = runs
+            out["latency_ms"]["serving_p50"] = runs["poisson_0.7x_capacity"]["p50_ms"]
+            out["latency_ms"]["serving_p99"] = runs["poisson_0.7x_capacity"]["p99_ms"]
         if not args.no_fp64:
             out["fp64"] = run_fp64(w, local)
             out["fp32_speedup_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["ms_per_step"]

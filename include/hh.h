@@ -114,6 +114,20 @@ typedef struct {
                              ONE grouped step with stored block columns of the strip inverse;
                              0: chains of N-2 and N-1 dependent steps and block-Thomas corrections
                              (2R+1 and R-1 dependent steps) */
+  int persistent;         /* HH_PREC_FP32 with the tensor cores, interface form 1, even column count:
+                             1: the whole sweep (every phase of its program) runs as ONE cooperative
+                             launch of one CTA per SM, grid barriers between the phases, factor and
+                             line tiles streamed by TMA through a ring that runs on from one work item
+                             to the next, two tensor-memory accumulators so that the epilogue of a
+                             tile overlaps the MMAs of the next; 2: the same, reading the complex64
+                             factor store once and splitting it into TF32 hi + lo in shared memory;
+                             0 (default, faster at one right-hand side on this part): one launch per
+                             phase, replayed as a CUDA graph */
+  int gs_first_fp32;      /* HH_PREC_FP32 with two Gram-Schmidt passes: 1 (default): the inner
+                             products of the FIRST pass against the basis in FP32 (their
+                             coefficients are applied in FP64 and the FP64 second pass corrects
+                             them, so H, the orthogonality of V and A Z = V H stay FP64-accurate);
+                             0: both passes in FP64 */
 } hh_opts;
 
 typedef struct {

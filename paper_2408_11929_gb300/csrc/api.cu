@@ -196,7 +196,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
       prog_double_d[d] = build_program(n, N, true, opts.interface_form, bdir, d);
       prog_single_d[d] = build_program(n, N, false, opts.interface_form, bdir, d);
     }
-  if (upload_programs()) return HH_ENOMEM;
+  if (upload_programs() || upload_persistent()) return HH_ENOMEM;
   cudaStreamSynchronize(stream);
 
   cudaEvent_t a, b;
@@ -235,6 +235,8 @@ Engine::~Engine() {
   dfree(factors); dfree(bar); dfree(err);
   dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial); dfree(w_t0); dfree(w_t1);
   dfree(prog_tasks);
+  dfree(pprog_tasks);
+  for (auto& kv : pphase_cache) dfree(kv.second);
   dfree(factors_hi); dfree(factors_lo);
   free_dense_scratch();
   if (own_stream && stream) cudaStreamDestroy(stream);
@@ -430,6 +432,8 @@ void hh_default_opts(hh_opts* o) {
   o->fuse_chains = 1;
   o->overlap_steps = 1;
   o->interface_form = 1;
+  o->persistent = 0;
+  o->gs_first_fp32 = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {

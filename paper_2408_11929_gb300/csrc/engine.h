@@ -42,6 +42,9 @@ std::vector<SweepStep> build_steps(int n, int N, bool double_sweep);
 // (zero outside 0..N-1).  The terms' K ranges are concatenated.  T0 and T1 hold one line.
 struct GTerm {
   int f, arr, line, ds, neg;
+  // optional: x = xbase[bline] + (-1)^neg C(arr[line]), C the identity (cpl = XC_NONE) or the
+  // coupling to the node line below / above (XC_LOWER / XC_UPPER), as in a block-Thomas step
+  int cpl = 0, barr = 0, bline = 0;
 };
 constexpr int GMAX_TERMS = 3;
 struct GTask {
@@ -112,6 +115,7 @@ class Engine {
   void* factors_hi = nullptr;
   void* factors_lo = nullptr;
   CUtensorMap tmap_hi{}, tmap_lo{};
+  CUtensorMap tmap_c{};  // the complex64 store itself, same view (persistent sweep kernel)
   bool tc_ready = false;
   int prepare_tensor_cores();  // sweep.cu
   // Dense complex64 GEMM C = A B (or A (-B)) of m x m blocks (leading dimension ldf) on the
@@ -162,7 +166,7 @@ class Engine {
   std::vector<SweepGraph> sweep_graphs;
   // grid barriers (GRID_BAR_WORDS words each): BAR_SETUP for the pivoted Gauss-Jordan of the
   // strip setup, BAR_CHAIN for the sweep's interface chains
-  enum { BAR_SETUP = 0, BAR_CHAIN = 1, BAR_COUNT = 2 };
+  enum { BAR_SETUP = 0, BAR_CHAIN = 1, BAR_PERSIST = 2, BAR_COUNT = 3 };
   static constexpr size_t BAR_BYTES = (size_t)BAR_COUNT * 64 * sizeof(unsigned);
   unsigned* bar = nullptr;
   int* err = nullptr;       // device error word
@@ -179,6 +183,13 @@ class Engine {
   int tune_depth(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes);
   GTask* prog_tasks = nullptr;
   int upload_programs();
+  // the same programs for the persistent sweep kernel (persist.cu): block-Thomas steps as
+  // grouped tasks, one device task table, device phase tables per (program, columns, shape)
+  std::vector<SweepPhase> pprog_double_d[8], pprog_single_d[8];
+  GTask* pprog_tasks = nullptr;
+  std::map<int64_t, void*> pphase_cache;
+  int upload_persistent();
+  bool no_alloc_call = false;  // inside hh_apply_preconditioner_noalloc
   size_t bytes_allocated = 0;
 
   // statistics

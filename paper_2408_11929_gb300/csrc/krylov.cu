@@ -407,6 +407,81 @@ __global__ void __launch_bounds__(256) gs_dot_kernel(KState S) {
   }
 }
 
+// First-pass inner products <v_a, w_b> in FP32 (FP64 data converted on load): with complex64
+// sweeps the first Gram-Schmidt pass only has to remove most of w's part in the basis; its
+// coefficients c1 (relative error about 1e-6 of |v||w|) are applied by the FP64 update, and the
+// FP64 second pass computes the correction c2 of what remains, so that H = c1 + c2, the new
+// vectors' orthogonality and the relation A Z = V H stay FP64-accurate.  Same grid and
+// partial layout as gs_dot_kernel; per-thread sums of a few terms in FP32, the block sum in FP64.
+template <int TT, int AB>
+__global__ void __launch_bounds__(256) gs_dot32_kernel(KState S, const double2* __restrict__ W) {
+  const int r = blockIdx.y;
+  if (S.done[r]) return;
+  const int nV = S.nV[r];
+  const size_t D = S.D;
+  const size_t chunk = (D + S.GX - 1) / S.GX;
+  const size_t g0 = blockIdx.x * chunk, g1 = min(D, g0 + chunk);
+  const double2* Wr = W + (size_t)r * TT * D;
+  __shared__ double sh[32 * (AB * TT * 2 > 8 ? AB * TT * 2 : 8)];
+  for (int a0 = 0; a0 < nV; a0 += AB) {
+    float ar[AB * TT], ai[AB * TT];
+#pragma unroll
+    for (int q = 0; q < AB * TT; ++q) ar[q] = ai[q] = 0.f;
+    const double2* vp[AB];
+#pragma unroll
+    for (int ab = 0; ab < AB; ++ab) vp[ab] = (a0 + ab < nV) ? S.Vptr[(size_t)r * S.maxV + a0 + ab] : nullptr;
+    for (size_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+      float2 w[TT];
+#pragma unroll
+      for (int b = 0; b < TT; ++b) {
+        const double2 x = Wr[b * D + g];
+        w[b] = make_float2((float)x.x, (float)x.y);
+      }
+#pragma unroll
+      for (int ab = 0; ab < AB; ++ab) {
+        const double2 vd = vp[ab] ? vp[ab][g] : make_double2(0, 0);
+        const float vx = (float)vd.x, vy = (float)vd.y;
+#pragma unroll
+        for (int b = 0; b < TT; ++b) {
+          const int q = ab * TT + b;
+          ar[q] = fmaf(vx, w[b].x, fmaf(vy, w[b].y, ar[q]));
+          ai[q] = fmaf(vx, w[b].y, fmaf(-vy, w[b].x, ai[q]));
+        }
+      }
+    }
+    double acc[AB * TT * 2];
+#pragma unroll
+    for (int q = 0; q < AB * TT; ++q) {
+      acc[2 * q] = ar[q];
+      acc[2 * q + 1] = ai[q];
+    }
+    if constexpr (AB * TT * 2 == 32) {
+      const double sum = block_sum32_scatter(acc, sh);
+      if (threadIdx.x < 32) {
+        const int q = threadIdx.x, ab = q / (TT * 2), b = (q / 2) % TT, part = q & 1;
+        if (a0 + ab < nV) {
+          const size_t p = ((size_t)r * S.maxV + a0 + ab) * TT + b;
+          reinterpret_cast<double*>(&S.Hpart[p * S.GX + blockIdx.x])[part] = sum;
+        }
+      }
+    } else {
+      block_sum<AB * TT * 2>(acc, sh);
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int ab = 0; ab < AB; ++ab) {
+          if (a0 + ab < nV) {
+#pragma unroll
+            for (int b = 0; b < TT; ++b) {
+              const size_t p = ((size_t)r * S.maxV + a0 + ab) * TT + b;
+              S.Hpart[p * S.GX + blockIdx.x] = make_double2(acc[(ab * TT + b) * 2], acc[(ab * TT + b) * 2 + 1]);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // Grid (pairs / 8, slots), one warp per (basis vector, new column) pair: the lanes take every
 // 32nd CTA partial and meet in a fixed shuffle tree (the same order on every run).
 __global__ void gs_reduce_kernel(KState S, int first) {
@@ -1125,7 +1200,10 @@ struct SlotSolver::Impl {
     E.count_launch();
     for (int pass = 0; pass < K.passes; ++pass) {
       if (tick) E.tick_begin(Engine::K_GSDOT);
-      gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K);
+      if (pass == 0 && K.passes >= 2 && E.precision == HH_PREC_FP32 && E.opts.gs_first_fp32)
+        gs_dot32_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K, W);
+      else
+        gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K);
       // one complex multiply-add (8 real flops) per basis element and new column; the basis
       // (16 bytes per element) is read once, the column planes (24 bytes) once per 4 vectors
       if (tick) E.tick_end(Engine::K_GSDOT, nv * D * 16.0 + (double)t * D * 24.0 * nv / 4.0, 8.0 * nv * t * D);

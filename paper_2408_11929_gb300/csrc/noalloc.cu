@@ -114,8 +114,10 @@ int Engine::apply_preconditioner_noalloc(int dcode, int ncols, const double2* r,
   int4 codes = make_int4(dcode, dcode, dcode, dcode);
   launch_pack(*this, tab, scale, ncols, 1, codes, rin);
   const size_t part_bytes = kNoAllocScratchBytes > off_part ? kNoAllocScratchBytes - off_part : 0;
+  no_alloc_call = true;
   rc = run_sweep_untimed(rin, v, w, ncols, single, part_bytes ? s + off_part : nullptr, part_bytes, false, s + off_t0,
                          s + off_t1);
+  no_alloc_call = false;
   if (rc == HH_OK) launch_unpack(*this, v, ncols, 1, codes, z, D);
   cudaError_t e = cudaStreamSynchronize(stream);
   if (rc) return rc;

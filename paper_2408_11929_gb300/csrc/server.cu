@@ -82,20 +82,29 @@ struct hh_server {
   int64_t setups = 0, hits = 0, evictions = 0, completed = 0;
   double setup_ms = 0;
 
-  // Device bytes a handle for this problem holds once warm (the estimate admission uses).
+  // Device bytes a handle for this problem can hold once warm (the estimate admission uses):
+  // its factor store (every block of its sweep form and cyclic-reduction depths, with the
+  // tensor cores' hi and lo copies), sweep workspaces, and per slot the Krylov state of a solve
+  // that runs to the iteration cap opts.maxit (basis and search directions of t columns per
+  // iteration), so that no admitted request can outgrow the budget.
   size_t estimate(const Key& k) const {
     const int n = std::get<1>(k), N = std::get<2>(k);
     const int t = popcount4(std::get<3>(k));
     const size_t m = (size_t)n + 1, R = (size_t)n / N, ldf = (m + 3) & ~(size_t)3;
     const size_t elem = opts.precision == HH_PREC_FP32 ? 8 : 16;
     const size_t copies = (opts.precision == HH_PREC_FP32 && opts.tensor_cores) ? 3 : 1;
-    const size_t factors = copies * (R + 3) * m * ldf * elem;
+    unsigned depths = 0;
+    if (opts.bcr_depth > 0) depths = 1u << opts.bcr_depth;
+    else if (opts.bcr_depth < 0)
+      for (int d = 1; d <= max_bcr_depth((int)R); ++d) depths |= 1u << d;
+    const size_t blocks = (size_t)block_directory((int)R, N, opts.interface_form, depths).total;
+    const size_t factors = copies * blocks * m * ldf * elem;
     const size_t C = (size_t)t * opts.serve_slots;
-    const size_t sweep = 3 * (R + 1) * m * N * C * elem + 8 * m * N * C * elem;
+    const size_t sweep = 3 * (R + 1) * m * N * C * elem + 10 * m * N * C * elem;
     const size_t D = m * m;
-    // per slot: t-column W and its three planes (1.5 t columns), b, staging x, and the basis
-    // block pool of about 30 iterations
-    const size_t krylov = (size_t)opts.serve_slots * D * 8 * (2 * t + 3 * t + 4 + 4 * 30 * t);
+    // per slot: t-column W and its three planes, b, staging x, and 2 t basis / search vectors
+    // per iteration up to the cap
+    const size_t krylov = (size_t)opts.serve_slots * D * 8 * (2 * t + 3 * t + 4 + 4 * (size_t)opts.maxit * t);
     return factors + sweep + krylov + (64u << 20);
   }
 

@@ -171,7 +171,7 @@ BlockDir block_directory(int R, int N, int form, unsigned depths) {
 //     u_p = Dinv r^(l-1)_p - (Dinv L) u_{p-h} - (Dinv U) u_{p+h}   (into V),
 //   the top eliminated line of the strips before the last without the last term.
 static void append_bcr_f1(std::vector<SweepPhase>& prog, int R, int N, int d, const BlockDir& bd) {
-  auto term = [](int f, int arr, int line, int neg) { return GTerm{f, arr, line, 0, neg}; };
+  auto term = [](int f, int arr, int line, int neg) { return GTerm{f, arr, line, 0, neg, 0, 0, 0}; };
   auto task = [](std::initializer_list<GTerm> terms, int out_arr, int out_line, int base_arr, int base_line,
                  int mode, int s0, int ns) {
     GTask t{};
@@ -270,7 +270,7 @@ std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form,
                   int mode, int s0, int ns) {
     GTask t{};
     t.nterm = 1;
-    t.term[0] = GTerm{f, arr, line, ds, neg};
+    t.term[0] = GTerm{f, arr, line, ds, neg, 0, 0, 0};
     t.out_arr = out_arr; t.out_line = out_line;
     t.base_arr = base_arr; t.base_line = base_line;
     t.mode = mode; t.s0 = s0; t.ns = ns;
@@ -982,9 +982,17 @@ static double group_flops(const Engine& E, const SweepPhase& ph, int C) {
 
 // The phases of a sweep program in order: runs of block-Thomas steps, grouped steps (on the
 // tensor cores for complex64 with an even column count) and line copies.
+int run_persistent(Engine& E, const GArrays& arrs, int C, bool single, void* partial_buf, size_t partial_bytes);
+int prepare_persistent(Engine& E, int C, size_t partial_bytes);
+
 template <typename R>
 static cudaError_t launch_steps_t(Engine& E, const GArrays& arrs, int C, bool single, void* partial_buf,
                                   size_t partial_bytes, bool allow_tick) {
+  if (std::is_same<R, float>::value && E.opts.persistent) {
+    const int prc = run_persistent(E, arrs, C, single, partial_buf, partial_bytes);
+    if (prc == HH_OK) return cudaSuccess;
+    if (prc != HH_EINVAL) return cudaErrorLaunchFailure;
+  }
   const std::vector<SweepPhase>& prog = E.program(C, single);
   const bool tick_gemm = allow_tick && E.opts.profile;
   for (size_t pi = 0; pi < prog.size();) {
@@ -1053,6 +1061,10 @@ int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool sin
   }
   if (opts.bcr_depth < 0 && allow_graph && !bcr_tuned.count(C)) {
     const int rc = tune_depth(C, Rin, V, W, partial, partial_bytes);
+    if (rc) return rc;
+  }
+  if (allow_graph) {
+    const int rc = prepare_persistent(*this, C, partial_bytes);
     if (rc) return rc;
   }
   const bool sampled = opts.profile && ((sweep_calls++ % sample_every() == 0) || sample_next_sweep);
@@ -1124,8 +1136,11 @@ int Engine::ensure_tuned(int C) {
     const int rc = tune_tc(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
     if (rc) return rc;
   }
-  if (opts.bcr_depth < 0 && !bcr_tuned.count(C)) return tune_depth(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
-  return HH_OK;
+  if (opts.bcr_depth < 0 && !bcr_tuned.count(C)) {
+    const int rc = tune_depth(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
+    if (rc) return rc;
+  }
+  return prepare_persistent(*this, C, w_partial_bytes);
 }
 
 // Autotuner of the cyclic-reduction depth for C columns per strip: every depth whose blocks
@@ -1218,6 +1233,7 @@ __global__ void tf32_split_kernel(const float* __restrict__ F, float* __restrict
 }
 
 void set_tc_group_attributes();
+void set_persist_attributes();
 
 int Engine::load_encoder() {
   if (precision != HH_PREC_FP32 || !opts.tensor_cores) return HH_OK;
@@ -1244,6 +1260,7 @@ int Engine::load_encoder() {
   cudaFuncSetAttribute((const void*)tc_line_gemm_kernel<tc::Huge, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)tc::Huge::SMEM);
   set_tc_group_attributes();
+  set_persist_attributes();
   return HH_OK;
 }
 
@@ -1392,8 +1409,10 @@ int Engine::prepare_tensor_cores() {
   const cuuint64_t strides[2] = {(cuuint64_t)ldf * 2 * sizeof(float), (cuuint64_t)m * ldf * 2 * sizeof(float)};
   const cuuint32_t box[3] = {32, (cuuint32_t)tc::BM, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  for (int h = 0; h < 2; ++h) {
-    CUresult r = encode(h ? &tmap_lo : &tmap_hi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h ? factors_lo : factors_hi, dims,
+  for (int h = 0; h < 3; ++h) {
+    CUtensorMap* mp = h == 2 ? &tmap_c : (h ? &tmap_lo : &tmap_hi);
+    void* src = h == 2 ? factors : (h ? factors_lo : factors_hi);
+    CUresult r = encode(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, src, dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {

@@ -585,3 +585,55 @@ def test_single_sweep_combinations_solve(precision, dirs):
     else:
         assert res.iterations <= ref.iterations + 2 and res.rel_res_explicit < 1.5e-6
         assert rel(x, ref.x) < 1e-4
+
+
+@pytest.mark.parametrize("k,n,N,ncols", [(20.0, 32, 4, 4), (40.0, 256, 16, 4), (60.0, 256, 8, 8), (30.0, 96, 3, 2)])
+@pytest.mark.parametrize("bcr", [0, 2])
+@pytest.mark.parametrize("form", [1, 2])
+def test_persistent_sweep_equals_phase_launches(k, n, N, ncols, bcr, form):
+    """The whole sweep as one persistent cooperative launch (every phase of the program, grid
+    barriers between them, K split through an L2 buffer where a phase has few tiles) equals
+    the same program launched phase by phase, and the oracle's sweep, for the double and the
+    single sweep."""
+    R = n // N
+    if R % (1 << bcr):
+        pytest.skip("depth needs R divisible by 2^d")
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], ncols, seed=50 + ncols)
+    rr = np.ascontiguousarray(r.ravel())
+    for single in (0, 1):
+        with hh.Handle(k, n, N, precision="fp32", bcr_depth=bcr, single_sweep=single, persistent=form) as hp, \
+                hh.Handle(k, n, N, precision="fp32", bcr_depth=bcr, single_sweep=single, persistent=0) as hl:
+            hp.apply_preconditioner("BT", rr, ncols)  # tuning runs outside the counted sweeps
+            hl.apply_preconditioner("BT", rr, ncols)
+            hp.reset_stats()
+            hl.reset_stats()
+            for d in sweep.DIRECTIONS:
+                zp = hp.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                zl = hl.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                assert rel(zp, zl) < 1e-5, (d, single)
+                sw = sweep.Sweeper(A, k, n, N, d)
+                for c in range(ncols):
+                    assert rel(zp[c], sw.apply(r[c], not single)) < 2e-4, (d, c, single)
+            # one launch per sweep besides the column tables, pack and unpack (graph replays count
+            # their kernels); the phase-by-phase form launches every phase
+            lp, ll = hp.stats()["kernel_launches"], hl.stats()["kernel_launches"]
+            assert lp <= 4 * 4, lp
+            assert ll > lp
+
+
+def test_fp32_first_gram_schmidt_pass():
+    """With complex64 sweeps the first Gram-Schmidt pass takes its inner products in FP32 and
+    the FP64 second pass corrects them: the same iterations as both passes in FP64, the same
+    solution to rounding, and the explicit residual on the implicit one (the Arnoldi relation
+    stays FP64-accurate)."""
+    k, n, N = 60.0, 128, 8
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    with hh.Handle(k, n, N, precision="fp32") as h1, hh.Handle(k, n, N, precision="fp32", gs_first_fp32=0) as h0:
+        x1, r1 = h1.solve(b, tol=1e-8)
+        x0, r0 = h0.solve(b, tol=1e-8)
+    assert r1.status == hh.HH_OK and r0.status == hh.HH_OK
+    assert abs(r1.iterations - r0.iterations) <= 1
+    assert rel(x1, x0) < 1e-6
+    assert r1.rel_res_explicit < 2 * max(r1.rel_res_implicit, 1e-10)
