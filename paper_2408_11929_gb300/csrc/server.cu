@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "../../include/hh.h"
+#include "engine.h"
 
 namespace hh {
 void set_error(const std::string& msg);
@@ -96,8 +97,8 @@ struct hh_server {
     unsigned depths = 0;
     if (opts.bcr_depth > 0) depths = 1u << opts.bcr_depth;
     else if (opts.bcr_depth < 0)
-      for (int d = 1; d <= max_bcr_depth((int)R); ++d) depths |= 1u << d;
-    const size_t blocks = (size_t)block_directory((int)R, N, opts.interface_form, depths).total;
+      for (int d = 1; d <= hh::max_bcr_depth((int)R); ++d) depths |= 1u << d;
+    const size_t blocks = (size_t)hh::block_directory((int)R, N, opts.interface_form, depths).total;
     const size_t factors = copies * blocks * m * ldf * elem;
     const size_t C = (size_t)t * opts.serve_slots;
     const size_t sweep = 3 * (R + 1) * m * N * C * elem + 10 * m * N * C * elem;
