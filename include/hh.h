@@ -55,12 +55,16 @@ typedef enum {
 
 /* direction bits (Section 4 vocabulary: the direction of the FORWARD pass) */
 enum { HH_DIR_LR = 1, HH_DIR_RL = 2, HH_DIR_BT = 4, HH_DIR_TB = 8 };
-enum { HH_PREC_FP64 = 0, HH_PREC_FP32 = 1 };                 /* precision of factors + sweeps */
+enum { HH_PREC_FP64 = 0, HH_PREC_FP32 = 1, HH_PREC_BF16 = 2 };  /* precision of factors + sweeps */
 enum { HH_SCHEME_AUTO = 0, HH_SCHEME_CROSS = 1, HH_SCHEME_SUM = 2 };
 
 typedef struct {
   int precision;          /* HH_PREC_FP64 (default) or HH_PREC_FP32: complex64 strip factors and
-                             sweeps; the global residual, Gram-Schmidt and Hessenberg stay FP64 */
+                             sweeps; HH_PREC_BF16: complex64 setup and sweep lines, but the factors
+                             stored in bf16 and every sweep product ONE bf16 tensor-core MMA per K step
+                             with FP32 accumulation (a cheaper, less accurate preconditioner: needs the
+                             tensor cores and interface_form 1; odd column counts take the complex64
+                             path); the global residual, Gram-Schmidt and Hessenberg stay FP64 */
   int scheme;             /* HH_SCHEME_AUTO: t=2 cross, t>2 sum */
   int single_sweep;       /* 1: forward sweeps only (LR, RL, BT, TB of Section 4) */
   int maxit;              /* iteration limit (default 200) */

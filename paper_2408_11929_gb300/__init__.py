@@ -21,7 +21,7 @@ HH_OK, HH_EINVAL, HH_ENOMEM, HH_ENOCONV, HH_EBREAKDOWN, HH_ENAN, HH_ETIMEOUT, HH
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOCONV", "EBREAKDOWN", "ENAN", "ETIMEOUT", "EPENDING", "ECUDA"]
 HH_DIR_LR, HH_DIR_RL, HH_DIR_BT, HH_DIR_TB = 1, 2, 4, 8
 DIR_BITS = {"LR": HH_DIR_LR, "RL": HH_DIR_RL, "BT": HH_DIR_BT, "TB": HH_DIR_TB}
-HH_PREC_FP64, HH_PREC_FP32 = 0, 1
+HH_PREC_FP64, HH_PREC_FP32, HH_PREC_BF16 = 0, 1, 2
 HH_SCHEME_AUTO, HH_SCHEME_CROSS, HH_SCHEME_SUM = 0, 1, 2
 
 
@@ -139,7 +139,8 @@ def default_opts(**kw) -> hh_opts:
     load().hh_default_opts(ctypes.byref(o))
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
-            v = HH_PREC_FP32 if v.lower() in ("fp32", "c64", "float") else HH_PREC_FP64
+            v = (HH_PREC_FP32 if v.lower() in ("fp32", "c64", "float")
+                 else HH_PREC_BF16 if v.lower() == "bf16" else HH_PREC_FP64)
         setattr(o, k, v)
     return o
 

@@ -128,7 +128,10 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   if (strips < 1 || n_ % strips != 0) return (set_error("n must be a multiple of strips"), HH_EINVAL);
   if (n_ / strips < 2) return (set_error("each strip needs at least two node lines (n / strips >= 2)"), HH_EINVAL);
   if ((dirs & 15u) == 0 || (dirs & ~15u)) return (set_error("dirs must be a non-empty subset of HH_DIR_*"), HH_EINVAL);
-  if (opts.precision != HH_PREC_FP32 && opts.precision != HH_PREC_FP64) return (set_error("bad precision"), HH_EINVAL);
+  if (opts.precision != HH_PREC_FP32 && opts.precision != HH_PREC_FP64 && opts.precision != HH_PREC_BF16)
+    return (set_error("bad precision"), HH_EINVAL);
+  if (opts.precision == HH_PREC_BF16 && (!opts.tensor_cores || opts.interface_form != 1))
+    return (set_error("HH_PREC_BF16 needs the tensor cores and interface_form 1"), HH_EINVAL);
   if (opts.maxit < 1 || opts.maxit > 2000) return (set_error("maxit must be in [1, 2000]"), HH_EINVAL);
   if (opts.bcr_depth < -1 || (opts.bcr_depth > 0 && (n_ % strips != 0 || opts.bcr_depth > max_bcr_depth(n_ / strips))))
     return (set_error("bcr_depth must be -1 (autotune), 0 (block Thomas) or d >= 1 with n / strips divisible by 2^d"),
@@ -138,7 +141,9 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   if (opts.interface_form != 0 && opts.interface_form != 1) return (set_error("interface_form must be 0 or 1"), HH_EINVAL);
   if (opts.timeout_cycles <= 0) opts.timeout_cycles = 4000000000LL;
   k = k_; n = n_; N = strips; m = n + 1; R = n / N;
-  precision = opts.precision;
+  // bf16 sweeps: complex64 everywhere but in the products of the sweep (lowp.cu)
+  lowp = opts.precision == HH_PREC_BF16;
+  precision = lowp ? HH_PREC_FP32 : opts.precision;
   ldf = (m + 3) & ~3;
   coef.init(k, n);
   {
@@ -206,6 +211,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
   int rc = load_encoder();
   if (rc == HH_OK) rc = factor();
   if (rc == HH_OK) rc = prepare_tensor_cores();
+  if (rc == HH_OK) rc = prepare_lowp();
   free_dense_scratch();
   cudaEventRecord(b, stream);
   cudaEventSynchronize(b);
@@ -237,7 +243,7 @@ Engine::~Engine() {
   dfree(prog_tasks);
   dfree(pprog_tasks);
   for (auto& kv : pphase_cache) dfree(kv.second);
-  dfree(factors_hi); dfree(factors_lo);
+  dfree(factors_hi); dfree(factors_lo); dfree(factors_bf16);
   free_dense_scratch();
   if (own_stream && stream) cudaStreamDestroy(stream);
 }

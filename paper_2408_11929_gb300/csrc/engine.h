@@ -190,6 +190,11 @@ class Engine {
   std::map<int64_t, void*> pphase_cache;
   int upload_persistent();
   bool no_alloc_call = false;  // inside hh_apply_preconditioner_noalloc
+  // HH_PREC_BF16 (lowp.cu): complex64 sweep lines and setup, bf16 factor store for the products
+  bool lowp = false;
+  void* factors_bf16 = nullptr;
+  CUtensorMap tmap_bf16{};
+  int prepare_lowp();
   size_t bytes_allocated = 0;
 
   // statistics

@@ -92,8 +92,8 @@ struct hh_server {
     const int n = std::get<1>(k), N = std::get<2>(k);
     const int t = popcount4(std::get<3>(k));
     const size_t m = (size_t)n + 1, R = (size_t)n / N, ldf = (m + 3) & ~(size_t)3;
-    const size_t elem = opts.precision == HH_PREC_FP32 ? 8 : 16;
-    const size_t copies = (opts.precision == HH_PREC_FP32 && opts.tensor_cores) ? 3 : 1;
+    const size_t elem = opts.precision != HH_PREC_FP64 ? 8 : 16;
+    const size_t copies = (opts.precision != HH_PREC_FP64 && opts.tensor_cores) ? 4 : 1;
     unsigned depths = 0;
     if (opts.bcr_depth > 0) depths = 1u << opts.bcr_depth;
     else if (opts.bcr_depth < 0)

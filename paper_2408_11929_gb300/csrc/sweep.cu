@@ -985,9 +985,16 @@ static double group_flops(const Engine& E, const SweepPhase& ph, int C) {
 int run_persistent(Engine& E, const GArrays& arrs, int C, bool single, void* partial_buf, size_t partial_bytes);
 int prepare_persistent(Engine& E, int C, size_t partial_bytes);
 
+int run_lowp(Engine& E, const GArrays& arrs, int C, bool single);
+
 template <typename R>
 static cudaError_t launch_steps_t(Engine& E, const GArrays& arrs, int C, bool single, void* partial_buf,
                                   size_t partial_bytes, bool allow_tick) {
+  if (std::is_same<R, float>::value && E.lowp) {
+    const int lrc = run_lowp(E, arrs, C, single);
+    if (lrc == HH_OK) return cudaSuccess;
+    if (lrc != HH_EINVAL) return cudaErrorLaunchFailure;
+  }
   if (std::is_same<R, float>::value && E.opts.persistent) {
     const int prc = run_persistent(E, arrs, C, single, partial_buf, partial_bytes);
     if (prc == HH_OK) return cudaSuccess;
@@ -1234,6 +1241,7 @@ __global__ void tf32_split_kernel(const float* __restrict__ F, float* __restrict
 
 void set_tc_group_attributes();
 void set_persist_attributes();
+void set_lowp_attributes();
 
 int Engine::load_encoder() {
   if (precision != HH_PREC_FP32 || !opts.tensor_cores) return HH_OK;
@@ -1261,6 +1269,7 @@ int Engine::load_encoder() {
                        (int)tc::Huge::SMEM);
   set_tc_group_attributes();
   set_persist_attributes();
+  set_lowp_attributes();
   return HH_OK;
 }
 

@@ -637,3 +637,45 @@ def test_fp32_first_gram_schmidt_pass():
     assert abs(r1.iterations - r0.iterations) <= 1
     assert rel(x1, x0) < 1e-6
     assert r1.rel_res_explicit < 2 * max(r1.rel_res_implicit, 1e-10)
+
+
+BF16_SWEEP_BAR = 3e-2
+
+
+@pytest.mark.parametrize("k,n,N", [(20.0, 32, 4), (40.0, 256, 16), (30.0, 96, 3)])
+@pytest.mark.parametrize("bcr", [0, 2])
+def test_bf16_sweeps(k, n, N, bcr):
+    """HH_PREC_BF16 (Section 5's lower-precision subsolves): the factors in bf16 and one bf16
+    tensor-core product per K step with FP32 accumulation.  Every product rounds its factor
+    entries and line values to 8 significant bits (relative 2^-9); the sweep stays within a few
+    per cent of the oracle's (banded LU in FP64), for the double and single sweeps, 4 columns."""
+    R = n // N
+    if R % (1 << bcr):
+        pytest.skip("depth needs R divisible by 2^d")
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], 4, seed=60)
+    rr = np.ascontiguousarray(r.ravel())
+    for single in (0, 1):
+        with hh.Handle(k, n, N, precision="bf16", bcr_depth=bcr, single_sweep=single) as h:
+            for d in sweep.DIRECTIONS:
+                z = h.apply_preconditioner(d, rr, 4).reshape(4, -1)
+                sw = sweep.Sweeper(A, k, n, N, d)
+                errs = [rel(z[c], sw.apply(r[c], not single)) for c in range(4)]
+                assert max(errs) < BF16_SWEEP_BAR, (d, single, errs)
+                assert max(errs) > 1e-5  # the products really are bf16
+
+
+@pytest.mark.parametrize("k,n,N", [(60.0, 128, 8), (100.0, 256, 16)])
+def test_bf16_solve_converges(k, n, N):
+    """Flexible MPGMRES with bf16 sweeps reaches tol 1e-6 in explicit residual (the Krylov side is
+    FP64), within a few iterations of the oracle's FP64 preconditioners, and the solution
+    agrees with the oracle's to the tolerance's level."""
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    ref = P.solve(b, tol=1e-6)
+    with hh.Handle(k, n, N, precision="bf16") as h:
+        x, res = h.solve(b, tol=1e-6)
+    assert res.status == hh.HH_OK
+    assert res.rel_res_explicit < 1.5e-6
+    assert res.iterations <= ref.iterations + 6, (res.iterations, ref.iterations)
+    assert rel(x, ref.x) < 1e-4
