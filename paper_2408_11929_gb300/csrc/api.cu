@@ -244,6 +244,7 @@ Engine::~Engine() {
   dfree(pprog_tasks);
   for (auto& kv : pphase_cache) dfree(kv.second);
   dfree(factors_hi); dfree(factors_lo); dfree(factors_bf16);
+  dfree(stage_buf[0]); dfree(stage_buf[1]);
   free_dense_scratch();
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
@@ -258,23 +259,42 @@ static bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Stages a caller buffer on the device when it lives in host memory.
+// Stages a caller buffer on the device when it lives in host memory, in one of the handle's two
+// staging buffers (slot 0 for an input, 1 for an output; grown on demand, kept for later calls,
+// so that a call with host buffers allocates nothing once warm).  The handle's staging lock is
+// held while the buffer is in use: calls on one handle from several threads take turns.
 struct Staged {
   Engine* E;
   const void* user;
   void* dev = nullptr;
   size_t bytes;
+  int slot;
   bool host;
-  Staged(Engine* e, const void* u, size_t b) : E(e), user(u), bytes(b) { host = !is_device_ptr(u); }
+  std::unique_lock<std::recursive_mutex> lk;
+  Staged(Engine* e, const void* u, size_t b, int s) : E(e), user(u), bytes(b), slot(s) {
+    host = !is_device_ptr(u);
+    if (host) lk = std::unique_lock<std::recursive_mutex>(E->stage_mu);
+  }
+  int ensure() {
+    if (E->stage_cap[slot] < bytes) {
+      E->dfree(E->stage_buf[slot]);
+      E->stage_buf[slot] = nullptr;
+      E->stage_cap[slot] = 0;
+      if (E->dmalloc(&E->stage_buf[slot], bytes)) return HH_ENOMEM;
+      E->stage_cap[slot] = bytes;
+    }
+    dev = E->stage_buf[slot];
+    return HH_OK;
+  }
   int in() {
     if (!host) { dev = const_cast<void*>(user); return HH_OK; }
-    if (E->dmalloc(&dev, bytes)) return HH_ENOMEM;
+    if (ensure()) return HH_ENOMEM;
     cudaMemcpyAsync(dev, user, bytes, cudaMemcpyHostToDevice, E->stream);
     return HH_OK;
   }
   int alloc_out() {
     if (!host) { dev = const_cast<void*>(user); return HH_OK; }
-    return E->dmalloc(&dev, bytes);
+    return ensure();
   }
   int out() {
     if (!host) return HH_OK;
@@ -283,10 +303,7 @@ struct Staged {
     return e == cudaSuccess ? HH_OK : HH_ECUDA;
   }
   ~Staged() {
-    if (host && dev) {
-      cudaStreamSynchronize(E->stream);
-      E->dfree(dev);
-    }
+    if (host) cudaStreamSynchronize(E->stream);
   }
 };
 
@@ -399,7 +416,7 @@ static int solve_common(hh_handle* h, int nrhs, const double* rhs, double* x, do
   cudaSetDevice(E.device);
   const size_t bytes = (size_t)nrhs * E.m * E.m * sizeof(double2);
   auto t0 = std::chrono::steady_clock::now();
-  Staged sb(&E, rhs, bytes), sx(&E, x, bytes);
+  Staged sb(&E, rhs, bytes, 0), sx(&E, x, bytes, 1);
   if (sb.in() || sx.alloc_out()) return HH_ENOMEM;
   std::vector<hh_result> tmp(nrhs);
   int rc = E.solve_batch_dev(nrhs, (const double2*)sb.dev, (double2*)sx.dev, tol, tmp.data());
@@ -471,7 +488,7 @@ hh_status hh_assemble_rhs(hh_handle* h, int nsrc, const double* src, double* rhs
   Engine& E = *h->E;
   std::lock_guard<std::mutex> lk(E.solve_mu);
   cudaSetDevice(E.device);
-  Staged so(&E, rhs, (size_t)E.m * E.m * sizeof(double2));
+  Staged so(&E, rhs, (size_t)E.m * E.m * sizeof(double2), 1);
   if (so.alloc_out()) return HH_ENOMEM;
   int rc = E.assemble_rhs(nsrc, src, (double2*)so.dev);
   if (rc == HH_OK && so.out()) rc = HH_ECUDA;
@@ -484,7 +501,7 @@ hh_status hh_apply_operator(hh_handle* h, int ncols, const double* x, double* y)
   std::lock_guard<std::mutex> lk(E.solve_mu);
   cudaSetDevice(E.device);
   const size_t bytes = (size_t)ncols * E.m * E.m * sizeof(double2);
-  Staged sx(&E, x, bytes), sy(&E, y, bytes);
+  Staged sx(&E, x, bytes, 0), sy(&E, y, bytes, 1);
   if (sx.in() || sy.alloc_out()) return HH_ENOMEM;
   int rc = E.apply_operator(ncols, (const double2*)sx.dev, (double2*)sy.dev);
   if (rc == HH_OK && sy.out()) rc = HH_ECUDA;
@@ -505,7 +522,7 @@ hh_status hh_apply_preconditioner(hh_handle* h, uint32_t dir, int ncols, const d
   std::lock_guard<std::mutex> lk(E.solve_mu);
   cudaSetDevice(E.device);
   const size_t bytes = (size_t)ncols * E.m * E.m * sizeof(double2);
-  Staged sr(&E, r, bytes), sz(&E, z, bytes);
+  Staged sr(&E, r, bytes, 0), sz(&E, z, bytes, 1);
   if (sr.in() || sz.alloc_out()) return HH_ENOMEM;
   int rc = E.apply_preconditioner_dev(code, ncols, (const double2*)sr.dev, (double2*)sz.dev, E.opts.single_sweep != 0);
   if (rc == HH_OK && sz.out()) rc = HH_ECUDA;

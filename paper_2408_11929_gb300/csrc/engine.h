@@ -190,6 +190,10 @@ class Engine {
   std::map<int64_t, void*> pphase_cache;
   int upload_persistent();
   bool no_alloc_call = false;  // inside hh_apply_preconditioner_noalloc
+  // device staging of host buffers passed to the C ABI (api.cu), grown on demand and kept
+  std::recursive_mutex stage_mu;
+  void* stage_buf[2] = {nullptr, nullptr};
+  size_t stage_cap[2] = {0, 0};
   // HH_PREC_BF16 (lowp.cu): complex64 sweep lines and setup, bf16 factor store for the products
   bool lowp = false;
   void* factors_bf16 = nullptr;
