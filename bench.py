@@ -676,7 +676,8 @@ def main():
             torch.cuda.synchronize()
             st = h.stats()
         print(json.dumps({"mode": "solve1", "iterations": res.iterations, "status": hh.STATUS_NAMES[res.status],
-                          "rel_res_explicit": res.rel_res_explicit, "kernel_launches": st["kernel_launches"]}),
+                          "rel_res_explicit": res.rel_res_explicit, "kernel_launches": st["kernel_launches"],
+                          "bcr_depth": st["bcr_depth"], "sweep_steps": st["sweep_steps"]}),
               flush=True)
         return
     if args.mode == "serve":

@@ -132,6 +132,10 @@ typedef struct {
                              coefficients are applied in FP64 and the FP64 second pass corrects
                              them, so H, the orthogonality of V and A Z = V H stay FP64-accurate);
                              0: both passes in FP64 */
+  int gs_tensor;          /* 1 (default): the inner products and updates of Gram-Schmidt against the
+                             basis run on the tensor cores as exact integer products of 7-bit slices
+                             of the FP64 data (FP64-accurate; about 64 more bytes of device memory
+                             per node for every basis vector); 0: on the FP64 pipe */
 } hh_opts;
 
 typedef struct {

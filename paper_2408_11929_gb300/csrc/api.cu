@@ -137,6 +137,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
     return (set_error("bcr_depth must be -1 (autotune), 0 (block Thomas) or d >= 1 with n / strips divisible by 2^d"),
             HH_EINVAL);
   if (opts.gs_passes != 1 && opts.gs_passes != 2) return (set_error("gs_passes must be 1 or 2"), HH_EINVAL);
+  if (opts.gs_tensor != 0 && opts.gs_tensor != 1) return (set_error("gs_tensor must be 0 or 1"), HH_EINVAL);
   if (opts.serve_slots < 1 || opts.serve_slots > 256) return (set_error("serve_slots must be in 1..256"), HH_EINVAL);
   if (opts.interface_form != 0 && opts.interface_form != 1) return (set_error("interface_form must be 0 or 1"), HH_EINVAL);
   if (opts.timeout_cycles <= 0) opts.timeout_cycles = 4000000000LL;
@@ -457,6 +458,7 @@ void hh_default_opts(hh_opts* o) {
   o->interface_form = 1;
   o->persistent = 0;
   o->gs_first_fp32 = 1;
+  o->gs_tensor = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {

@@ -20,35 +20,22 @@
 
 #include "common.cuh"
 #include "engine.h"
+#include "kstate.h"
 
 namespace hh {
 
 void launch_pack(Engine& E, const double2* const* srcptr, const double* scale, int C, int t, int4 codes, void* X);
 void launch_unpack(Engine& E, const void* X, int C, int t, int4 codes, double2* dst, size_t stride);
-
-struct KState {
-  int nrhs, t, D, maxit, maxV, maxZ, GX, GQ, scheme, passes;  // nrhs = number of slots
-  double eta;
-  double* tolv;            // per slot tolerance
-  double2** Zcur;          // per slot: this iteration's Z block (t columns)
-  double2** Vcur;          // per slot: this iteration's block of new basis vectors
-  int* adm;                // per slot: 1 = being admitted now (start kernels)
-  int* fin;                // per slot: 1 = being finalised now (solution kernels)
-  double2** xout;          // per slot: where its solution goes
-  double2* bdev;           // per slot right-hand side (slots x D)
-  double* beta;
-  int *done, *status, *nV, *nZ, *iters, *nacc, *amap;
-  double *rho, *nu, *cs, *hist, *npart;
-  double* azpart;          // per slot, new column j, CTA c of gs_wprep_kernel: its part of ||A z_j||^2
-  double2 **Vptr, **Zptr;
-  double2 *Hacc, *Hthis, *Hpart, *Rnew, *sn, *g, *Rrot, *y, *qpart, *sbuf, *V0;
-  const double2** srcptr;
-  double* scale;
-  double* res_exp;
-  // per slot, new column b, plane q: (Re w, Im w - Re w, Re w + Im w) of the new columns, the
-  // operand of the inner products in Gauss's three-multiplication form (slots x t x 3 x D)
-  double* Wp;
-};
+// tensor-core Gram-Schmidt (gs_tc.cu)
+cudaError_t gst_set_attributes(int t);
+void gst_slice_basis(Engine& E, const KState& K, int S, int mode);
+void gst_pass_dot(Engine& E, const KState& K, int S, const double2* W, bool first);
+void gst_pass_update(Engine& E, const KState& K, int S, double2* W);
+int gst_dot_ctas(const Engine& E, const KState& K, int S);
+size_t gst_vector_bytes(size_t Dp);
+size_t gst_wimage_bytes(size_t Dp, int t);
+size_t gst_cimage_bytes(int maxV, int t);
+int gst_nu_rows(int t);
 
 // ------------------------------------------------------------------ reductions
 template <int NV>
@@ -258,6 +245,11 @@ __global__ void start_kernel(KState S) {
     S.rho[r] = beta;
     S.g[(size_t)r * (S.maxZ + 1)] = make_double2(beta, 0);
     S.Vptr[(size_t)r * S.maxV] = S.V0 + (size_t)r * S.D;
+    if (S.gst) {
+      S.VSptr[(size_t)r * S.maxV] = S.V0S + (size_t)r * 64 * S.Dp;
+      S.vnew0[r] = 0;
+      S.vnew1[r] = 1;
+    }
     for (int d = 0; d < S.t; ++d) {
       S.srcptr[r * S.t + d] = S.V0 + (size_t)r * S.D;
       S.scale[r * S.t + d] = 1.0;
@@ -484,7 +476,7 @@ __global__ void __launch_bounds__(256) gs_dot32_kernel(KState S, const double2* 
 
 // Grid (pairs / 8, slots), one warp per (basis vector, new column) pair: the lanes take every
 // 32nd CTA partial and meet in a fixed shuffle tree (the same order on every run).
-__global__ void gs_reduce_kernel(KState S, int first) {
+__global__ void gs_reduce_kernel(KState S, int first, int gx) {
   const int r = blockIdx.y;
   if (S.done[r]) return;
   const int cnt = S.nV[r] * S.t;
@@ -492,7 +484,7 @@ __global__ void gs_reduce_kernel(KState S, int first) {
   if (p >= cnt) return;
   const size_t base = ((size_t)r * S.maxV * S.t + p);
   double2 s = make_double2(0, 0);
-  for (int q = lane; q < S.GX; q += 32) s = cadd(s, S.Hpart[base * S.GX + q]);
+  for (int q = lane; q < gx; q += 32) s = cadd(s, S.Hpart[base * S.GX + q]);
 #pragma unroll
   for (int o = 16; o; o >>= 1) s = cadd(s, shfl_xor(s, o));
   if (lane == 0) {
@@ -799,6 +791,9 @@ __device__ void givens(double2 a, double2 b, double& c, double2& s) {
 // one per element); lane 0 then applies the rotations in order, which is inherently sequential.
 __global__ void hess_kernel(KState S, int stage) {
   const int r = blockIdx.x, lane = threadIdx.x;
+  // the basis vectors this step adds, for the slicing of the tensor-core Gram-Schmidt: none
+  // unless the step ends normally below
+  if (S.gst && lane == 0) S.vnew1[r] = S.vnew0[r];
   if (S.done[r]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* col = reinterpret_cast<double2*>(smem_raw);  // maxZ + 2
@@ -861,7 +856,14 @@ __global__ void hess_kernel(KState S, int stage) {
     __syncwarp();
     nZ = c + 1;
   }
-  for (int q = lane; q < nacc; q += blockDim.x) S.Vptr[(size_t)r * S.maxV + nold + q] = S.Vcur[r] + (size_t)q * D;
+  for (int q = lane; q < nacc; q += blockDim.x) {
+    S.Vptr[(size_t)r * S.maxV + nold + q] = S.Vcur[r] + (size_t)q * D;
+    if (S.gst) S.VSptr[(size_t)r * S.maxV + nold + q] = S.VScur[r] + (size_t)q * 64 * S.Dp;
+  }
+  if (S.gst && lane == 0) {
+    S.vnew0[r] = nold;
+    S.vnew1[r] = nold + nacc;
+  }
   __syncwarp();
   if (lane != 0) return;
   S.nV[r] = nold + nacc;
@@ -1043,9 +1045,12 @@ struct SlotSolver::Impl {
     double2* xdev = nullptr;  // where the device solution goes
     double* xuser = nullptr;  // caller buffer (host) or nullptr
     std::vector<void*> blocks;
+    std::vector<void*> sblocks;  // slice images of this slot's basis blocks (tensor-core Gram-Schmidt)
   };
   std::vector<Slot> slots;
   std::vector<void*> pool;
+  std::vector<void*> spool;  // slice-image blocks (t basis vectors each)
+  unsigned char** h_vscur = nullptr;
   int4 codes{};
 
   explicit Impl(Engine& e) : E(e) {}
@@ -1054,8 +1059,11 @@ struct SlotSolver::Impl {
     for (auto& g : step_graphs) cudaGraphExecDestroy(g.exec);
     for (void* p : owned) E.dfree(p);
     for (void* p : pool) E.dfree(p);
-    for (auto& sl : slots)
+    for (void* p : spool) E.dfree(p);
+    for (auto& sl : slots) {
       for (void* p : sl.blocks) E.dfree(p);
+      for (void* p : sl.sblocks) E.dfree(p);
+    }
     for (void* p : pinned) cudaFreeHost(p);
   }
   template <typename T_> T_* dev(size_t count) {
@@ -1079,6 +1087,17 @@ struct SlotSolver::Impl {
     }
     void* p = nullptr;
     if (E.dmalloc(&p, (size_t)t * D * sizeof(double2))) return nullptr;
+    return p;
+  }
+
+  void* sblock() {
+    if (!spool.empty()) {
+      void* p = spool.back();
+      spool.pop_back();
+      return p;
+    }
+    void* p = nullptr;
+    if (E.dmalloc(&p, (size_t)t * gst_vector_bytes(K.Dp))) return nullptr;
     return p;
   }
 
@@ -1116,13 +1135,37 @@ struct SlotSolver::Impl {
     K.tolv = dev<double>(S); K.Zcur = dev<double2*>(S); K.Vcur = dev<double2*>(S);
     K.adm = dev<int>(S); K.fin = dev<int>(S); K.xout = dev<double2*>(S); K.bdev = dev<double2>((size_t)S * D);
     W = dev<double2>((size_t)S * t * D);
-    K.Wp = dev<double>((size_t)S * t * 3 * D);
+    K.gst = E.opts.gs_tensor ? 1 : 0;
+    K.Dp = (int)((D + 767) / 768 * 768);  // whole 256-node groups and 384-node update tiles
+    K.NU = gst_nu_rows(t);
+    if (K.gst) {
+      if (gst_set_attributes(t) != cudaSuccess) {
+        cudaGetLastError();
+        return (set_error("tensor-core Gram-Schmidt: kernel attributes refused"), HH_ECUDA);
+      }
+      K.VSptr = dev<unsigned char*>((size_t)S * K.maxV);
+      K.VScur = dev<unsigned char*>(S);
+      K.V0S = dev<unsigned char>((size_t)S * gst_vector_bytes(K.Dp));
+      K.vexp = dev<int>((size_t)S * K.maxV);
+      K.vnew0 = dev<int>(S);
+      K.vnew1 = dev<int>(S);
+      K.vmaxb = dev<unsigned long long>((size_t)S * t);
+      K.wmaxb = dev<unsigned long long>((size_t)S * t);
+      K.WI = dev<unsigned char>((size_t)S * gst_wimage_bytes(K.Dp, t));
+      K.CB = dev<unsigned char>((size_t)S * gst_cimage_bytes(K.maxV, t));
+      K.cexp = dev<int>((size_t)S * t);
+      h_vscur = host<unsigned char*>(S);
+      if (!K.VSptr || !K.V0S || !K.WI || !K.CB || !K.cexp || !h_vscur) return HH_ENOMEM;
+    } else {
+      K.Wp = dev<double>((size_t)S * t * 3 * D);
+      if (!K.Wp) return HH_ENOMEM;
+    }
     qbar = dev<unsigned>((size_t)S * GRID_BAR_WORDS);
     xstage = dev<double2>((size_t)S * D);
     d_act = dev<int>(S);
     T.src = (const double2**)dev<double2*>((size_t)S * t); T.scale = dev<double>((size_t)S * t);
     T.zdst = dev<double2*>((size_t)S * t); T.wdst = dev<double2*>((size_t)S * t);
-    if (!W || !K.Wp || !xstage || !T.wdst || !K.bdev || !K.Rrot) return HH_ENOMEM;
+    if (!W || !xstage || !T.wdst || !K.bdev || !K.Rrot) return HH_ENOMEM;
     h_act = host<int>(S); h_done = host<int>(S); h_iters = host<int>(S); h_status = host<int>(S);
     h_mask = host<int>(S); h_rho = host<double>(S); h_beta = host<double>(S); h_res = host<double>(S);
     h_tolv = host<double>(S);
@@ -1184,6 +1227,7 @@ struct SlotSolver::Impl {
     start_kernel<<<S, 32, 0, E.stream>>>(K);
     scale_copy_kernel<<<ng, 256, 0, E.stream>>>(K);
     E.count_launch(3);
+    if (K.gst) gst_slice_basis(E, K, S, 1);
     // slots whose right-hand side is zero (or not finite) finish at once
     cudaMemcpyAsync(h_done, K.done, sizeof(int) * S, cudaMemcpyDeviceToHost, E.stream);
     cudaError_t e = cudaStreamSynchronize(E.stream);
@@ -1196,6 +1240,22 @@ struct SlotSolver::Impl {
   // nv: basis vectors of all active slots (each projected against its t new columns)
   void gs_and_qr(cudaError_t& ce, double nv, bool tick) {
     dim3 gsgrid(K.GX, S);
+    if (K.gst) {
+      for (int pass = 0; pass < K.passes; ++pass) {
+        if (tick) E.tick_begin(Engine::K_GSDOT);
+        gst_pass_dot(E, K, S, W, pass == 0);
+        // algorithmic: one complex multiply-add per basis element and new column; the basis
+        // slice images (32 bytes per node) are read once, the new columns' image once per CTA
+        if (tick) E.tick_end(Engine::K_GSDOT, nv * (double)K.Dp * 32.0 + (double)t * K.Dp * 64.0, 8.0 * nv * t * D);
+        gs_reduce_kernel<<<dim3((K.maxV * t + 7) / 8, S), 256, 0, E.stream>>>(K, pass == 0, gst_dot_ctas(E, K, S));
+        E.count_launch();
+        gst_pass_update(E, K, S, W);
+      }
+      cudaMemsetAsync(qbar, 0, sizeof(unsigned) * S * GRID_BAR_WORDS, E.stream);
+      void* args[] = {(void*)&K, (void*)&W, (void*)&qbar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
+      ce = E.launch_coop((const void*)qr_kernel<TT>, K.GQ, 256, 0, args, S);
+      return;
+    }
     gs_wprep_kernel<TT><<<gsgrid, 256, 0, E.stream>>>(K, W);
     E.count_launch();
     for (int pass = 0; pass < K.passes; ++pass) {
@@ -1207,7 +1267,7 @@ struct SlotSolver::Impl {
       // one complex multiply-add (8 real flops) per basis element and new column; the basis
       // (16 bytes per element) is read once, the column planes (24 bytes) once per 4 vectors
       if (tick) E.tick_end(Engine::K_GSDOT, nv * D * 16.0 + (double)t * D * 24.0 * nv / 4.0, 8.0 * nv * t * D);
-      gs_reduce_kernel<<<dim3((K.maxV * t + 7) / 8, S), 256, 0, E.stream>>>(K, pass == 0);
+      gs_reduce_kernel<<<dim3((K.maxV * t + 7) / 8, S), 256, 0, E.stream>>>(K, pass == 0, K.GX);
       const size_t smem = (size_t)K.maxV * TT * 3 * sizeof(double) + (size_t)K.maxV * sizeof(void*);
       cudaFuncSetAttribute((const void*)gs_update_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       gs_update_kernel<TT><<<gsgrid, 256, smem, E.stream>>>(K, W, pass + 1 < K.passes ? 1 : 0);
@@ -1239,7 +1299,14 @@ struct SlotSolver::Impl {
         slots[r].blocks.push_back(v);
         h_zcur[r] = (double2*)z;
         h_vcur[r] = (double2*)v;
+        if (K.gst) {
+          void* sv = sblock();
+          if (!sv) return HH_ENOMEM;
+          slots[r].sblocks.push_back(sv);
+          h_vscur[r] = (unsigned char*)sv;
+        }
       }
+      if (K.gst) cudaMemcpyAsync(K.VScur, h_vscur, sizeof(unsigned char*) * S, cudaMemcpyHostToDevice, E.stream);
       cudaMemcpyAsync(K.Zcur, h_zcur, sizeof(double2*) * S, cudaMemcpyHostToDevice, E.stream);
       cudaMemcpyAsync(K.Vcur, h_vcur, sizeof(double2*) * S, cudaMemcpyHostToDevice, E.stream);
       cudaMemcpyAsync(d_act, h_act, sizeof(int) * nact, cudaMemcpyHostToDevice, E.stream);
@@ -1306,6 +1373,7 @@ struct SlotSolver::Impl {
     source_sum_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K);
     source_final_kernel<<<S, 32, 0, E.stream>>>(K);
     E.count_launch(3);
+    if (K.gst) gst_slice_basis(E, K, S, 0);
     return HH_OK;
   }
 
@@ -1404,6 +1472,8 @@ struct SlotSolver::Impl {
       out.push_back(d);
       for (void* p : slots[r].blocks) pool.push_back(p);
       slots[r].blocks.clear();
+      for (void* p : slots[r].sblocks) spool.push_back(p);
+      slots[r].sblocks.clear();
       slots[r] = Slot();
     }
     return HH_OK;

@@ -630,13 +630,55 @@ def test_fp32_first_gram_schmidt_pass():
     k, n, N = 60.0, 128, 8
     P = solver.Problem(k, n, N)
     b = P.rhs(hh_inputs.centre_source())
-    with hh.Handle(k, n, N, precision="fp32") as h1, hh.Handle(k, n, N, precision="fp32", gs_first_fp32=0) as h0:
+    with hh.Handle(k, n, N, precision="fp32", gs_tensor=0) as h1, \
+            hh.Handle(k, n, N, precision="fp32", gs_first_fp32=0, gs_tensor=0) as h0:
         x1, r1 = h1.solve(b, tol=1e-8)
         x0, r0 = h0.solve(b, tol=1e-8)
     assert r1.status == hh.HH_OK and r0.status == hh.HH_OK
     assert abs(r1.iterations - r0.iterations) <= 1
     assert rel(x1, x0) < 1e-6
     assert r1.rel_res_explicit < 2 * max(r1.rel_res_implicit, 1e-10)
+
+
+@pytest.mark.parametrize("dirs", ["BT", "LR+BT", "LR+BT+RL", "LR+RL+BT+TB"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tensor_core_gram_schmidt(dirs, precision):
+    """Gram-Schmidt against the basis as exact integer products of 7-bit slices on the tensor
+    cores (hh_opts.gs_tensor = 1) against the FP64-pipe kernels: FP64-accurate inner products
+    and updates give the same iterations, the same solution to rounding, and the explicit
+    residual on the implicit one, for t = 1..4 new columns per iteration.  The two round
+    differently (FP64 sums in another order; slices truncated at 2^-56 of a vector's largest
+    entry), and the Krylov basis amplifies that: FP64 solutions agree to 1e-11, ten times
+    inside the oracle parity bar."""
+    k, n, N = 60.0, 128, 8
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    with hh.Handle(k, n, N, dirs, precision=precision) as h1, \
+            hh.Handle(k, n, N, dirs, precision=precision, gs_tensor=0) as h0:
+        x1, r1 = h1.solve(b, tol=1e-10)
+        x0, r0 = h0.solve(b, tol=1e-10)
+    assert r1.status == hh.HH_OK and r0.status == hh.HH_OK
+    assert r1.iterations == r0.iterations
+    assert rel(x1, x0) < (1e-11 if precision == "fp64" else 1e-9)
+    assert r1.rel_res_explicit < 2 * max(r1.rel_res_implicit, 1e-12)
+
+
+def test_tensor_core_gram_schmidt_long_basis():
+    """More than 128 basis vectors (two tensor-memory rounds of the inner products, three
+    exact-accumulation segments of the update) with single sweeps to a tight tolerance: the
+    same iterations and solution as the FP64-pipe kernels."""
+    k, n, N = 40.0, 64, 8
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    kw = dict(precision="fp64", single_sweep=1, maxit=60)
+    with hh.Handle(k, n, N, "LR+RL+BT+TB", **kw) as h1, \
+            hh.Handle(k, n, N, "LR+RL+BT+TB", gs_tensor=0, **kw) as h0:
+        x1, r1 = h1.solve(b, tol=1e-13)
+        x0, r0 = h0.solve(b, tol=1e-13)
+    assert r0.iterations >= 33, r0.iterations  # 1 + 4 x 32 > 128 basis vectors
+    assert abs(r1.iterations - r0.iterations) <= 1
+    assert rel(x1, x0) < 1e-10
+    assert r1.rel_res_explicit < 10 * max(r1.rel_res_implicit, 1e-13)
 
 
 BF16_SWEEP_BAR = 3e-2
