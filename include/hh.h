@@ -180,6 +180,9 @@ typedef struct {
   int step_graph_fallback;  /* 1 if a step could not be captured and ran eagerly */
   int bcr_depth;            /* cyclic-reduction depth of the strip solves for the last column
                                count (fixed by opts.bcr_depth or autotuned) */
+  double gsdot_bytes;       /* algorithmic bytes of the timed inner-product launches (the
+                               tensor-core form: the basis slice images and the new columns'
+                               image, read once) */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -224,6 +227,16 @@ hh_status hh_apply_operator(hh_handle* h, int ncols, const double* x, double* y)
 /* z = M_d^{-1} r for ncols columns and ONE direction bit (the handle's precision; a double
  * sweep unless opts.single_sweep).  dir need not be in the handle's dirs. */
 hh_status hh_apply_preconditioner(hh_handle* h, uint32_t dir, int ncols, const double* r, double* z);
+
+/* One pass of the block classical Gram-Schmidt of Section 3 against p basis columns, with the
+ * solver's kernels (hh_opts.gs_tensor of the handle selects the tensor-core slices or the
+ * FP64 pipe): H = V^H W, then W <- W - V H.
+ *   V  p complex128 columns of (n+1)^2 entries (column stride 2 (n+1)^2 doubles), host or device;
+ *   W  t complex128 columns (1 <= t <= 4), host or device, overwritten with W - V H;
+ *   H  HOST memory, p x t complex128, entry (a, b) at 2 (a t + b): <v_a, w_b> = sum conj(v_a) w_b.
+ * Allocates its working buffers (the slice images: 64 bytes per node per basis column) for the
+ * call.  HH_EINVAL for p < 1, t outside 1..4 or a NULL pointer. */
+hh_status hh_gram_schmidt_pass(hh_handle* h, int p, const double* V, int t, double* W, double* H);
 
 /*
  * z = M_d^{-1} r like hh_apply_preconditioner, for callers that cannot allocate device

@@ -57,7 +57,8 @@ class hh_stats(ctypes.Structure):
                 ("gsdot_flops", ctypes.c_double), ("gs_flops", ctypes.c_double), ("wide_steps", ctypes.c_int64),
                 ("ns_blocks", ctypes.c_int), ("ns_iterations", ctypes.c_int), ("tc_bnc", ctypes.c_int),
                 ("tc_nsplit", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_us", ctypes.c_double), ("iterations_total", ctypes.c_int64),
-                ("step_graphs", ctypes.c_int), ("step_graph_fallback", ctypes.c_int), ("bcr_depth", ctypes.c_int)]
+                ("step_graphs", ctypes.c_int), ("step_graph_fallback", ctypes.c_int), ("bcr_depth", ctypes.c_int),
+                ("gsdot_bytes", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -74,7 +75,8 @@ class hh_server_stats(ctypes.Structure):
 
 
 EXPORTS = ["hh_default_opts", "hh_setup", "hh_solve", "hh_solve_batch", "hh_submit", "hh_poll", "hh_assemble_rhs",
-           "hh_apply_operator", "hh_apply_preconditioner", "hh_apply_preconditioner_noalloc", "hh_get_factor",
+           "hh_apply_operator", "hh_apply_preconditioner", "hh_apply_preconditioner_noalloc", "hh_gram_schmidt_pass",
+           "hh_get_factor",
            "hh_get_stats", "hh_reset_stats", "hh_destroy", "hh_last_error", "hh_server_create", "hh_server_submit",
            "hh_server_poll", "hh_server_get_stats", "hh_server_destroy"]
 
@@ -101,6 +103,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hh_apply_operator.argtypes = [vp, i, vp, vp]
     L.hh_apply_preconditioner.argtypes = [vp, u32, i, vp, vp]
     L.hh_apply_preconditioner_noalloc.argtypes = [vp, u32, i, vp, vp]
+    L.hh_gram_schmidt_pass.argtypes = [vp, i, vp, i, vp, vp]
     L.hh_get_factor.argtypes = [vp, i, vp]
     L.hh_get_stats.argtypes = [vp, ctypes.POINTER(hh_stats)]
     L.hh_reset_stats.argtypes = [vp]
@@ -255,6 +258,14 @@ class Handle:
         Returns the status (HH_OK, or HH_EINVAL for host buffers / a request above the fixed
         scratch size)."""
         return self.lib.hh_apply_preconditioner_noalloc(self.h, DIR_BITS[direction], int(ncols), _ptr(r), _ptr(z))
+
+    def gram_schmidt_pass(self, V, p: int, W, t: int) -> np.ndarray:
+        """hh_gram_schmidt_pass: H = V^H W (returned, p x t complex128) and W <- W - V H in place
+        (V: p columns, W: t columns, numpy arrays or device tensors)."""
+        H = np.zeros(p * t, dtype=np.complex128)
+        st = self.lib.hh_gram_schmidt_pass(self.h, int(p), _ptr(V), int(t), _ptr(W), H.ctypes.data)
+        self._check(st, "hh_gram_schmidt_pass")
+        return H.reshape(p, t)
 
     def get_factor(self, j: int) -> np.ndarray:
         out = np.zeros(self.m * self.m, dtype=np.complex128)

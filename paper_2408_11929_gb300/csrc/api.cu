@@ -510,6 +510,19 @@ hh_status hh_apply_operator(hh_handle* h, int ncols, const double* x, double* y)
   return (hh_status)rc;
 }
 
+hh_status hh_gram_schmidt_pass(hh_handle* h, int p, const double* V, int t, double* W, double* H) {
+  if (!h || !V || !W || !H || p < 1 || t < 1 || t > 4) return (set_error("bad arguments"), HH_EINVAL);
+  Engine& E = *h->E;
+  std::lock_guard<std::mutex> lk(E.solve_mu);
+  cudaSetDevice(E.device);
+  const size_t col = (size_t)E.m * E.m * sizeof(double2);
+  Staged sv(&E, V, (size_t)p * col, 0), sw(&E, W, (size_t)t * col, 1);
+  if (sv.in() || sw.in()) return HH_ENOMEM;
+  int rc = gram_schmidt_pass(E, p, (const double2*)sv.dev, t, (double2*)sw.dev, reinterpret_cast<double2*>(H));
+  if (rc == HH_OK && sw.out()) rc = HH_ECUDA;
+  return (hh_status)rc;
+}
+
 hh_status hh_apply_preconditioner(hh_handle* h, uint32_t dir, int ncols, const double* r, double* z) {
   if (!h || !r || !z || ncols < 1) return (set_error("bad arguments"), HH_EINVAL);
   int code;
@@ -599,6 +612,7 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->gsdot_launches = E.launches[Engine::K_GSDOT];
   st->gsdot_ms = E.ms[Engine::K_GSDOT];
   st->gsdot_flops = E.flops[Engine::K_GSDOT];
+  st->gsdot_bytes = E.bytes[Engine::K_GSDOT];
   st->gs_flops = E.flops[Engine::K_GS];
   st->ns_blocks = E.ns_blocks;
   st->ns_iterations = E.ns_iterations;

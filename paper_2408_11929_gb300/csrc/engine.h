@@ -19,6 +19,9 @@
 namespace hh {
 
 void set_error(const std::string& msg);
+struct Engine;
+// H = V^H W and W <- W - V H (one block classical Gram-Schmidt pass, krylov.cu)
+int gram_schmidt_pass(Engine& E, int p, const double2* V, int t, double2* W, double2* H_host);
 
 // One step of the batched sweep (see sweep.cu): for strips s0 .. s0+ns-1,
 //   out[out_j] (set / -= / +=) F_f * x,   x = base[base_j] +- C(src[src_j], strip s + src_ds)

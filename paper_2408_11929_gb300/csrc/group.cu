@@ -216,7 +216,7 @@ template <class CF, bool CLUSTER>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     tc_group_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                     const __grid_constant__ GMaps maps, const GTask* __restrict__ tasks, int ntask, GArrays arrs,
-                    int m, int N, int C, int kst, int* err, long long budget) {
+                    int m, int N, int C, int kst, int split, int* err, long long budget) {
   using namespace tc;
   constexpr int BNC = CF::BNC, STAGES = CF::STAGES, BTILE = CF::BTILE;
   constexpr int STAGE_BYTES = CF::STAGE_BYTES, PAIR_GROUPS = CF::PAIR_GROUPS;
@@ -276,9 +276,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const int s = kt % STAGES, st = kb + kt;
         const int q = st / spt, k0 = (st % spt) * BKC;
         unsigned char* stp = sm + (size_t)s * STAGE_BYTES;
-        mbar_expect_tx(&full_a[s], 2 * TILE + RAW_BYTES);
-        tc::tma_load_3d(stp, &map_hi, 2 * k0, row0, tk.term[q].f, &full_a[s]);
-        tc::tma_load_3d(stp + TILE, &map_lo, 2 * k0, row0, tk.term[q].f, &full_a[s]);
+        if (split) {
+          // map_hi is the complex64 store itself: the builders split the tile into hi + lo
+          mbar_expect_tx(&full_a[s], TILE + RAW_BYTES);
+          tc::tma_load_3d(stp, &map_hi, 2 * k0, row0, tk.term[q].f, &full_a[s]);
+        } else {
+          mbar_expect_tx(&full_a[s], 2 * TILE + RAW_BYTES);
+          tc::tma_load_3d(stp, &map_hi, 2 * k0, row0, tk.term[q].f, &full_a[s]);
+          tc::tma_load_3d(stp + TILE, &map_lo, 2 * k0, row0, tk.term[q].f, &full_a[s]);
+        }
       };
       auto load_raw = [&](int kt) {
         const int s = kt % STAGES, st = kb + kt;
@@ -357,6 +363,19 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       const int st = kb + kt;
       const int k0 = (st % spt) * BKC;
       const float sg = tk.term[st / spt].neg ? -1.f : 1.f;
+      if (split) {
+        // A = hi + lo elementwise, the swizzled layout kept: hi in place, lo in the second tile
+        float4* ah = reinterpret_cast<float4*>(sm + (size_t)s * STAGE_BYTES);
+        float4* al = reinterpret_cast<float4*>(sm + (size_t)s * STAGE_BYTES + TILE);
+        for (int e = threadIdx.x; e < TILE / 16; e += BUILDERS) {
+          const float4 v = ah[e];
+          float4 hv, lv;
+          tc::split_tf32(v.x, hv.x, lv.x); tc::split_tf32(v.y, hv.y, lv.y);
+          tc::split_tf32(v.z, hv.z, lv.z); tc::split_tf32(v.w, hv.w, lv.w);
+          ah[e] = hv;
+          al[e] = lv;
+        }
+      }
       unsigned char* bh = sm + (size_t)s * STAGE_BYTES + 2 * TILE;
       unsigned char* bl = bh + BTILE;
       const float2* rb = reinterpret_cast<const float2*>(bh);
@@ -569,13 +588,18 @@ static cudaError_t launch_tc_group_shape(Engine& E, const SweepPhase& ph, const 
   cfg.attrs = attr;
   cfg.numAttrs = na;
   const GTask* tasks = E.prog_tasks + ph.dev_off;
+  // split = 1 would read the factor tiles from the complex64 store and split them into TF32
+  // hi + lo in shared memory (half the factor bytes); measured slower at k = 400 (2.82 against
+  // 2.69 ms per sweep): these steps are not bound by HBM, and the splitting delays the MMAs
+  const int split = 0;
+  const CUtensorMap& fa = split ? E.tmap_c : E.tmap_hi;
   cudaError_t ce;
   if (nsplit > 1)
-    ce = cudaLaunchKernelEx(&cfg, tc_group_kernel<CF, true>, E.tmap_hi, E.tmap_lo, maps, tasks, ntask, arrs, E.m, E.N,
-                            C, kst, E.err, E.opts.timeout_cycles);
+    ce = cudaLaunchKernelEx(&cfg, tc_group_kernel<CF, true>, fa, E.tmap_lo, maps, tasks, ntask, arrs, E.m, E.N,
+                            C, kst, split, E.err, E.opts.timeout_cycles);
   else
-    ce = cudaLaunchKernelEx(&cfg, tc_group_kernel<CF, false>, E.tmap_hi, E.tmap_lo, maps, tasks, ntask, arrs, E.m, E.N,
-                            C, kst, E.err, E.opts.timeout_cycles);
+    ce = cudaLaunchKernelEx(&cfg, tc_group_kernel<CF, false>, fa, E.tmap_lo, maps, tasks, ntask, arrs, E.m, E.N,
+                            C, kst, split, E.err, E.opts.timeout_cycles);
   E.count_launch();
   return ce;
 }

@@ -643,7 +643,9 @@ __global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, int*
       const int nflush = (ns + DOT_FL - 1) / DOT_FL;
       for (int f = 0; f < nflush && ok; ++f) {
         for (int T = 0; T < nt; ++T) {
-          if (!mbar_wait(&accfull[T], (unsigned)cnt[T] & 1u, err, budget) || tc::aborted(&abort_s)) {
+          // warp-uniform decision: the shuffles below need every lane of the warp
+          const bool got = mbar_wait(&accfull[T], (unsigned)cnt[T] & 1u, err, budget) && !tc::aborted(&abort_s);
+          if (!__all_sync(0xffffffffu, got)) {
             ok = false;
             break;
           }
@@ -717,8 +719,8 @@ __global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, int*
 // coefficient image CB, three MMAs (M = 128 nodes, N = NU, K = 16) into one of two tensor-memory
 // buffers; every 64 vectors the buffer is read out and its weight groups summed in int64.
 template <int TT>
-__global__ void __launch_bounds__(gst::UPD_THREADS, 1) gst_upd_kernel(KState S, double2* __restrict__ W, int* err,
-                                                                      long long budget) {
+__global__ void __launch_bounds__(gst::UPD_THREADS, 1) gst_upd_kernel(KState S, double2* __restrict__ W,
+                                                                      int track_max, int* err, long long budget) {
   using namespace gst;
   constexpr int NU = nu_rows(TT), CBB = NU * 32, STB = upd_stage_bytes(TT), NOUT = 2 * TT, NCOLS = 20 * TT;
   constexpr uint32_t IDESC =
@@ -852,7 +854,8 @@ __global__ void __launch_bounds__(gst::UPD_THREADS, 1) gst_upd_kernel(KState S, 
       for (int b = 0; b < NOUT; ++b) oh[b] = ol[b] = 0;
       for (int sg = 0; sg < nseg; ++sg) {
         const int buf = sc & 1;
-        if (!mbar_wait(&accfull[buf], (unsigned)(sc >> 1) & 1u, err, budget) || tc::aborted(&abort_s)) {
+        const bool got = mbar_wait(&accfull[buf], (unsigned)(sc >> 1) & 1u, err, budget) && !tc::aborted(&abort_s);
+        if (!__all_sync(0xffffffffu, got)) {  // warp-uniform: the warp reductions need every lane
           ok = false;
           break;
         }
@@ -878,6 +881,9 @@ __global__ void __launch_bounds__(gst::UPD_THREADS, 1) gst_upd_kernel(KState S, 
       }
       if (!ok) break;
       const size_t g = (size_t)tile * UPD_NODES + h * 128 + R;
+      unsigned long long mx[TT];
+#pragma unroll
+      for (int b = 0; b < TT; ++b) mx[b] = 0;
       if (g < D) {
 #pragma unroll
         for (int b = 0; b < TT; ++b) {
@@ -892,6 +898,15 @@ __global__ void __launch_bounds__(gst::UPD_THREADS, 1) gst_upd_kernel(KState S, 
             w.y -= i64_scaled(oh[2 * b + 1], Eb - 42) + i64_scaled(ol[2 * b + 1], Eb - 77);
           }
           Wr[b * D + g] = w;
+          mx[b] = max(gst::abs_bits(w.x), gst::abs_bits(w.y));
+        }
+      }
+      if (track_max) {
+        // the next pass's column maxima (its slice scale), instead of another pass over W
+#pragma unroll
+        for (int b = 0; b < TT; ++b) {
+          const unsigned long long mw = warp_max_u64(mx[b]);
+          if (lane == 0 && mw) atomicMax(&S.wmaxb[(size_t)r * TT + b], mw);
         }
       }
     }
@@ -941,19 +956,27 @@ void gst_slice_basis(Engine& E, const KState& K, int S, int mode) {
 }
 
 template <int TT>
-static void pass_a_t(Engine& E, const KState& K, int S, const double2* W, bool first, int gd) {
-  cudaMemsetAsync(K.wmaxb, 0, sizeof(unsigned long long) * S * TT, E.stream);
-  gst_wscan_kernel<TT><<<dim3(K.GX, S), 256, 0, E.stream>>>(K, W, first ? 1 : 0);
+static void prep_w_t(Engine& E, const KState& K, int S, const double2* W, bool first) {
+  if (first) {  // later passes take the column maxima from the previous pass's update
+    cudaMemsetAsync(K.wmaxb, 0, sizeof(unsigned long long) * S * TT, E.stream);
+    gst_wscan_kernel<TT><<<dim3(K.GX, S), 256, 0, E.stream>>>(K, W, 1);
+    E.count_launch(1);
+  }
   const int gs = std::max(1, std::min(E.num_sms * 4 / std::max(1, S), K.Dp / 256));
   gst_wslice_kernel<TT><<<dim3(gs, S), 256, 8 * gst::dot_bbytes(TT), E.stream>>>(K, W);
+  E.count_launch(1);
+}
+template <int TT>
+static void dot_t(Engine& E, const KState& K, int S, int gd) {
   gst_dot_kernel<TT><<<dim3(gd, S), gst::THREADS, gst::dot_smem(TT), E.stream>>>(K, E.err, E.opts.timeout_cycles);
-  E.count_launch(3);
+  E.count_launch(1);
 }
 
 template <int TT>
-static void pass_b_t(Engine& E, const KState& K, int S, double2* W, int gu) {
+static void pass_b_t(Engine& E, const KState& K, int S, double2* W, int gu, bool track_max) {
   gst_cslice_kernel<TT><<<S, 256, 0, E.stream>>>(K);
-  gst_upd_kernel<TT><<<dim3(gu, S), gst::UPD_THREADS, gst::upd_smem(TT), E.stream>>>(K, W, E.err,
+  if (track_max) cudaMemsetAsync(K.wmaxb, 0, sizeof(unsigned long long) * S * TT, E.stream);
+  gst_upd_kernel<TT><<<dim3(gu, S), gst::UPD_THREADS, gst::upd_smem(TT), E.stream>>>(K, W, track_max ? 1 : 0, E.err,
                                                                                     E.opts.timeout_cycles);
   E.count_launch(2);
 }
@@ -966,26 +989,36 @@ int gst_upd_ctas(const Engine& E, const KState& K, int S) {
   return std::max(1, std::min(E.num_sms / std::max(1, S), K.Dp / gst::UPD_NODES));
 }
 
-// First half of a Gram-Schmidt pass: the new columns' maxima (and, first pass, the deflation
-// reference), their slice image, and the inner-product partials (gst_dot_ctas per slot).
-void gst_pass_dot(Engine& E, const KState& K, int S, const double2* W, bool first) {
-  const int gd = gst_dot_ctas(E, K, S);
+// First part of a Gram-Schmidt pass: (first pass) the new columns' maxima and the deflation
+// reference, then their slice image.
+void gst_prepare_columns(Engine& E, const KState& K, int S, const double2* W, bool first) {
   switch (K.t) {
-    case 1: pass_a_t<1>(E, K, S, W, first, gd); break;
-    case 2: pass_a_t<2>(E, K, S, W, first, gd); break;
-    case 3: pass_a_t<3>(E, K, S, W, first, gd); break;
-    default: pass_a_t<4>(E, K, S, W, first, gd); break;
+    case 1: prep_w_t<1>(E, K, S, W, first); break;
+    case 2: prep_w_t<2>(E, K, S, W, first); break;
+    case 3: prep_w_t<3>(E, K, S, W, first); break;
+    default: prep_w_t<4>(E, K, S, W, first); break;
   }
 }
 
-// Second half, after the partials are summed into Hthis: the coefficient images and the update.
-void gst_pass_update(Engine& E, const KState& K, int S, double2* W) {
+// Second part: the inner-product partials (gst_dot_ctas CTAs per slot).
+void gst_inner_products(Engine& E, const KState& K, int S) {
+  const int gd = gst_dot_ctas(E, K, S);
+  switch (K.t) {
+    case 1: dot_t<1>(E, K, S, gd); break;
+    case 2: dot_t<2>(E, K, S, gd); break;
+    case 3: dot_t<3>(E, K, S, gd); break;
+    default: dot_t<4>(E, K, S, gd); break;
+  }
+}
+
+// Last part, after the partials are summed into Hthis: the coefficient images and the update.
+void gst_pass_update(Engine& E, const KState& K, int S, double2* W, bool track_max) {
   const int gu = gst_upd_ctas(E, K, S);
   switch (K.t) {
-    case 1: pass_b_t<1>(E, K, S, W, gu); break;
-    case 2: pass_b_t<2>(E, K, S, W, gu); break;
-    case 3: pass_b_t<3>(E, K, S, W, gu); break;
-    default: pass_b_t<4>(E, K, S, W, gu); break;
+    case 1: pass_b_t<1>(E, K, S, W, gu, track_max); break;
+    case 2: pass_b_t<2>(E, K, S, W, gu, track_max); break;
+    case 3: pass_b_t<3>(E, K, S, W, gu, track_max); break;
+    default: pass_b_t<4>(E, K, S, W, gu, track_max); break;
   }
 }
 

@@ -29,8 +29,9 @@ void launch_unpack(Engine& E, const void* X, int C, int t, int4 codes, double2* 
 // tensor-core Gram-Schmidt (gs_tc.cu)
 cudaError_t gst_set_attributes(int t);
 void gst_slice_basis(Engine& E, const KState& K, int S, int mode);
-void gst_pass_dot(Engine& E, const KState& K, int S, const double2* W, bool first);
-void gst_pass_update(Engine& E, const KState& K, int S, double2* W);
+void gst_prepare_columns(Engine& E, const KState& K, int S, const double2* W, bool first);
+void gst_inner_products(Engine& E, const KState& K, int S);
+void gst_pass_update(Engine& E, const KState& K, int S, double2* W, bool track_max);
 int gst_dot_ctas(const Engine& E, const KState& K, int S);
 size_t gst_vector_bytes(size_t Dp);
 size_t gst_wimage_bytes(size_t Dp, int t);
@@ -1242,14 +1243,16 @@ struct SlotSolver::Impl {
     dim3 gsgrid(K.GX, S);
     if (K.gst) {
       for (int pass = 0; pass < K.passes; ++pass) {
+        gst_prepare_columns(E, K, S, W, pass == 0);
         if (tick) E.tick_begin(Engine::K_GSDOT);
-        gst_pass_dot(E, K, S, W, pass == 0);
-        // algorithmic: one complex multiply-add per basis element and new column; the basis
-        // slice images (32 bytes per node) are read once, the new columns' image once per CTA
+        gst_inner_products(E, K, S);
+        // algorithmic: the basis slice images (32 bytes per node and vector) and the new
+        // columns' image (64 t bytes per node), each read once; one complex multiply-add per
+        // basis element and new column
         if (tick) E.tick_end(Engine::K_GSDOT, nv * (double)K.Dp * 32.0 + (double)t * K.Dp * 64.0, 8.0 * nv * t * D);
         gs_reduce_kernel<<<dim3((K.maxV * t + 7) / 8, S), 256, 0, E.stream>>>(K, pass == 0, gst_dot_ctas(E, K, S));
         E.count_launch();
-        gst_pass_update(E, K, S, W);
+        gst_pass_update(E, K, S, W, pass + 1 < K.passes);
       }
       cudaMemsetAsync(qbar, 0, sizeof(unsigned) * S * GRID_BAR_WORDS, E.stream);
       void* args[] = {(void*)&K, (void*)&W, (void*)&qbar, (void*)&E.err, (void*)&E.opts.timeout_cycles};
@@ -1359,8 +1362,14 @@ struct SlotSolver::Impl {
       case 3: gs_and_qr<3>(ce, nv, tick_dot); break;
       default: gs_and_qr<4>(ce, nv, tick_dot); break;
     }
+    // algorithmic bytes per pass: the basis read twice (FP64: 16 bytes per node and vector;
+    // tensor-core form: its 32-byte slice image, by the inner products and by the update) and
+    // the new columns (FP64: three planes; slices: their 64 t-byte image, W read and written);
+    // the block QR about six passes over the new columns
     if (timed)
-      E.tick_end(Engine::K_GS, K.passes * (2.0 * nv * D * 16 + 3.0 * C * D * 16) + 6.0 * C * D * 16,
+      E.tick_end(Engine::K_GS,
+                 (K.gst ? K.passes * (2.0 * nv * K.Dp * 32 + 64.0 * C * K.Dp + 2.0 * C * D * 16)
+                        : K.passes * (2.0 * nv * D * 16 + 3.0 * C * D * 16)) + 6.0 * C * D * 16,
                  K.passes * 16.0 * nv * t * D);
     if (ce != cudaSuccess) return HH_ECUDA;
     // the Hessenberg column, and the rotations too when they fit in shared memory
@@ -1595,6 +1604,118 @@ int Engine::apply_preconditioner_dev(int dcode, int ncols, const double2* r, dou
   if (rc) return rc;
   if (e != cudaSuccess) { set_cuda_error(e, "apply_preconditioner"); return HH_ECUDA; }
   return check_device_error("sweep");
+}
+
+}  // namespace hh
+
+namespace hh {
+
+// ------------------------------------------------------------------ one Gram-Schmidt pass
+// H = V^H W and W <- W - V H for p basis columns and t new columns (device pointers; H to host
+// memory, p x t row-major by basis column), with the solver's own kernels: the tensor-core
+// slices when opts.gs_tensor, else the FP64-pipe kernels.  A one-slot kernel state with
+// temporary buffers (allocated and freed here).
+template <int TT>
+static int gs_pass_t(Engine& E, KState& K, double2* W, unsigned char* tmp_slices) {
+  const int p = K.maxV;
+  dim3 gsgrid(K.GX, 1);
+  if (K.gst) {
+    std::vector<unsigned char*> sp(p);
+    for (int a = 0; a < p; ++a) sp[a] = tmp_slices + (size_t)a * gst_vector_bytes(K.Dp);
+    cudaMemcpyAsync(K.VSptr, sp.data(), sizeof(unsigned char*) * p, cudaMemcpyHostToDevice, E.stream);
+    for (int c = 0; c < p; c += TT) {
+      const int range[2] = {c, std::min(p, c + TT)};
+      cudaMemcpyAsync(K.vnew0, &range[0], sizeof(int), cudaMemcpyHostToDevice, E.stream);
+      cudaMemcpyAsync(K.vnew1, &range[1], sizeof(int), cudaMemcpyHostToDevice, E.stream);
+      gst_slice_basis(E, K, 1, 0);
+      cudaStreamSynchronize(E.stream);  // range lives on this stack frame
+    }
+    gst_prepare_columns(E, K, 1, W, true);
+    gst_inner_products(E, K, 1);
+    gs_reduce_kernel<<<dim3((K.maxV * TT + 7) / 8, 1), 256, 0, E.stream>>>(K, 1, gst_dot_ctas(E, K, 1));
+    gst_pass_update(E, K, 1, W, false);
+  } else {
+    gs_wprep_kernel<TT><<<gsgrid, 256, 0, E.stream>>>(K, W);
+    gs_dot_kernel<TT, 4><<<gsgrid, 256, 0, E.stream>>>(K);
+    gs_reduce_kernel<<<dim3((K.maxV * TT + 7) / 8, 1), 256, 0, E.stream>>>(K, 1, K.GX);
+    const size_t smem = (size_t)K.maxV * TT * 3 * sizeof(double) + (size_t)K.maxV * sizeof(void*);
+    if (cudaFuncSetAttribute((const void*)gs_update_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return (set_error("Gram-Schmidt pass: too many basis columns for the FP64 update kernel"), HH_EINVAL);
+    gs_update_kernel<TT><<<gsgrid, 256, smem, E.stream>>>(K, W, 0);
+  }
+  return HH_OK;
+}
+
+int gram_schmidt_pass(Engine& E, int p, const double2* V, int t, double2* W, double2* H_host) {
+  const size_t D = (size_t)E.m * E.m;
+  KState K{};
+  std::vector<void*> owned;
+  auto dev = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (E.dmalloc(&q, std::max<size_t>(bytes, 16))) return nullptr;
+    cudaMemsetAsync(q, 0, std::max<size_t>(bytes, 16), E.stream);
+    owned.push_back(q);
+    return q;
+  };
+  struct Free {
+    Engine& E;
+    std::vector<void*>& v;
+    ~Free() {
+      cudaStreamSynchronize(E.stream);
+      for (void* q : v) E.dfree(q);
+    }
+  } guard{E, owned};
+  K.nrhs = 1; K.t = t; K.D = (int)D; K.maxit = 1; K.maxV = p; K.maxZ = 1; K.passes = 1;
+  K.GX = std::max(1, std::min(E.num_sms * 2 + 1, (int)((D + 255) / 256)));
+  K.GX = std::min(K.GX, E.num_sms * 2);
+  K.gst = E.opts.gs_tensor ? 1 : 0;
+  K.Dp = (int)((D + 767) / 768 * 768);
+  K.NU = gst_nu_rows(t);
+  K.done = (int*)dev(sizeof(int));
+  K.nV = (int*)dev(sizeof(int));
+  K.adm = (int*)dev(sizeof(int));
+  K.Vptr = (double2**)dev(sizeof(double2*) * p);
+  K.Hpart = (double2*)dev(sizeof(double2) * p * t * K.GX);
+  K.Hthis = (double2*)dev(sizeof(double2) * p * t);
+  K.Hacc = (double2*)dev(sizeof(double2) * p * t);
+  K.azpart = (double*)dev(sizeof(double) * t * K.GX);
+  unsigned char* slices = nullptr;
+  if (K.gst) {
+    if (gst_set_attributes(t) != cudaSuccess) return (E.set_cuda_error(cudaGetLastError(), "attributes"), HH_ECUDA);
+    K.VSptr = (unsigned char**)dev(sizeof(unsigned char*) * p);
+    K.vexp = (int*)dev(sizeof(int) * p);
+    K.vnew0 = (int*)dev(sizeof(int));
+    K.vnew1 = (int*)dev(sizeof(int));
+    K.vmaxb = (unsigned long long*)dev(sizeof(unsigned long long) * t);
+    K.wmaxb = (unsigned long long*)dev(sizeof(unsigned long long) * t);
+    K.WI = (unsigned char*)dev(gst_wimage_bytes(K.Dp, t));
+    K.CB = (unsigned char*)dev(gst_cimage_bytes(p, t));
+    K.cexp = (int*)dev(sizeof(int) * t);
+    slices = (unsigned char*)dev((size_t)p * gst_vector_bytes(K.Dp));
+    if (!slices || !K.CB || !K.WI) return HH_ENOMEM;
+  } else {
+    K.Wp = (double*)dev(sizeof(double) * t * 3 * D);
+    if (!K.Wp) return HH_ENOMEM;
+  }
+  if (!K.Hpart || !K.azpart) return HH_ENOMEM;
+  std::vector<double2*> vp(p);
+  for (int a = 0; a < p; ++a) vp[a] = const_cast<double2*>(V) + (size_t)a * D;
+  cudaMemcpyAsync(K.Vptr, vp.data(), sizeof(double2*) * p, cudaMemcpyHostToDevice, E.stream);
+  const int pv = p;
+  cudaMemcpyAsync(K.nV, &pv, sizeof(int), cudaMemcpyHostToDevice, E.stream);
+  int rc;
+  switch (t) {
+    case 1: rc = gs_pass_t<1>(E, K, W, slices); break;
+    case 2: rc = gs_pass_t<2>(E, K, W, slices); break;
+    case 3: rc = gs_pass_t<3>(E, K, W, slices); break;
+    default: rc = gs_pass_t<4>(E, K, W, slices); break;
+  }
+  if (rc) return rc;
+  cudaMemcpyAsync(H_host, K.Hthis, sizeof(double2) * p * t, cudaMemcpyDeviceToHost, E.stream);
+  cudaError_t e = cudaStreamSynchronize(E.stream);
+  if (e != cudaSuccess) return (E.set_cuda_error(e, "Gram-Schmidt pass"), HH_ECUDA);
+  return E.check_device_error("Gram-Schmidt pass");
 }
 
 }  // namespace hh

@@ -72,6 +72,7 @@ def test_default_opts(lib):
     (10.0, 36, 4, 15, {"bcr_depth": 2}),   # R = 9 is odd: no cyclic reduction
     (10.0, 32, 4, 15, {"bcr_depth": -2}),
     (10.0, 32, 4, 15, {"gs_passes": 3}),
+    (10.0, 32, 4, 15, {"gs_tensor": 2}),
     (10.0, 32, 4, 15, {"serve_slots": 0}),
     (10.0, 32, 4, 15, {"serve_slots": 257}),
     (10.0, 1, 1, 15, {}),
@@ -91,6 +92,7 @@ def test_null_arguments(lib):
     assert lib.hh_solve(None, None, None, 1e-8, None) == hh.HH_EINVAL
     assert lib.hh_solve_batch(None, 1, None, None, 1e-8, None) == hh.HH_EINVAL
     assert lib.hh_apply_operator(None, 1, None, None) == hh.HH_EINVAL
+    assert lib.hh_gram_schmidt_pass(None, 1, None, 1, None, None) == hh.HH_EINVAL
     assert lib.hh_get_stats(None, None) == hh.HH_EINVAL
     res = hh.hh_result()
     assert lib.hh_poll(ctypes.c_uint64(987654321), ctypes.byref(res)) == hh.HH_EINVAL

@@ -721,3 +721,71 @@ def test_bf16_solve_converges(k, n, N):
     assert res.rel_res_explicit < 1.5e-6
     assert res.iterations <= ref.iterations + 6, (res.iterations, ref.iterations)
     assert rel(x, ref.x) < 1e-4
+
+
+def _gs_inputs(D, p, t, seed):
+    """Basis columns of unit norm with a few large entries, new columns of very different
+    scales (1, 1e-9, 1e7, and one with a single spike)."""
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((p, D)) + 1j * rng.standard_normal((p, D))
+    V[:, rng.integers(0, D, 5)] *= 40.0
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    W = rng.standard_normal((t, D)) + 1j * rng.standard_normal((t, D))
+    scales = [1.0, 1e-9, 1e7, 1.0][:t]
+    W *= np.array(scales)[:, None]
+    if t == 4:
+        W[3] *= 1e-6
+        W[3, D // 3] = 3.0 + 4.0j
+    W += 0.3 * (V[:t].T @ np.eye(t)).T * np.array(scales)[:, None]  # a part inside the basis
+    return np.ascontiguousarray(V), np.ascontiguousarray(W)
+
+
+@pytest.mark.parametrize("gs_tensor", [1, 0])
+@pytest.mark.parametrize("p,t", [(37, 4), (5, 1), (130, 3)])
+def test_gram_schmidt_pass_fp64_bound(gs_tensor, p, t):
+    """hh_gram_schmidt_pass against an 80-bit (long double) reference of H = V^H W and of
+    W - V H (with the GPU's own H).
+
+    FP64-pipe kernels: every inner product within 4u of sum |v||w| (u = 2^-53; the sums are
+    blocked over threads and CTAs, far inside Higham's gamma_n), every updated entry within
+    2 (p + 4) u of sum_a |v_a||h_ab| + |result| (the worst case of a p-term sum, doubled for
+    the three-multiplication complex product).
+    Tensor cores: the same terms plus the slice truncation, which is relative to each vector's
+    largest entry (|dv| < 2^-55 max|v|, |dw| < 2^-55 max|w|, |dh_ab| < 2^-54 max_a |h_ab| m_a /
+    m_a with m_a = max|v_a|): 2^-53 (max|v| |w|_1 + max|w| |v|_1) per inner product and
+    2^-53 (sum_a m_a |h_ab| + max_a (m_a |h_ab|) sum_a |v_a| / m_a) per updated entry.  A
+    typical-case check on top: every inner product within 1e-15 |v| |w| (the truncation errors
+    have random signs; the worst case is sqrt(2 D) times larger)."""
+    k, n, N = 30.0, 96, 4
+    D = (n + 1) ** 2
+    V, W = _gs_inputs(D, p, t, seed=11 + p)
+    ld = np.longdouble
+    Vr, Vi = V.real.astype(ld), V.imag.astype(ld)
+    Wr, Wi = W.real.astype(ld), W.imag.astype(ld)
+    Hr = Vr @ Wr.T + Vi @ Wi.T          # Re conj(v) w
+    Hi = Vr @ Wi.T - Vi @ Wr.T          # Im conj(v) w
+    aV, aW = np.abs(V), np.abs(W)
+    with hh.Handle(k, n, N, gs_tensor=gs_tensor) as h:
+        W1 = W.copy()
+        H = h.gram_schmidt_pass(V.ravel(), p, W1.ravel(), t)
+        W1 = W1.reshape(t, D)
+    u = 2.0 ** -53
+    mv, mw = aV.max(axis=1), aW.max(axis=1)
+    bound_h = 4 * u * (aV @ aW.T)
+    if gs_tensor:
+        bound_h = bound_h + u * (np.outer(mv, aW.sum(axis=1)) + np.outer(aV.sum(axis=1), mw))
+    err_h = np.abs(H - (Hr.astype(np.float64) + 1j * Hi.astype(np.float64)))
+    assert np.all(err_h <= bound_h), float(np.max(err_h / bound_h))
+    if gs_tensor:
+        nv = np.linalg.norm(V, axis=1)[:, None] * np.linalg.norm(W, axis=1)[None, :]
+        assert np.all(err_h <= 1e-15 * nv), float(np.max(err_h / nv))
+    Hg_r, Hg_i = H.real.astype(ld), H.imag.astype(ld)
+    Ur = Wr - (Vr.T @ Hg_r - Vi.T @ Hg_i).T
+    Ui = Wi - (Vr.T @ Hg_i + Vi.T @ Hg_r).T
+    err_w = np.abs(W1 - (Ur.astype(np.float64) + 1j * Ui.astype(np.float64)))
+    aH = np.abs(H)
+    bound_w = (4 if gs_tensor else 2 * (p + 4)) * u * ((aV.T @ aH).T + np.abs(W1))
+    if gs_tensor:
+        mh = (mv[:, None] * aH).max(axis=0)                       # max_a m_a |h_ab|, per b
+        bound_w = bound_w + u * ((mv @ aH)[:, None] + mh[:, None] * (aV / mv[:, None]).sum(axis=0)[None, :])
+    assert np.all(err_w <= bound_w), float(np.max(err_w / bound_w))
