@@ -594,6 +594,37 @@ def run_candidates(args):
     print(json.dumps({"mode": "candidates", "n": args.n, "strips": args.strips, "ms_per_sweep": out}), flush=True)
 
 
+def run_fd_table(args):
+    """The paper's own setting (five-point finite differences, 8 overlapping strips, the paper's
+    source, tol 1e-6) for Table 1's preconditioner combinations: iterations and GPU times, to set
+    beside the paper's printed counts.  One line per (k, combination)."""
+    import torch
+    import __graft_entry__
+    import paper_2408_11929_gb300 as hh
+    __graft_entry__.build()
+    n, N = args.n, 8
+    for k in (50.0, 100.0):
+        # Section 4's source 3e4 exp(-200 k |x - (1/2, 1/2)|^2): a Gaussian with sigma^2 = 1/(400 k)
+        src = np.array([[0.5, 0.5, (1.0 / (400.0 * k)) ** 0.5, 3e4, 0.0]])
+        for dirs, double in (("LR", True), ("LR+BT", True), ("LR+RL", False), ("LR+RL+BT+TB", False),
+                             ("LR+RL+BT+TB", True)):
+            with hh.Handle(k, n, N, dirs, discretization=hh.HH_DISC_FD, single_sweep=0 if double else 1,
+                           maxit=300) as h:
+                b = torch.from_numpy(h.assemble_rhs(src)).cuda()
+                h.solve(b, tol=1e-6)  # warm-up: graph capture
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                x, res = h.solve(b, tol=1e-6)
+                e1.record()
+                torch.cuda.synchronize()
+                st = h.stats()
+            print(json.dumps({"mode": "fd", "k": k, "n": n, "strips": N, "dirs": dirs,
+                              "sweeps": "double" if double else "single", "iterations": res.iterations,
+                              "status": hh.STATUS_NAMES[res.status], "rel_res_explicit": res.rel_res_explicit,
+                              "setup_ms": st["setup_ms"], "solve_ms": e0.elapsed_time(e1)}), flush=True)
+
+
 def run_sweep_only(args):
     """One direction's double sweep on 4 columns (the column count of one 4-direction solve
     iteration), k = 0.39 n, timed with CUDA events on the launching stream."""
@@ -648,7 +679,7 @@ def main():
     ap.add_argument("--serve-nreq", type=int, default=500, help="requests of the mixed-k serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=0.0,
                     help="--mode serve: Poisson arrival rate (1/s); 0: all at once (capacity)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "solve1", "candidates"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "solve1", "candidates", "fd"],
                     help="sweep: time hh_apply_preconditioner alone (4 columns) -- the profiling case")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--strips", type=int, default=32)
@@ -683,6 +714,9 @@ def main():
                           "rel_res_explicit": res.rel_res_explicit, "kernel_launches": st["kernel_launches"],
                           "bcr_depth": st["bcr_depth"], "sweep_steps": st["sweep_steps"]}),
               flush=True)
+        return
+    if args.mode == "fd":
+        run_fd_table(args)
         return
     if args.mode == "serve":
         import __graft_entry__

@@ -57,6 +57,7 @@ typedef enum {
 enum { HH_DIR_LR = 1, HH_DIR_RL = 2, HH_DIR_BT = 4, HH_DIR_TB = 8 };
 enum { HH_PREC_FP64 = 0, HH_PREC_FP32 = 1, HH_PREC_BF16 = 2 };  /* precision of factors + sweeps */
 enum { HH_SCHEME_AUTO = 0, HH_SCHEME_CROSS = 1, HH_SCHEME_SUM = 2 };
+enum { HH_DISC_P1 = 0, HH_DISC_FD = 1 };  /* hh_opts.discretization */
 
 typedef struct {
   int precision;          /* HH_PREC_FP64 (default) or HH_PREC_FP32: complex64 strip factors and
@@ -132,6 +133,11 @@ typedef struct {
                              coefficients are applied in FP64 and the FP64 second pass corrects
                              them, so H, the orthogonality of V and A Z = V H stay FP64-accurate);
                              0: both passes in FP64 */
+  int discretization;     /* HH_DISC_P1 (default): P1 finite elements on the right-triangle mesh and
+                             non-overlapping strips; HH_DISC_FD: the paper's own setting (Section 4),
+                             five-point finite differences with ghost-node Robin rows and strips
+                             overlapping by 2h that exchange Robin data, every node taking the most
+                             recent subdomain solve; FP64 only (HH_PREC_FP64), sweeps on the CUDA cores */
   int gs_tensor;          /* 1 (default): the inner products and updates of Gram-Schmidt against the
                              basis run on the tensor cores as exact integer products of 7-bit slices
                              of the FP64 data (FP64-accurate; about 64 more bytes of device memory

@@ -23,6 +23,7 @@ HH_DIR_LR, HH_DIR_RL, HH_DIR_BT, HH_DIR_TB = 1, 2, 4, 8
 DIR_BITS = {"LR": HH_DIR_LR, "RL": HH_DIR_RL, "BT": HH_DIR_BT, "TB": HH_DIR_TB}
 HH_PREC_FP64, HH_PREC_FP32, HH_PREC_BF16 = 0, 1, 2
 HH_SCHEME_AUTO, HH_SCHEME_CROSS, HH_SCHEME_SUM = 0, 1, 2
+HH_DISC_P1, HH_DISC_FD = 0, 1
 
 
 class hh_opts(ctypes.Structure):
@@ -33,7 +34,7 @@ class hh_opts(ctypes.Structure):
                 ("tensor_cores", ctypes.c_int), ("autotune", ctypes.c_int), ("fuse_chains", ctypes.c_int),
                 ("overlap_steps", ctypes.c_int), ("interface_form", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("gs_first_fp32", ctypes.c_int),
-                ("gs_tensor", ctypes.c_int)]
+                ("discretization", ctypes.c_int), ("gs_tensor", ctypes.c_int)]
 
 
 class hh_result(ctypes.Structure):

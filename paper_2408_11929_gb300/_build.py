@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libhh.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["setup.cu", "sweep.cu", "group.cu", "persist.cu", "lowp.cu", "gs_tc.cu", "krylov.cu", "api.cu", "noalloc.cu", "server.cu"]
+SOURCES = ["setup.cu", "sweep.cu", "group.cu", "persist.cu", "lowp.cu", "gs_tc.cu", "fd.cu", "krylov.cu", "api.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -138,6 +138,10 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
             HH_EINVAL);
   if (opts.gs_passes != 1 && opts.gs_passes != 2) return (set_error("gs_passes must be 1 or 2"), HH_EINVAL);
   if (opts.gs_tensor != 0 && opts.gs_tensor != 1) return (set_error("gs_tensor must be 0 or 1"), HH_EINVAL);
+  if (opts.discretization != HH_DISC_P1 && opts.discretization != HH_DISC_FD)
+    return (set_error("discretization must be HH_DISC_P1 or HH_DISC_FD"), HH_EINVAL);
+  if (opts.discretization == HH_DISC_FD && opts.precision != HH_PREC_FP64)
+    return (set_error("the five-point mode (HH_DISC_FD) runs in FP64 only"), HH_EINVAL);
   if (opts.serve_slots < 1 || opts.serve_slots > 256) return (set_error("serve_slots must be in 1..256"), HH_EINVAL);
   if (opts.interface_form != 0 && opts.interface_form != 1) return (set_error("interface_form must be 0 or 1"), HH_EINVAL);
   if (opts.timeout_cycles <= 0) opts.timeout_cycles = 4000000000LL;
@@ -185,6 +189,26 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
     if (rc) return rc;
   }
 
+  if (opts.discretization == HH_DISC_FD) {
+    // the paper's five-point scheme and overlapping strips: its own inverses and sweeps (fd.cu)
+    if (dmalloc((void**)&bar, BAR_BYTES) || dmalloc((void**)&err, 64)) return HH_ENOMEM;
+    cudaMemsetAsync(bar, 0, BAR_BYTES, stream);
+    cudaMemsetAsync(err, 0, 64, stream);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, stream);
+    const int rc = fd_setup(*this);
+    cudaEventRecord(b, stream);
+    cudaEventSynchronize(b);
+    float t_ms = 0;
+    cudaEventElapsedTime(&t_ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    setup_ms_total = t_ms;
+    collect_ticks();
+    return rc;
+  }
   const size_t fbytes = (size_t)factor_blocks() * m * ldf * sweep_elem();
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -239,6 +263,7 @@ Engine::~Engine() {
   sweep_graphs.clear();
   collect_ticks();
   for (auto ev : event_pool) cudaEventDestroy(ev);
+  fd_free(*this);
   dfree(factors); dfree(bar); dfree(err);
   dfree(w_rin); dfree(w_v); dfree(w_w); dfree(w_partial); dfree(w_t0); dfree(w_t1);
   dfree(prog_tasks);
@@ -547,6 +572,7 @@ hh_status hh_apply_preconditioner(hh_handle* h, uint32_t dir, int ncols, const d
 hh_status hh_get_factor(hh_handle* h, int j, double* out) {
   if (!h || !out) return (set_error("bad arguments"), HH_EINVAL);
   Engine& E = *h->E;
+  if (E.fd) return (set_error("the five-point mode keeps no P1 strip factors"), HH_EINVAL);
   if (j < 0 || j > E.R) return (set_error("factor index out of range"), HH_EINVAL);
   std::lock_guard<std::mutex> lk(E.solve_mu);
   cudaSetDevice(E.device);
@@ -600,6 +626,10 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->kernel_launches = E.kernel_launches;
   st->factor_bytes = (int64_t)E.factor_blocks() * E.m * E.ldf * (int64_t)E.sweep_elem();
   st->factor_blocks = E.factor_blocks();
+  if (E.fd) {  // the five-point mode: its chain of line-block inverses and the top ones
+    st->factor_blocks = fd_blocks(E);
+    st->factor_bytes = (int64_t)st->factor_blocks * E.m * E.ldf * (int64_t)sizeof(double2);
+  }
   st->m = E.m;
   st->ldf = E.ldf;
   st->columns = E.last_columns;

@@ -96,6 +96,16 @@ int max_bcr_depth(int R);
 enum DirCode { DC_BT = 0, DC_TB = 1, DC_LR = 2, DC_RL = 3 };
 
 class SlotSolver;  // continuous-batching MPGMRES driver (krylov.cu)
+struct FdState;    // five-point finite differences with overlapping strips (fd.cu)
+class Engine;
+int fd_setup(Engine& E);
+void fd_free(Engine& E);
+int fd_precondition(Engine& E, const double2* const* src, const double* scale, int C, int t, int4 codes,
+                    double2* const* dst, bool single);
+void fd_operator(Engine& E, const double2* const* xcol, double2* const* ycol, int ncols);
+void fd_load(Engine& E, const double* dsrc, int nsrc, double2* b);
+int fd_reserve(Engine& E, int C);  // sweep buffers for C columns, before any graph capture
+int fd_blocks(const Engine& E);     // stored m x m inverses
 
 class Engine {
  public:
@@ -110,6 +120,9 @@ class Engine {
   Coef coef{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // hh_opts.discretization = HH_DISC_FD: the paper's five-point scheme and overlapping strips
+  // (fd.cu); none of the P1 strip factors or sweep programs below exist then
+  FdState* fd = nullptr;
 
   // device buffers
   void* factors = nullptr;  // R+3 blocks of m x ldf complex: F_0..F_R, G, K (setup.cu)

@@ -1176,7 +1176,7 @@ struct SlotSolver::Impl {
     for (int r = 0; r < S; ++r) h_done[r] = 1;
     cudaMemcpyAsync(K.done, h_done, sizeof(int) * S, cudaMemcpyHostToDevice, E.stream);
     slots.assign(S, Slot());
-    if (E.ensure_sweep_ws(S * t)) return HH_ENOMEM;
+    if (E.fd ? fd_reserve(E, S * t) : E.ensure_sweep_ws(S * t)) return HH_ENOMEM;
     int* cp = &codes.x;
     for (int d = 0; d < 4; ++d) cp[d] = d < t ? E.dir_codes[d] : 0;
     cudaError_t e = cudaStreamSynchronize(E.stream);
@@ -1344,16 +1344,27 @@ struct SlotSolver::Impl {
     const int C = nact * t;
     gather_tables_kernel<<<1, 256, 0, E.stream>>>(K, d_act, nact, T, W);
     E.count_launch();
-    launch_pack(E, T.src, T.scale, C, t, codes, E.w_rin);
-    if (timed) E.sample_next_sweep = E.opts.profile != 0;
-    int rc = timed ? E.run_sweep(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0)
-                   : E.sweep_inline(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0);
-    if (rc) return rc;
-    launch_unpack_tab(E, E.w_v, C, t, codes, T.zdst);
-    if (timed) E.tick_begin(Engine::K_SPMV);
-    spmv_tab_kernel<<<dim3(std::max(1u, E.grid_for(D * C) / C), C), 256, 0, E.stream>>>(T.zdst, T.wdst, C, E.coef);
-    E.count_launch();
-    if (timed) E.tick_end(Engine::K_SPMV, 2.0 * C * D * 16.0, 0);
+    if (E.fd) {
+      // the paper's five-point scheme: overlapping-strip sweeps and the five-point operator
+      if (timed) E.tick_begin(Engine::K_SWEEP);
+      const int frc = fd_precondition(E, T.src, T.scale, C, t, codes, T.zdst, E.opts.single_sweep != 0);
+      if (timed) E.tick_end(Engine::K_SWEEP, 0, 0);
+      if (frc) return frc;
+      if (timed) E.tick_begin(Engine::K_SPMV);
+      fd_operator(E, (const double2* const*)T.zdst, T.wdst, C);
+      if (timed) E.tick_end(Engine::K_SPMV, 2.0 * C * D * 16.0, 0);
+    } else {
+      launch_pack(E, T.src, T.scale, C, t, codes, E.w_rin);
+      if (timed) E.sample_next_sweep = E.opts.profile != 0;
+      int rc = timed ? E.run_sweep(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0)
+                     : E.sweep_inline(E.w_rin, E.w_v, E.w_w, C, E.opts.single_sweep != 0);
+      if (rc) return rc;
+      launch_unpack_tab(E, E.w_v, C, t, codes, T.zdst);
+      if (timed) E.tick_begin(Engine::K_SPMV);
+      spmv_tab_kernel<<<dim3(std::max(1u, E.grid_for(D * C) / C), C), 256, 0, E.stream>>>(T.zdst, T.wdst, C, E.coef);
+      E.count_launch();
+      if (timed) E.tick_end(Engine::K_SPMV, 2.0 * C * D * 16.0, 0);
+    }
     if (timed) E.tick_begin(Engine::K_GS);
     const bool tick_dot = timed;
     switch (t) {
@@ -1399,7 +1410,7 @@ struct SlotSolver::Impl {
       }
     if (!exec) {
       const int C = nact * t;
-      int rc = E.ensure_tuned(C);  // tuning runs kernels and synchronises: not inside a capture
+      int rc = E.fd ? HH_OK : E.ensure_tuned(C);  // tuning runs kernels and synchronises: not in a capture
       if (rc) return rc;
       cudaGraph_t graph = nullptr;
       const int64_t before = E.kernel_launches;
@@ -1451,8 +1462,11 @@ struct SlotSolver::Impl {
     cudaFuncSetAttribute((const void*)xsol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsmem);
     xsol_kernel<<<dim3(K.GX, S), 256, xsmem, E.stream>>>(K);
     E.tick_begin(Engine::K_SPMV);
-    spmv_tab_kernel<<<dim3(std::max(1u, E.grid_for(D * nfin) / nfin), nfin), 256, 0, E.stream>>>(
-        (const double2* const*)T.zdst, T.wdst, nfin, E.coef);
+    if (E.fd)
+      fd_operator(E, (const double2* const*)T.zdst, T.wdst, nfin);
+    else
+      spmv_tab_kernel<<<dim3(std::max(1u, E.grid_for(D * nfin) / nfin), nfin), 256, 0, E.stream>>>(
+          (const double2* const*)T.zdst, T.wdst, nfin, E.coef);
     E.tick_end(Engine::K_SPMV, 2.0 * nfin * D * 16.0, 0);
     resid_part_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K, W);
     resid_final_kernel<<<S, 32, 0, E.stream>>>(K);
@@ -1548,10 +1562,33 @@ int Engine::solve_batch_dev(int nrhs, const double2* b, double2* x, double tol, 
   return worst;
 }
 
+// device tables of column pointers base + c D (the five-point kernels take tables), freed by
+// the caller
+static int column_table(Engine& E, const double2* base, int ncols, const double2*** out) {
+  const size_t D = (size_t)E.m * E.m;
+  std::vector<const double2*> hp(ncols);
+  for (int c = 0; c < ncols; ++c) hp[c] = base + (size_t)c * D;
+  if (E.dmalloc((void**)out, sizeof(void*) * ncols)) return HH_ENOMEM;
+  cudaMemcpyAsync(*out, hp.data(), sizeof(void*) * ncols, cudaMemcpyHostToDevice, E.stream);
+  return HH_OK;
+}
+
 int Engine::apply_operator(int ncols, const double2* x, double2* y) {
   const size_t D = (size_t)m * m;
   tick_begin(K_SPMV);
-  spmv_kernel<<<dim3(std::max(1u, grid_for(D * ncols) / ncols), ncols), 256, 0, stream>>>(x, y, ncols, coef);
+  if (fd) {
+    const double2 **xt = nullptr, **yt = nullptr;
+    if (column_table(*this, x, ncols, &xt) || column_table(*this, y, ncols, &yt)) {
+      dfree(xt);
+      return HH_ENOMEM;
+    }
+    fd_operator(*this, xt, (double2* const*)yt, ncols);
+    cudaStreamSynchronize(stream);
+    dfree(xt);
+    dfree(yt);
+  } else {
+    spmv_kernel<<<dim3(std::max(1u, grid_for(D * ncols) / ncols), ncols), 256, 0, stream>>>(x, y, ncols, coef);
+  }
   count_launch();
   tick_end(K_SPMV, 2.0 * ncols * D * 16.0, 0);
   cudaError_t e = cudaStreamSynchronize(stream);
@@ -1569,9 +1606,13 @@ int Engine::assemble_rhs(int nsrc, const double* src_host, double2* rhs) {
     return HH_ENOMEM;
   }
   if (nsrc > 0) cudaMemcpyAsync(dsrc, src_host, sizeof(double) * 5 * nsrc, cudaMemcpyHostToDevice, stream);
-  gauss_nodal_kernel<<<grid_for(D), 256, 0, stream>>>(dsrc, nsrc, n, f);
-  mass_neg_kernel<<<grid_for(D), 256, 0, stream>>>(f, rhs, n);
-  count_launch(2);
+  if (fd) {
+    fd_load(*this, dsrc, nsrc, rhs);  // b = s (-h^2 f), the five-point load vector
+  } else {
+    gauss_nodal_kernel<<<grid_for(D), 256, 0, stream>>>(dsrc, nsrc, n, f);
+    mass_neg_kernel<<<grid_for(D), 256, 0, stream>>>(f, rhs, n);
+    count_launch(2);
+  }
   cudaError_t e = cudaStreamSynchronize(stream);
   dfree(dsrc);
   dfree(f);
@@ -1581,6 +1622,24 @@ int Engine::assemble_rhs(int nsrc, const double* src_host, double2* rhs) {
 
 int Engine::apply_preconditioner_dev(int dcode, int ncols, const double2* r, double2* z, bool single) {
   const size_t D = (size_t)m * m;
+  if (fd) {
+    const double2 **rt = nullptr, **zt = nullptr;
+    if (column_table(*this, r, ncols, &rt) || column_table(*this, z, ncols, &zt)) {
+      dfree(rt);
+      return HH_ENOMEM;
+    }
+    tick_begin(K_SWEEP);
+    const int4 codes = make_int4(dcode, dcode, dcode, dcode);
+    int rc = fd_precondition(*this, rt, nullptr, ncols, 1, codes, (double2* const*)zt, single);
+    tick_end(K_SWEEP, 0, 0);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    dfree(rt);
+    dfree(zt);
+    collect_ticks();
+    if (rc) return rc;
+    if (e != cudaSuccess) { set_cuda_error(e, "apply_preconditioner"); return HH_ECUDA; }
+    return check_device_error("five-point sweep");
+  }
   if (ensure_sweep_ws(ncols)) return HH_ENOMEM;
   std::vector<const double2*> hp(ncols);
   std::vector<double> hs(ncols, 1.0);

@@ -148,6 +148,7 @@ extern "C" hh_status hh_apply_preconditioner_noalloc(hh_handle* h, uint32_t dir,
     default: return (set_error("dir must be exactly one HH_DIR_* bit"), HH_EINVAL);
   }
   Engine& E = *h->E;
+  if (E.fd) return (set_error("the no-allocation entry point serves the P1 mode only"), HH_EINVAL);
   std::lock_guard<std::mutex> lk(E.solve_mu);
   cudaSetDevice(E.device);
   if (!is_device_pointer(r) || !is_device_pointer(z))

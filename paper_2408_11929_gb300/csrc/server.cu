@@ -273,7 +273,8 @@ hh_status hh_server_create(const hh_opts* opts, size_t mem_budget, hh_server** o
   auto* s = new hh_server();
   hh_default_opts(&s->opts);
   if (opts) s->opts = *opts;
-  if (s->opts.serve_slots < 1 || s->opts.serve_slots > 256 || s->opts.maxit < 1) {
+  if (s->opts.serve_slots < 1 || s->opts.serve_slots > 256 || s->opts.maxit < 1 ||
+      s->opts.discretization != HH_DISC_P1) {
     delete s;
     return (hh::set_error("invalid options"), HH_EINVAL);
   }

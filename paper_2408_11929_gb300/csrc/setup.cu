@@ -19,6 +19,7 @@
 // and stores G = Y_{R-1} L and K = Y_{R-1}^T U (D is complex symmetric, so
 // D^{-1}[0, R-1] = Y_{R-1}^T) as blocks R+1 and R+2.
 #include <cstdio>
+#include <functional>
 #include <vector>
 
 #include <cmath>
@@ -667,6 +668,25 @@ struct BlockInverter {
     return E.check_device_error("cyclic-reduction setup");
   }
 };
+
+// out[q] = S_q^{-1} for q = 0 .. count-1 by pivoted Gauss-Jordan in FP64, S_q formed by
+// form(q, S) into one scratch block just before its inversion (it may read out[0 .. q-1]): the
+// strip inverses of the five-point mode (fd.cu)
+int invert_chain_fp64(Engine& E, int count, const std::function<int(int, double2*)>& form, double2* const* out) {
+  BlockInverter<double> inv(E);
+  if (inv.alloc()) return HH_ENOMEM;
+  double2* S = nullptr;
+  if (E.dmalloc((void**)&S, (size_t)E.m * E.ldf * sizeof(double2))) return HH_ENOMEM;
+  cudaMemsetAsync(S, 0, (size_t)E.m * E.ldf * sizeof(double2), E.stream);
+  int rc = HH_OK;
+  for (int q = 0; q < count && rc == HH_OK; ++q) {
+    rc = form(q, S);
+    if (rc == HH_OK) rc = inv.invert(S, nullptr, out[q]);
+  }
+  cudaStreamSynchronize(E.stream);
+  E.dfree(S);
+  return rc;
+}
 
 // Blocks of block cyclic reduction of the strip solves (see append_bcr_f1 in sweep.cu).  The
 // level-0 system of a strip is block tridiagonal over its node lines: diagonal blocks D_BOT

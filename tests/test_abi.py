@@ -73,6 +73,8 @@ def test_default_opts(lib):
     (10.0, 32, 4, 15, {"bcr_depth": -2}),
     (10.0, 32, 4, 15, {"gs_passes": 3}),
     (10.0, 32, 4, 15, {"gs_tensor": 2}),
+    (10.0, 32, 4, 15, {"discretization": 2}),
+    (10.0, 32, 4, 15, {"discretization": 1, "precision": 1}),   # the five-point mode is FP64 only
     (10.0, 32, 4, 15, {"serve_slots": 0}),
     (10.0, 32, 4, 15, {"serve_slots": 257}),
     (10.0, 1, 1, 15, {}),
