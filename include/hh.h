@@ -138,6 +138,10 @@ typedef struct {
                              five-point finite differences with ghost-node Robin rows and strips
                              overlapping by 2h that exchange Robin data, every node taking the most
                              recent subdomain solve; FP64 only (HH_PREC_FP64), sweeps on the CUDA cores */
+  int group_wide_tiles;   /* complex64 tensor-core sweeps: 1 (default): a grouped step whose tasks are
+                             wider than 64 columns and at most 128 (the one-shot corrections of
+                             interface form 1 at one right-hand side) runs with 128-column tiles,
+                             reading each factor tile once; 0: the autotuned line-step shape */
   int gs_tensor;          /* 1 (default): the inner products and updates of Gram-Schmidt against the
                              basis run on the tensor cores as exact integer products of 7-bit slices
                              of the FP64 data (FP64-accurate; about 64 more bytes of device memory

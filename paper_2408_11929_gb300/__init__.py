@@ -34,7 +34,7 @@ class hh_opts(ctypes.Structure):
                 ("tensor_cores", ctypes.c_int), ("autotune", ctypes.c_int), ("fuse_chains", ctypes.c_int),
                 ("overlap_steps", ctypes.c_int), ("interface_form", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("gs_first_fp32", ctypes.c_int),
-                ("discretization", ctypes.c_int), ("gs_tensor", ctypes.c_int)]
+                ("discretization", ctypes.c_int), ("group_wide_tiles", ctypes.c_int), ("gs_tensor", ctypes.c_int)]
 
 
 class hh_result(ctypes.Structure):

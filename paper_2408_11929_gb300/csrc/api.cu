@@ -484,6 +484,7 @@ void hh_default_opts(hh_opts* o) {
   o->persistent = 0;
   o->gs_first_fp32 = 1;
   o->gs_tensor = 1;
+  o->group_wide_tiles = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {

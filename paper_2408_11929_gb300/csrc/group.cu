@@ -605,6 +605,16 @@ static cudaError_t launch_tc_group_shape(Engine& E, const SweepPhase& ph, const 
 }
 
 cudaError_t launch_tc_group(Engine& E, int shape, const SweepPhase& ph, const GArrays& arrs, int C) {
+  // a task wider than one 64-column tile but within one 128-column tile: the 128-column shape
+  // reads each of its factor tiles once instead of once per column tile
+  if (shape == 0 && E.opts.group_wide_tiles) {
+    int wmin = 1 << 30, wmax = 0;
+    for (const GTask& g : ph.tasks) {
+      wmin = std::min(wmin, g.ns * C);
+      wmax = std::max(wmax, g.ns * C);
+    }
+    if (wmin > tc::Wide::BNC && wmax <= tc::Huge::BNC) shape = 2;
+  }
   if (shape == 1) return launch_tc_group_shape<tc::Narrow>(E, ph, arrs, C);
   if (shape == 2) return launch_tc_group_shape<tc::Huge>(E, ph, arrs, C);
   return launch_tc_group_shape<tc::Wide>(E, ph, arrs, C);
