@@ -4,8 +4,8 @@ tests/golden/make_golden.py from oracle/ only).
 * k = 100, n = 256, 16 strips, 8 right-hand sides, FP64: the same iteration count as the
   oracle for every right-hand side and the solution within 1e-10 relative (sampled nodes).
 * k = 200, n = 512, 16 strips, 64 right-hand sides in one batch, complex64 sweeps: tol 1e-6
-  reached within the oracle's iterations + 2, and the solution close to the oracle's
-  solution at tol 1e-10 (sampled nodes).
+  reached within the oracle's iterations + 2 for every right-hand side, and every solution to
+  tol 1e-7 within 1e-5 of the oracle's tight solution (sampled nodes).
 * k = 400, n = 1024, 32 strips: the FP64 GPU path with the oracle's iteration count and its
   solution within 1e-10 (sampled nodes); the complex64 path within the oracle's iterations + 2
   at tol 1e-6, and its solution within 1e-5 of the oracle's tight solution.
@@ -43,14 +43,6 @@ def built():
     __graft_entry__.build()
 
 
-def stop_err(g, r):
-    """The oracle's own error from stopping at the workload tolerance (sampled nodes)."""
-    gr = g["rhs"][str(r)]
-    x = np.array(gr["x_sample_re"]) + 1j * np.array(gr["x_sample_im"])
-    t = np.array(gr["tight_x_sample_re"]) + 1j * np.array(gr["tight_x_sample_im"])
-    return np.linalg.norm(x - t) / np.linalg.norm(t)
-
-
 def sample_err(x, g, r, tight=False):
     idx = np.array(g["sample_nodes"])
     pre = "tight_" if tight else ""
@@ -74,20 +66,25 @@ def test_k100_fp64_eight_rhs():
 
 
 def test_k200_fp32_batch_of_64():
+    """All 64 right-hand sides in one batch: at the workload tolerance, the oracle's iterations + 2
+    and the explicit residual at the tolerance; solved to 1e-7, every solution within 1e-5 of the
+    oracle's tight solution (sampled nodes), as at k = 400."""
     w = hh_inputs.workload("k200_n512_b64")
     g = golden(w.name)
+    assert len(g["rhs"]) == w.nrhs
     torch = pytest.importorskip("torch")
     with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32") as h:
         B = torch.cat([torch.from_numpy(h.assemble_rhs(s)) for s in w.sources]).cuda()
         X, res = h.solve_batch(B, w.nrhs, tol=w.tol)
-    X = X.reshape(w.nrhs, -1).cpu().numpy()
-    for r in (int(k) for k in g["rhs"]):
+        X7, res7 = h.solve_batch(B, w.nrhs, tol=1e-7)
+    X7 = X7.reshape(w.nrhs, -1).cpu().numpy()
+    for r in range(w.nrhs):
         gr = g["rhs"][str(r)]
         assert res[r].status == hh.HH_OK
         assert res[r].iterations <= gr["iterations"] + 2, r
         assert res[r].rel_res_explicit < 1.05 * w.tol, r
-        assert sample_err(X[r], g, r, tight=True) < 3 * stop_err(g, r), r
-    assert all(q.status == hh.HH_OK for q in res)
+        assert res7[r].status == hh.HH_OK
+        assert sample_err(X7[r], g, r, tight=True) < 1e-5, r
 
 
 def test_k400_fp32():
