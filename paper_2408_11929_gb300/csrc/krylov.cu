@@ -548,6 +548,15 @@ __global__ void __launch_bounds__(256) gs_update_kernel(KState S, double2* __res
   }
 }
 
+// acc -= a b in four FP64 FMAs (the QR kernel is bound by the FP64 pipe; a product followed by a
+// subtraction takes six operations)
+__device__ __forceinline__ void cfms(double2& acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
 // Sum TT complex values (v[2q], v[2q+1]) over the CTAs of one right-hand side of qr_kernel:
 // per-CTA partials into qpart[parity], grid barrier, then every CTA adds the GQ partials with
 // all its threads in one fixed order, so that all CTAs hold bit-identical sums (red_out).
@@ -690,7 +699,7 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
             double2 wv = w[g];
 #pragma unroll
             for (int q = 0; q < TT - 1; ++q)
-              if (q < acc) wv = csub(wv, cmul(cur[q], Vr[q * D + g]));
+              if (q < acc) cfms(wv, cur[q], Vr[q * D + g]);
             w[g] = wv;
 #pragma unroll
             for (int q = 0; q < TT - 1; ++q)
@@ -719,7 +728,7 @@ __global__ void __launch_bounds__(256) qr_kernel(KState S, double2* __restrict__
           if (acc > 0) {
 #pragma unroll
             for (int q = 0; q < TT - 1; ++q)
-              if (q < acc) wv = csub(wv, cmul(cur[q], Vr[q * D + g]));
+              if (q < acc) cfms(wv, cur[q], Vr[q * D + g]);
             w[g] = wv;
           }
           v[0] += cabs2(wv);
