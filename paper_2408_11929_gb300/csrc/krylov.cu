@@ -798,19 +798,28 @@ __device__ void givens(double2 a, double2 b, double& c, double2& s) {
 
 // One warp per slot.  The new Hessenberg columns, the stored rotations (when they fit, `stage`)
 // and the block R are loaded by all lanes into shared memory (one memory latency instead of
-// one per element); lane 0 then applies the rotations in order, which is inherently sequential.
-__global__ void hess_kernel(KState S, int stage) {
+// one per element).  The rotations of earlier iterations act on every new column alike, so lane
+// j applies them to column j (the columns in parallel); then lane 0 takes the columns in order,
+// applying the rotations the block's earlier columns generated and generating the column's own
+// (inherently sequential).  Each column sees the same operations in the same order as one lane
+// applying all of them.
+// mode bit 0: the columns in shared memory (else in S.hcol); bit 1: the rotations staged there too
+__global__ void hess_kernel(KState S, int mode) {
+  const bool cols_smem = (mode & 1) != 0, stage = (mode & 2) != 0;
   const int r = blockIdx.x, lane = threadIdx.x;
   // the basis vectors this step adds, for the slicing of the tensor-core Gram-Schmidt: none
   // unless the step ends normally below
   if (S.gst && lane == 0) S.vnew1[r] = S.vnew0[r];
   if (S.done[r]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* col = reinterpret_cast<double2*>(smem_raw);  // maxZ + 2
-  // rotations: staged copies, or the stored arrays themselves
-  double2* snS = stage ? col + S.maxZ + 2 : S.sn + (size_t)r * S.maxZ;
-  double* csS = stage ? reinterpret_cast<double*>(col + 2 * S.maxZ + 2) : S.cs + (size_t)r * S.maxZ;
   const int t = S.t;
+  const int ld = S.maxZ + 2;
+  // the t new Hessenberg columns (maxZ + 2 entries each), then the rotations: staged copies, or
+  // the stored arrays themselves
+  double2* cols = cols_smem ? reinterpret_cast<double2*>(smem_raw) : S.hcol + (size_t)r * t * ld;
+  double2* rot = reinterpret_cast<double2*>(smem_raw) + (cols_smem ? (size_t)t * ld : 0);
+  double2* snS = stage ? rot : S.sn + (size_t)r * S.maxZ;
+  double* csS = stage ? reinterpret_cast<double*>(rot + S.maxZ) : S.cs + (size_t)r * S.maxZ;
   const int nold = S.nV[r], nacc = S.nacc[r];
   const size_t D = S.D;
   double2* g = S.g + (size_t)r * (S.maxZ + 1);
@@ -822,6 +831,7 @@ __global__ void hess_kernel(KState S, int stage) {
     return;
   }
   int nZ = S.nZ[r];
+  const int nZ0 = nZ;
   if (stage)
     for (int i = lane; i < nZ; i += blockDim.x) {
       csS[i] = S.cs[(size_t)r * S.maxZ + i];
@@ -830,25 +840,43 @@ __global__ void hess_kernel(KState S, int stage) {
   for (int j = 0; j < t; ++j) {
     const int pos = S.amap[r * t + j];
     if (pos < 0) continue;
-    const int c = nZ;
-    const int len = nold + pos + 1;  // == c + 2
-    for (int i = lane; i < nold; i += blockDim.x) col[i] = S.Hacc[((size_t)r * S.maxV + i) * t + j];
-    for (int q = lane; q <= pos; q += blockDim.x) col[nold + q] = S.Rnew[(size_t)r * t * t + q * t + j];
-    for (int i = len + lane; i < c + 2; i += blockDim.x) col[i] = make_double2(0, 0);
-    __syncwarp();
+    double2* cj = cols + (size_t)j * ld;
+    for (int i = lane; i < nold; i += blockDim.x) cj[i] = S.Hacc[((size_t)r * S.maxV + i) * t + j];
+    for (int q = lane; q <= pos; q += blockDim.x) cj[nold + q] = S.Rnew[(size_t)r * t * t + q * t + j];
+  }
+  __syncwarp();
+  // the rotations of earlier iterations, the same for every new column: one lane per column
+  if (lane < t && S.amap[r * t + lane] >= 0) {
+    double2* cj = cols + (size_t)lane * ld;
+    for (int i = 0; i < nZ0; ++i) {
+      const double cs = csS[i];
+      const double2 sn = snS[i];
+      const double2 a0 = cj[i], a1 = cj[i + 1];
+      cj[i] = cadd(cscale(a0, cs), cmul(sn, a1));
+      const double2 msc = make_double2(-sn.x, sn.y);  // -conj(sn)
+      cj[i + 1] = cadd(cmul(msc, a0), cscale(a1, cs));
+    }
+  }
+  __syncwarp();
+  for (int j = 0; j < t; ++j) {
+    const int pos = S.amap[r * t + j];
+    if (pos < 0) continue;
+    const int c = nZ;  // == nold + pos - 1: this column's entries 0 .. c + 1
+    double2* cj = cols + (size_t)j * ld;
     if (lane == 0) {
-      for (int i = 0; i < c; ++i) {
+      // the rotations this iteration's earlier columns generated, then this column's own
+      for (int i = nZ0; i < c; ++i) {
         const double cs = csS[i];
         const double2 sn = snS[i];
-        const double2 a0 = col[i], a1 = col[i + 1];
-        col[i] = cadd(cscale(a0, cs), cmul(sn, a1));
-        const double2 msc = make_double2(-sn.x, sn.y);  // -conj(sn)
-        col[i + 1] = cadd(cmul(msc, a0), cscale(a1, cs));
+        const double2 a0 = cj[i], a1 = cj[i + 1];
+        cj[i] = cadd(cscale(a0, cs), cmul(sn, a1));
+        const double2 msc = make_double2(-sn.x, sn.y);
+        cj[i + 1] = cadd(cmul(msc, a0), cscale(a1, cs));
       }
       double cs;
       double2 sn;
-      givens(col[c], col[c + 1], cs, sn);
-      col[c] = cadd(cscale(col[c], cs), cmul(sn, col[c + 1]));
+      givens(cj[c], cj[c + 1], cs, sn);
+      cj[c] = cadd(cscale(cj[c], cs), cmul(sn, cj[c + 1]));
       csS[c] = cs;
       snS[c] = sn;
       if (stage) {
@@ -862,7 +890,7 @@ __global__ void hess_kernel(KState S, int stage) {
     }
     __syncwarp();
     double2* Rc = S.Rrot + (size_t)r * ((size_t)S.maxZ * (S.maxZ + 1) / 2) + (size_t)c * (c + 1) / 2;
-    for (int i = lane; i <= c; i += blockDim.x) Rc[i] = col[i];
+    for (int i = lane; i <= c; i += blockDim.x) Rc[i] = cj[i];
     __syncwarp();
     nZ = c + 1;
   }
@@ -1139,6 +1167,7 @@ struct SlotSolver::Impl {
     K.g = dev<double2>((size_t)S * (K.maxZ + 1));
     K.Rrot = dev<double2>((size_t)S * ((size_t)K.maxZ * (K.maxZ + 1) / 2));
     K.y = dev<double2>((size_t)S * K.maxZ); K.qpart = dev<double2>((size_t)2 * S * K.GQ * 4);
+    K.hcol = dev<double2>((size_t)S * t * (K.maxZ + 2));
     K.sbuf = dev<double2>((size_t)S * D); K.V0 = dev<double2>((size_t)S * D);
     K.srcptr = (const double2**)dev<double2*>((size_t)S * t); K.scale = dev<double>((size_t)S * t);
     K.res_exp = dev<double>(S);
@@ -1393,12 +1422,13 @@ struct SlotSolver::Impl {
                  K.passes * 16.0 * nv * t * D);
     if (ce != cudaSuccess) return HH_ECUDA;
     // the Hessenberg column, and the rotations too when they fit in shared memory
-    const size_t hcol = (size_t)(K.maxZ + 2) * sizeof(double2);
+    const size_t hcol = (size_t)t * (K.maxZ + 2) * sizeof(double2);
     const size_t hrot = (size_t)K.maxZ * (sizeof(double2) + sizeof(double));
-    const int stage = hcol + hrot <= 200 * 1024;
-    const size_t hsmem = hcol + (stage ? hrot : 0);
+    const int cols_smem = hcol <= 160 * 1024;
+    const int stage = (cols_smem ? hcol : 0) + hrot <= 200 * 1024;
+    const size_t hsmem = (cols_smem ? hcol : 0) + (stage ? hrot : 0);
     cudaFuncSetAttribute((const void*)hess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
-    hess_kernel<<<S, 32, hsmem, E.stream>>>(K, stage);
+    hess_kernel<<<S, 32, hsmem, E.stream>>>(K, cols_smem | (stage << 1));
     source_sum_kernel<<<dim3(K.GX, S), 256, 0, E.stream>>>(K);
     source_final_kernel<<<S, 32, 0, E.stream>>>(K);
     E.count_launch(3);

@@ -23,6 +23,7 @@ struct KState {
   const double2** srcptr;
   double* scale;
   double* res_exp;
+  double2* hcol;           // per slot: t Hessenberg columns of maxZ + 2 (when they exceed shared memory)
   // per slot, new column b, plane q: (Re w, Im w - Re w, Re w + Im w) of the new columns, the
   // operand of the inner products in Gauss's three-multiplication form (slots x t x 3 x D)
   double* Wp;
