@@ -635,9 +635,10 @@ def run_sweep_only(args):
     k = 400.0 * args.n / 1024
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        extra = {} if args.twisted is None else {"twisted": args.twisted}
         h = hh.Handle(k, args.n, args.strips, "LR+RL+BT+TB", precision=args.precision, profile=1,
                       autotune=args.autotune, bcr_depth=args.bcr_depth,
-                      stream=stream.cuda_stream)
+                      stream=stream.cuda_stream, **extra)
         dofs = (args.n + 1) ** 2
         r = torch.from_numpy(np.ascontiguousarray(hh_inputs.random_vector(dofs, 4, seed=1).ravel())).cuda()
         z = torch.zeros_like(r)
@@ -655,7 +656,7 @@ def run_sweep_only(args):
         h.close()
     ms = st["sweep_ms"] / max(1, st["sweep_launches"])
     print(json.dumps({"mode": "sweep", "n": args.n, "strips": args.strips, "precision": args.precision,
-                      "bcr_depth": st["bcr_depth"], "setup_ms": st["setup_ms"],
+                      "bcr_depth": st["bcr_depth"], "twisted": st["twisted"], "setup_ms": st["setup_ms"],
                       "sweep_ms": ms, "steps_per_launch": st["sweep_steps"],
                       "us_per_step": ms * 1e3 / st["sweep_steps"],
                       "GBps": st["sweep_bytes"] / max(1, st["sweep_launches"]) / (ms / 1e3) / 1e9,
@@ -686,6 +687,9 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--bcr-depth", type=int, default=-1,
                     help="cyclic-reduction depth of the strip solves (-1: autotuned, 0: block Thomas)")
+    ap.add_argument("--twisted", type=int, default=None,
+                    help="--mode sweep/solve1: hh_opts.twisted (1: twisted strip solves, -1: timed against "
+                         "block Thomas, 0: off; default: the library's)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="--mode solve1/sweep: hh_opts.autotune (0: the default tile; -(1 + 7 shape + variant): "
                          "one candidate, e.g. -13 = 32 columns, 4 K slices summed in a cluster)")
@@ -705,14 +709,15 @@ def main():
         w = hh_inputs.workload(WORKLOAD)
         # no autotuning: under a profiler the tuner's timings are blurred by the per-launch
         # overhead; --autotune forces the candidate the tuner picks in the live bench
-        with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", autotune=args.autotune) as h:
+        extra = {} if args.twisted is None else {"twisted": args.twisted}
+        with hh.Handle(w.k, w.n, w.strips, w.dirs, precision="fp32", autotune=args.autotune, **extra) as h:
             b = torch.from_numpy(h.assemble_rhs(w.sources[0])).cuda()
             x, res = h.solve(b, tol=w.tol)
             torch.cuda.synchronize()
             st = h.stats()
         print(json.dumps({"mode": "solve1", "iterations": res.iterations, "status": hh.STATUS_NAMES[res.status],
                           "rel_res_explicit": res.rel_res_explicit, "kernel_launches": st["kernel_launches"],
-                          "bcr_depth": st["bcr_depth"], "sweep_steps": st["sweep_steps"]}),
+                          "bcr_depth": st["bcr_depth"], "twisted": st["twisted"], "sweep_steps": st["sweep_steps"]}),
               flush=True)
         return
     if args.mode == "fd":

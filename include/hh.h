@@ -146,6 +146,16 @@ typedef struct {
                              basis run on the tensor cores as exact integer products of 7-bit slices
                              of the FP64 data (FP64-accurate; about 64 more bytes of device memory
                              per node for every basis vector); 0: on the FP64 pipe */
+  int twisted;            /* the strip solves with a full right-hand side by a twisted block
+                             factorisation (complex64 tensor-core sweeps, interface_form 1,
+                             strips >= 2, n / strips >= 4; other sweeps keep block Thomas): the
+                             first R = n / strips lines of every strip are eliminated from both
+                             ends at once, meeting at line R/2, so that each dependent step carries
+                             a top and a bottom task and the chain is R + 1 steps instead of
+                             2R + 1, with the same factor bytes; the last strip's extra line R
+                             follows by its Schur complement after the interface corrections.
+                             1: used; -1: stored and timed against block Thomas (and the stored
+                             cyclic-reduction depths) per column count; 0 (default): not stored */
 } hh_opts;
 
 typedef struct {
@@ -193,6 +203,8 @@ typedef struct {
   double gsdot_bytes;       /* algorithmic bytes of the timed inner-product launches (the
                                tensor-core form: the basis slice images and the new columns'
                                image, read once) */
+  int twisted;              /* 1 when the strip solves of the last column count use the twisted
+                               factorisation (opts.twisted) */
 } hh_stats;
 
 /* Fill *o with the defaults listed above. */

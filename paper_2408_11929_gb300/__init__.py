@@ -34,7 +34,8 @@ class hh_opts(ctypes.Structure):
                 ("tensor_cores", ctypes.c_int), ("autotune", ctypes.c_int), ("fuse_chains", ctypes.c_int),
                 ("overlap_steps", ctypes.c_int), ("interface_form", ctypes.c_int),
                 ("persistent", ctypes.c_int), ("gs_first_fp32", ctypes.c_int),
-                ("discretization", ctypes.c_int), ("group_wide_tiles", ctypes.c_int), ("gs_tensor", ctypes.c_int)]
+                ("discretization", ctypes.c_int), ("group_wide_tiles", ctypes.c_int), ("gs_tensor", ctypes.c_int),
+                ("twisted", ctypes.c_int)]
 
 
 class hh_result(ctypes.Structure):
@@ -59,7 +60,7 @@ class hh_stats(ctypes.Structure):
                 ("ns_blocks", ctypes.c_int), ("ns_iterations", ctypes.c_int), ("tc_bnc", ctypes.c_int),
                 ("tc_nsplit", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_us", ctypes.c_double), ("iterations_total", ctypes.c_int64),
                 ("step_graphs", ctypes.c_int), ("step_graph_fallback", ctypes.c_int), ("bcr_depth", ctypes.c_int),
-                ("gsdot_bytes", ctypes.c_double)]
+                ("gsdot_bytes", ctypes.c_double), ("twisted", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

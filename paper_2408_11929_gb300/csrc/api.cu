@@ -138,6 +138,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
             HH_EINVAL);
   if (opts.gs_passes != 1 && opts.gs_passes != 2) return (set_error("gs_passes must be 1 or 2"), HH_EINVAL);
   if (opts.gs_tensor != 0 && opts.gs_tensor != 1) return (set_error("gs_tensor must be 0 or 1"), HH_EINVAL);
+  if (opts.twisted < -1 || opts.twisted > 1) return (set_error("twisted must be -1 (autotune), 0 or 1"), HH_EINVAL);
   if (opts.discretization != HH_DISC_P1 && opts.discretization != HH_DISC_FD)
     return (set_error("discretization must be HH_DISC_P1 or HH_DISC_FD"), HH_EINVAL);
   if (opts.discretization == HH_DISC_FD && opts.precision != HH_PREC_FP64)
@@ -158,7 +159,9 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
     if (opts.bcr_depth > 0) depths = 1u << opts.bcr_depth;
     else if (opts.bcr_depth < 0)
       for (int d = 1; d <= dl; ++d) depths |= 1u << d;
-    bdir = block_directory(R, N, opts.interface_form, depths);
+    // the twisted strip solves run on the complex64 tensor-core kernels only
+    const bool twisted = opts.twisted != 0 && precision == HH_PREC_FP32 && opts.tensor_cores;
+    bdir = block_directory(R, N, opts.interface_form, depths, twisted);
   }
   static const int bitcode[4] = {DC_LR, DC_RL, DC_BT, DC_TB};
   dir_codes.clear();
@@ -226,6 +229,10 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
       prog_double_d[d] = build_program(n, N, true, opts.interface_form, bdir, d);
       prog_single_d[d] = build_program(n, N, false, opts.interface_form, bdir, d);
     }
+  if (bdir.iTw >= 0) {
+    prog_double_d[PROG_TWISTED] = build_program(n, N, true, opts.interface_form, bdir, PROG_TWISTED);
+    prog_single_d[PROG_TWISTED] = build_program(n, N, false, opts.interface_form, bdir, PROG_TWISTED);
+  }
   if (upload_programs() || upload_persistent()) return HH_ENOMEM;
   cudaStreamSynchronize(stream);
 
@@ -485,6 +492,7 @@ void hh_default_opts(hh_opts* o) {
   o->gs_first_fp32 = 1;
   o->gs_tensor = 1;
   o->group_wide_tiles = 1;
+  o->twisted = 0;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {
@@ -635,7 +643,11 @@ hh_status hh_get_stats(hh_handle* h, hh_stats* st) {
   st->ldf = E.ldf;
   st->columns = E.last_columns;
   st->sweep_steps = (int64_t)E.program(E.last_columns, E.opts.single_sweep != 0).size();
-  st->bcr_depth = E.depth_for(E.last_columns);
+  {
+    const int d = E.depth_for(E.last_columns);
+    st->bcr_depth = d == PROG_TWISTED ? 0 : d;
+    st->twisted = d == PROG_TWISTED ? 1 : 0;
+  }
   st->gemm_launches = E.launches[Engine::K_GEMM];
   st->gemm_ms = E.ms[Engine::K_GEMM];
   st->gemm_flops = E.flops[Engine::K_GEMM];

@@ -83,12 +83,24 @@ struct BlockDir {
   // F_top, G_1..G_{nd-1} (F_i L), G_top, H_0..H_{nd-1} (F_i U) from iDeep[d].
   int dmax = 0, iLev = -1;
   int iDeep[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  // twisted block factorisation of the strip solves (lines 0..R-1 of every strip, meeting at
+  // line q = R/2): G_j = P_j^{-1} from the bottom, P_{R-1} = D_int, P_j = D_int - U G_{j+1} L
+  // (j = R-1 .. q+1, at iTw + j - q - 1); M = (D_int - L F_{q-1} U - U G_{q+1} L)^{-1} at iTwM;
+  // Z_0 = D_int^{-1}[0, R-1] U at iZ0 (the last strip's extra line enters through Z_0..Z_{R-1})
+  int iTw = -1, iTwM = -1, iZ0 = -1, twq = 0;
   int total = 0;  // blocks in the store
 };
-// form: interface form (0, 1); depths: bit d set = the blocks of cyclic-reduction depth d
-BlockDir block_directory(int R, int N, int form, unsigned depths = 0);
-// depth: cyclic-reduction levels of the full-right-hand-side strip solves (0: block Thomas)
+// Index of the twisted program among the per-depth programs (0..7: cyclic-reduction depth).
+constexpr int PROG_TWISTED = 8;
+constexpr int NPROG = 9;
+// form: interface form (0, 1); depths: bit d set = the blocks of cyclic-reduction depth d;
+// twisted: the blocks of the twisted strip solves (form 1, N >= 2, R >= 4)
+BlockDir block_directory(int R, int N, int form, unsigned depths = 0, bool twisted = false);
+// depth: cyclic-reduction levels of the full-right-hand-side strip solves (0: block Thomas), or
+// PROG_TWISTED for the twisted factorisation
 std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form, const BlockDir& bd, int depth = 0);
+// whether the twisted strip solves can be stored for R lines per strip, N strips, form
+bool twisted_possible(int R, int N, int form);
 // largest usable depth: R divisible by 2^d (at most 7)
 int max_bcr_depth(int R);
 
@@ -190,18 +202,21 @@ class Engine {
   // sweep programs (opts.interface_form): phases of a double and of a single sweep, their
   // grouped tasks in one device table
   BlockDir bdir;
-  // programs of every cyclic-reduction depth whose blocks are stored (index = depth)
-  std::vector<SweepPhase> prog_double_d[8], prog_single_d[8];
+  // programs of every cyclic-reduction depth whose blocks are stored (index = depth) and of
+  // the twisted strip solves (index PROG_TWISTED)
+  std::vector<SweepPhase> prog_double_d[NPROG], prog_single_d[NPROG];
   int bcr_blocks();                          // setup.cu: the cyclic-reduction blocks of bdir
-  std::map<int, int> bcr_tuned;              // depth per column count (fixed or autotuned)
-  int depth_for(int C) const;                // the depth a sweep of C columns uses
+  std::map<int, int> bcr_tuned;              // program per column count (fixed or autotuned)
+  int depth_for(int C) const;                // the program (depth or PROG_TWISTED) of C columns
+  bool twisted_ok(int C) const;              // the twisted program can run C columns
+  int twisted_blocks();                      // setup.cu: the twisted strip-solve blocks of bdir
   const std::vector<SweepPhase>& program(int C, bool single) const;
   int tune_depth(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes);
   GTask* prog_tasks = nullptr;
   int upload_programs();
   // the same programs for the persistent sweep kernel (persist.cu): block-Thomas steps as
   // grouped tasks, one device task table, device phase tables per (program, columns, shape)
-  std::vector<SweepPhase> pprog_double_d[8], pprog_single_d[8];
+  std::vector<SweepPhase> pprog_double_d[NPROG], pprog_single_d[NPROG];
   GTask* pprog_tasks = nullptr;
   std::map<int64_t, void*> pphase_cache;
   int upload_persistent();

@@ -202,26 +202,31 @@ __global__ void copy_line_kernel(const T* __restrict__ src, T* __restrict__ dst,
 // One 3-D view per sweep array (floats of a node row, node rows, lines), box 2 BNC floats x
 // 16 rows x 1 line: the raw input rows of a stage.
 struct GMaps {
-  CUtensorMap m[SB_COUNT];
+  CUtensorMap m[SB_COUNT];  // 16-row boxes: plain input rows, base rows
+  CUtensorMap s[SB_COUNT];  // 18-row boxes: line-coupled input rows (one halo row each side)
 };
 
 // grid = (ceil(m / 128), total column tiles of the tasks (BNC columns each), nsplit), 320
 // threads, the roles of tc_line_gemm_kernel: lane 0 of warp 8 issues the TMA loads (factor
-// tiles hi and lo of term q's block, 16 raw rows of term q's input line), lane 0 of warp 9 the
-// MMAs (TF32 x 3 into one FP32 accumulator in tensor memory), warps 0-7 build the B tiles
-// (x or -x, split hi + lo, swizzled) and run the epilogue.  K split z covers stages
-// [z kst, (z+1) kst) of the concatenated terms.  CLUSTER: the nsplit CTAs of a tile form a
-// cluster (1, 1, nsplit) and sum their tiles in rank order through distributed shared memory.
+// tiles hi and lo of term q's block; the raw rows of term q's input: 16 rows of a plain line,
+// or 18 rows of a line-coupled one with a halo row each side, after the term's 16 base rows
+// if it has a base), lane 0 of warp 9 the MMAs (TF32 x 3 into one FP32 accumulator in tensor
+// memory), warps 0-7 build the B tiles (x = base +- C(input), split hi + lo, swizzled) and run
+// the epilogue.  The coupling C to the node line below / above takes vert (vedge at the line's
+// end nodes, vint inside) times the node plus dg times its neighbour along the line, as in the
+// block-Thomas step.  K split z covers stages [z kst, (z+1) kst) of the concatenated terms.
+// CLUSTER: the nsplit CTAs of a tile form a cluster (1, 1, nsplit) and sum their tiles in rank
+// order through distributed shared memory.
 template <class CF, bool CLUSTER>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     tc_group_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                     const __grid_constant__ GMaps maps, const GTask* __restrict__ tasks, int ntask, GArrays arrs,
-                    int m, int N, int C, int kst, int split, int* err, long long budget) {
+                    int m, int N, int C, int kst, int split, float2 vedge, float2 vint, float dg, int* err,
+                    long long budget) {
   using namespace tc;
   constexpr int BNC = CF::BNC, STAGES = CF::STAGES, BTILE = CF::BTILE;
   constexpr int STAGE_BYTES = CF::STAGE_BYTES, PAIR_GROUPS = CF::PAIR_GROUPS;
   constexpr int PAIRS_PER_THREAD = CF::PAIRS_PER_THREAD, TMEM_COLS = CF::TMEM_COLS, RAW_ROW = CF::RAW_ROW;
-  constexpr int RAW_BYTES = RAW_BASE_ROWS * RAW_ROW;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   const uint32_t raw_s = smem_u32(tc_smem_raw);
   unsigned char* sm = tc_smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);
@@ -275,25 +280,33 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       auto load_a = [&](int kt) {
         const int s = kt % STAGES, st = kb + kt;
         const int q = st / spt, k0 = (st % spt) * BKC;
+        const GTerm& g = tk.term[q];
+        const int raw = (g.barr ? RAW_BASE_ROWS * RAW_ROW : 0) + (g.cpl ? RAW_SRC_ROWS : RAW_BASE_ROWS) * RAW_ROW;
         unsigned char* stp = sm + (size_t)s * STAGE_BYTES;
         if (split) {
           // map_hi is the complex64 store itself: the builders split the tile into hi + lo
-          mbar_expect_tx(&full_a[s], TILE + RAW_BYTES);
-          tc::tma_load_3d(stp, &map_hi, 2 * k0, row0, tk.term[q].f, &full_a[s]);
+          mbar_expect_tx(&full_a[s], TILE + raw);
+          tc::tma_load_3d(stp, &map_hi, 2 * k0, row0, g.f, &full_a[s]);
         } else {
-          mbar_expect_tx(&full_a[s], 2 * TILE + RAW_BYTES);
-          tc::tma_load_3d(stp, &map_hi, 2 * k0, row0, tk.term[q].f, &full_a[s]);
-          tc::tma_load_3d(stp + TILE, &map_lo, 2 * k0, row0, tk.term[q].f, &full_a[s]);
+          mbar_expect_tx(&full_a[s], 2 * TILE + raw);
+          tc::tma_load_3d(stp, &map_hi, 2 * k0, row0, g.f, &full_a[s]);
+          tc::tma_load_3d(stp + TILE, &map_lo, 2 * k0, row0, g.f, &full_a[s]);
         }
       };
       auto load_raw = [&](int kt) {
         const int s = kt % STAGES, st = kb + kt;
         const int q = st / spt, k0 = (st % spt) * BKC;
         const GTerm& g = tk.term[q];
+        unsigned char* rawp = sm + (size_t)s * STAGE_BYTES + 2 * TILE;
         // float index of the tile's first column in the input rows: even C keeps it a multiple
-        // of 4 floats (16 bytes); strips outside 0..N-1 read the zero fill
-        const int xb = 2 * ((tk.s0 + g.ds) * C + colc0);
-        tc::tma_load_3d(sm + (size_t)s * STAGE_BYTES + 2 * TILE, &maps.m[g.arr], xb, k0, g.line, &full_a[s]);
+        // of 4 floats (16 bytes); strips outside 0..N-1 read the zero fill, and so do the halo
+        // rows before node 0 and after node m-1
+        if (g.barr) tc::tma_load_3d(rawp, &maps.m[g.barr], 2 * (tk.s0 * C + colc0), k0, g.bline, &full_a[s]);
+        const int xs = 2 * ((tk.s0 + g.ds) * C + colc0);
+        if (g.cpl)
+          tc::tma_load_3d(rawp + RAW_BASE_ROWS * RAW_ROW, &maps.s[g.arr], xs, k0 - 1, g.line, &full_a[s]);
+        else
+          tc::tma_load_3d(rawp + RAW_BASE_ROWS * RAW_ROW, &maps.m[g.arr], xs, k0, g.line, &full_a[s]);
       };
       const int pre = min(nk, STAGES);
       for (int kt = 0; kt < pre; ++kt) load_a(kt);
@@ -362,7 +375,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       }
       const int st = kb + kt;
       const int k0 = (st % spt) * BKC;
-      const float sg = tk.term[st / spt].neg ? -1.f : 1.f;
+      const GTerm& g = tk.term[st / spt];
+      const float sg = g.neg ? -1.f : 1.f;
       if (split) {
         // A = hi + lo elementwise, the swizzled layout kept: hi in place, lo in the second tile
         float4* ah = reinterpret_cast<float4*>(sm + (size_t)s * STAGE_BYTES);
@@ -379,12 +393,29 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       unsigned char* bh = sm + (size_t)s * STAGE_BYTES + 2 * TILE;
       unsigned char* bl = bh + BTILE;
       const float2* rb = reinterpret_cast<const float2*>(bh);
+      const float2* rs = reinterpret_cast<const float2*>(bh + RAW_BASE_ROWS * RAW_ROW);
       float2 x[2 * PAIRS_PER_THREAD];
 #pragma unroll
       for (int u = 0; u < 2 * PAIRS_PER_THREAD; ++u) {
         const int kk = 2 * (pg + PAIR_GROUPS * (u >> 1)) + (u & 1);
-        const float2 v = rb[kk * BNC + c];
-        x[u] = (k0 + kk < m && cvalid) ? make_float2(sg * v.x, sg * v.y) : make_float2(0.f, 0.f);
+        const int k = k0 + kk;
+        float2 v = g.barr ? rb[kk * BNC + c] : make_float2(0.f, 0.f);
+        float2 cp;
+        if (g.cpl) {
+          // raw row kk + 1 is node k; its neighbour along the line is row kk or kk + 2
+          cp = rs[(kk + 1) * BNC + c];
+          const int nb = g.cpl == XC_LOWER ? k - 1 : k + 1;
+          const float2 y = (nb >= 0 && nb < m) ? rs[(kk + 1 + (g.cpl == XC_LOWER ? -1 : 1)) * BNC + c]
+                                               : make_float2(0.f, 0.f);
+          cp = cmul((k == 0 || k == m - 1) ? vedge : vint, cp);
+          cp.x += dg * y.x;
+          cp.y += dg * y.y;
+        } else {
+          cp = rs[kk * BNC + c];
+        }
+        v.x += sg * cp.x;
+        v.y += sg * cp.y;
+        x[u] = (k < m && cvalid) ? v : make_float2(0.f, 0.f);
       }
       asm volatile("bar.sync 1, %0;" ::"n"(BUILDERS) : "memory");
 #pragma unroll
@@ -520,6 +551,10 @@ template <typename R>
 cudaError_t launch_group_simt(Engine& E, const SweepPhase& ph, const GArrays& arrs, int C, void* partial_buf,
                               size_t partial_bytes) {
   using T = typename Cx<R>::T;
+  // line-coupled terms (the twisted strip solves) run on the tensor-core kernels only
+  for (const GTask& g : ph.tasks)
+    for (int q = 0; q < g.nterm; ++q)
+      if (g.term[q].cpl || g.term[q].barr) return cudaErrorInvalidValue;
   constexpr int BM = 64, BN = 64, BK = 16, STG = 3;
   constexpr size_t smem = (size_t)STG * (BM * BK + BK * BN) * sizeof(T);
   auto fn = group_gemm_kernel<R, BM, BN, BK, 4, 4, STG>;
@@ -559,6 +594,7 @@ static cudaError_t launch_tc_group_shape(Engine& E, const SweepPhase& ph, const 
     const Engine::LineMaps* lm = E.line_maps_for(arrs.p[b], C, CF::BNC, lines);
     if (!lm) return cudaErrorInvalidValue;
     maps.m[b] = lm->base;
+    maps.s[b] = lm->src;
   }
   const int ntask = (int)ph.tasks.size();
   const int gx = (E.m + tc::BM - 1) / tc::BM, gy = total_tiles(ph, C, CF::BNC);
@@ -594,12 +630,14 @@ static cudaError_t launch_tc_group_shape(Engine& E, const SweepPhase& ph, const 
   const int split = 0;
   const CUtensorMap& fa = split ? E.tmap_c : E.tmap_hi;
   cudaError_t ce;
+  const float2 vedge = E.coef.vert_f[0], vint = E.coef.vert_f[E.coef.n > 1 ? 1 : 0];
+  const float dg = E.coef.diag_f;
   if (nsplit > 1)
     ce = cudaLaunchKernelEx(&cfg, tc_group_kernel<CF, true>, fa, E.tmap_lo, maps, tasks, ntask, arrs, E.m, E.N,
-                            C, kst, split, E.err, E.opts.timeout_cycles);
+                            C, kst, split, vedge, vint, dg, E.err, E.opts.timeout_cycles);
   else
     ce = cudaLaunchKernelEx(&cfg, tc_group_kernel<CF, false>, fa, E.tmap_lo, maps, tasks, ntask, arrs, E.m, E.N,
-                            C, kst, split, E.err, E.opts.timeout_cycles);
+                            C, kst, split, vedge, vint, dg, E.err, E.opts.timeout_cycles);
   E.count_launch();
   return ce;
 }
@@ -614,6 +652,9 @@ cudaError_t launch_tc_group(Engine& E, int shape, const SweepPhase& ph, const GA
       wmax = std::max(wmax, g.ns * C);
     }
     if (wmin > tc::Wide::BNC && wmax <= tc::Huge::BNC) shape = 2;
+    // every task within one 32-column tile (the last strip's corrections of the twisted strip
+    // solves at one right-hand side): the narrow shape, half the MMA work of the wide one
+    if (wmax <= tc::Narrow::BNC) shape = 1;
   }
   if (shape == 1) return launch_tc_group_shape<tc::Narrow>(E, ph, arrs, C);
   if (shape == 2) return launch_tc_group_shape<tc::Huge>(E, ph, arrs, C);

@@ -496,7 +496,7 @@ static bool step_to_task(const SweepStep& s, GTask& t) {
 // run (it then stays on the per-phase launches).
 int Engine::upload_persistent() {
   std::vector<GTask> all;
-  for (int d = 0; d < 8; ++d)
+  for (int d = 0; d < NPROG; ++d)
     for (int single = 0; single < 2; ++single) {
       const std::vector<SweepPhase>& prog = single ? prog_single_d[d] : prog_double_d[d];
       std::vector<SweepPhase>& pp = single ? pprog_single_d[d] : pprog_double_d[d];

@@ -299,7 +299,8 @@ static void exact_gemm(Engine& E, const typename Cx<R>::T* A, const typename Cx<
 //     backward  X_top = y_top,  X_j = y_j - (F_j U) X_{j+1};
 //   Y_j = X_j L for the strips visited before the last (top = R-1) and for the last (top = R);
 //   last block column of the strips before the last, X = D^{-1} E_{R-1}:
-//     X_{R-1} = F_{R-1},  X_j = -(F_j U) X_{j+1},  Z_j = X_j U  (j = 1..R-1);
+//     X_{R-1} = F_{R-1},  X_j = -(F_j U) X_{j+1},  Z_j = X_j U  (j = 1..R-1, and j = 0 when
+//     the twisted strip solves are stored);
 //   G^(2^l) and K^(2^l) by repeated squaring.
 // The products chain up to R factors, so they run on the exact GEMM (as the interface blocks).
 template <typename R>
@@ -359,16 +360,16 @@ int inverse_columns_impl(Engine& E) {
     X = Xn;
     ++products;
   }
-  // last block column of the strips before the last
+  // last block column of the strips before the last (and Z_0 for the twisted strip solves)
   X = B(Rr - 1);
   rmul(X, B(bd.iZ + Rr - 2), 1);
   pp = 0;
-  for (int j = Rr - 2; j >= 1; --j) {
+  for (int j = Rr - 2; j >= (bd.iZ0 >= 0 ? 0 : 1); --j) {
     rmul(B(j), FU, 1);
     T* Xn = P[pp];
     pp ^= 1;
     exact_gemm<R>(E, FU, X, Xn, -1.0);
-    rmul(Xn, B(bd.iZ + j - 1), 1);
+    rmul(Xn, j == 0 ? B(bd.iZ0) : B(bd.iZ + j - 1), 1);
     X = Xn;
     ++products;
   }
@@ -688,6 +689,95 @@ int invert_chain_fp64(Engine& E, int count, const std::function<int(int, double2
   return rc;
 }
 
+// S = D_type - L X U - U X2 L (a null X or X2 leaves its product out), with L and U the
+// couplings of a node line to the line below / above (see rmul_kernel):
+//   (L X U)[a][b] = v_a v_b X[a][b] + v_a d X[a][b-1] + d v_b X[a-1][b] + d^2 X[a-1][b-1],
+//   (U X L)[a][b] = v_a v_b X[a][b] + v_a d X[a][b+1] + d v_b X[a+1][b] + d^2 X[a+1][b+1],
+// v = vert, d = diag: the Schur complements of the twisted strip solves.  Padding columns are
+// left as they are.
+template <typename R>
+__global__ void schur2_kernel(const typename Cx<R>::T* __restrict__ X, const typename Cx<R>::T* __restrict__ X2,
+                              int ld, int type, Coef cf, typename Cx<R>::T* __restrict__ S, int m) {
+  using T = typename Cx<R>::T;
+  const size_t total = (size_t)m * m;
+  const R dg = (R)cf.diag();
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / m), b = (int)(idx % m);
+    double2 d = make_double2(0.0, 0.0);
+    if (a == b) d = cf.centre(a, type);
+    else if (a - b == 1 || b - a == 1) d = cf.horiz(type);
+    T v = mk<T>(d.x, d.y);
+    const double2 va = cf.vert(a), vb = cf.vert(b);
+    const T tva = mk<T>(va.x, va.y), tvb = mk<T>(vb.x, vb.y);
+    const T tvab = cmul(tva, tvb);
+    if (X) {
+      T acc = mk<T>(0, 0);
+      cfma(acc, tvab, X[(size_t)a * ld + b]);
+      if (b >= 1) cfma(acc, cscale(tva, dg), X[(size_t)a * ld + b - 1]);
+      if (a >= 1) cfma(acc, cscale(tvb, dg), X[(size_t)(a - 1) * ld + b]);
+      if (a >= 1 && b >= 1) acc = cadd(acc, cscale(X[(size_t)(a - 1) * ld + b - 1], (R)(dg * dg)));
+      v = csub(v, acc);
+    }
+    if (X2) {
+      T acc = mk<T>(0, 0);
+      cfma(acc, tvab, X2[(size_t)a * ld + b]);
+      if (b + 1 < m) cfma(acc, cscale(tva, dg), X2[(size_t)a * ld + b + 1]);
+      if (a + 1 < m) cfma(acc, cscale(tvb, dg), X2[(size_t)(a + 1) * ld + b]);
+      if (a + 1 < m && b + 1 < m) acc = cadd(acc, cscale(X2[(size_t)(a + 1) * ld + b + 1], (R)(dg * dg)));
+      v = csub(v, acc);
+    }
+    S[(size_t)a * ld + b] = v;
+  }
+}
+
+// Blocks of the twisted strip solves (see append_twisted_f1 in sweep.cu): from the bottom of
+// the strip matrix of lines 0..R-1 (every line below line 0 of the interior type),
+//   G_{R-1} = D_int^{-1},  G_j = (D_int - U G_{j+1} L)^{-1}  (j = R-2 .. q+1),
+// and the block of the meeting line q,  M = (D_int - L F_{q-1} U - U G_{q+1} L)^{-1}.
+// Each inverse by Newton-Schulz from the previous block (M: from F_q), as the top-down factors.
+template <typename R>
+int twisted_blocks_impl(Engine& E) {
+  using T = typename Cx<R>::T;
+  const BlockDir& bd = E.bdir;
+  if (bd.iTw < 0) return HH_OK;
+  const int m = E.m, ld = E.ldf, Rr = E.R, q = bd.twq;
+  const size_t blk = (size_t)m * ld;
+  T* F = reinterpret_cast<T*>(E.factors);
+  auto B = [&](int i) { return F + (size_t)i * blk; };
+  auto G = [&](int j) { return B(bd.iTw + j - q - 1); };
+  T* S = nullptr;
+  if (E.dmalloc((void**)&S, blk * sizeof(T))) return HH_ENOMEM;
+  cudaMemsetAsync(S, 0, blk * sizeof(T), E.stream);
+  int rc = HH_OK;
+  {
+    BlockInverter<R> inv(E);
+    rc = inv.alloc();
+    const unsigned g = E.grid_for((size_t)m * m);
+    E.tick_begin(Engine::K_SETUP);
+    for (int j = Rr - 1; j >= q + 1 && rc == HH_OK; --j) {
+      const T* prev = j == Rr - 1 ? nullptr : G(j + 1);
+      schur2_kernel<R><<<g, 256, 0, E.stream>>>(nullptr, prev, ld, LINE_INT, E.coef, S, m);
+      E.count_launch();
+      rc = inv.invert(S, prev, G(j));
+    }
+    if (rc == HH_OK) {
+      schur2_kernel<R><<<g, 256, 0, E.stream>>>(B(q - 1), G(q + 1), ld, LINE_INT, E.coef, S, m);
+      E.count_launch();
+      rc = inv.invert(S, B(q), B(bd.iTwM));
+    }
+    E.tick_end(Engine::K_SETUP, 0.0, 0.0);
+  }
+  const cudaError_t ce = cudaStreamSynchronize(E.stream);
+  E.dfree(S);
+  if (rc) return rc;
+  if (ce != cudaSuccess) { E.set_cuda_error(ce, "twisted strip setup"); return HH_ECUDA; }
+  return E.check_device_error("twisted strip setup");
+}
+
+int Engine::twisted_blocks() {
+  return precision == HH_PREC_FP32 ? twisted_blocks_impl<float>(*this) : twisted_blocks_impl<double>(*this);
+}
+
 // Blocks of block cyclic reduction of the strip solves (see append_bcr_f1 in sweep.cu).  The
 // level-0 system of a strip is block tridiagonal over its node lines: diagonal blocks D_BOT
 // (line 0), D_INT, D_TOP (the last strip's line R), couplings L (to the line below) and U.
@@ -883,6 +973,7 @@ int factor_impl(Engine& E) {
   if (status == HH_OK) status = interface_blocks<R>(E, bufA, bufB);
   if (status == HH_OK) status = inverse_columns_impl<R>(E);
   if (status == HH_OK) status = bcr_blocks_impl<R>(E);
+  if (status == HH_OK) status = twisted_blocks_impl<R>(E);
   E.dfree(bufA); E.dfree(bufB); E.dfree(col); E.dfree(piv); E.dfree(srcidx);
   E.dfree(bufC); E.dfree(bufD); E.dfree(part_dev); E.dfree(sums_dev);
   if (part_host) cudaFreeHost(part_host);

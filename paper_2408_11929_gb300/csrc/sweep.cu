@@ -129,7 +129,9 @@ int max_bcr_depth(int R) {
   return d;
 }
 
-BlockDir block_directory(int R, int N, int form, unsigned depths) {
+bool twisted_possible(int R, int N, int form) { return form != 0 && N >= 2 && R >= 4; }
+
+BlockDir block_directory(int R, int N, int form, unsigned depths, bool twisted) {
   BlockDir bd;
   bd.total = R + 3;
   if (form != 0 && N >= 2) {
@@ -153,6 +155,13 @@ BlockDir block_directory(int R, int N, int form, unsigned depths) {
         bd.iDeep[d] = bd.total;
         bd.total += 3 * (R >> d) + 1;
       }
+  }
+  if (twisted && twisted_possible(R, N, form)) {
+    bd.twq = R / 2;
+    bd.iTw = bd.total;
+    bd.iTwM = bd.iTw + (R - 1 - bd.twq);
+    bd.iZ0 = bd.iTwM + 1;
+    bd.total = bd.iZ0 + 1;
   }
   return bd;
 }
@@ -249,6 +258,70 @@ static void append_bcr_f1(std::vector<SweepPhase>& prog, int R, int N, int d, co
 //   B2  u_s[j] = v_s[j] - Z_j u_{s+1}[0], lines j = 1..R-1 of strips 0..N-2 in one step,
 //       Z_j = D^{-1}[j, R-1] U.
 // Every step is exact algebra on the block-Thomas form; only the order of the sums differs.
+// F1 by the twisted block factorisation of the strip matrix D of lines 0..R-1 (the same in
+// every strip; the last strip's extra line R follows after F3, see build_program): with the
+// block-Thomas factors F_j from the top, G_j from the bottom and M at line q (BlockDir),
+//   forward, step i = 0, 1, ..: the top line j = i < q,       y_j = F_j (r_j - L y_{j-1}),
+//                               the bottom line j = R-1-i > q, z_j = G_j (r_j - U z_{j+1});
+//   middle:                     x_q = M (r_q - L y_{q-1} - U z_{q+1});
+//   back, step i = 0, 1, ..:    x_j = y_j - F_j U x_{j+1} (j = q-1-i),
+//                               x_j = z_j - G_j L x_{j-1} (j = q+1+i).
+// Both ends advance in one grouped step (two tasks over all strips), so the dependent chain
+// is 2 max(q, R-1-q) + 1 steps instead of block Thomas's 2R - 1, with the same factor bytes.
+// Every line j of V holds y_j (j < q) or z_j (j > q) until the back substitution overwrites it.
+static void append_twisted_f1(std::vector<SweepPhase>& prog, int R, int N, const BlockDir& bd) {
+  const int q = bd.twq;
+  auto coupled = [](int f, int line, int cpl, int bline) {
+    // x = Rin[bline] - C(V[line]) (bline < 0: no base)
+    GTerm g{f, SB_V, line, 0, 1, cpl, bline >= 0 ? SB_RIN : 0, bline >= 0 ? bline : 0};
+    return g;
+  };
+  auto task = [&](std::initializer_list<GTerm> terms, int out_line, int mode) {
+    GTask t{};
+    t.nterm = 0;
+    for (const GTerm& g : terms) t.term[t.nterm++] = g;
+    t.out_arr = SB_V; t.out_line = out_line;
+    t.base_arr = SB_NONE; t.base_line = 0;
+    t.mode = mode; t.s0 = 0; t.ns = N;
+    return t;
+  };
+  const int half = std::max(q, R - 1 - q);
+  for (int i = 0; i < half; ++i) {
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    if (i < q) {
+      const int j = i;
+      p.tasks.push_back(j == 0 ? task({GTerm{0, SB_RIN, 0, 0, 0, 0, 0, 0}}, 0, OUT_SET)
+                               : task({coupled(j, j - 1, XC_LOWER, j)}, j, OUT_SET));
+    }
+    if (R - 1 - i > q) {
+      const int j = R - 1 - i, f = bd.iTw + j - q - 1;
+      p.tasks.push_back(j == R - 1 ? task({GTerm{f, SB_RIN, j, 0, 0, 0, 0, 0}}, j, OUT_SET)
+                                   : task({coupled(f, j + 1, XC_UPPER, j)}, j, OUT_SET));
+    }
+    prog.push_back(p);
+  }
+  {
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    p.tasks.push_back(task({coupled(bd.iTwM, q - 1, XC_LOWER, q), coupled(bd.iTwM, q + 1, XC_UPPER, -1)}, q, OUT_SET));
+    prog.push_back(p);
+  }
+  for (int i = 0; i < half; ++i) {
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    if (q - 1 - i >= 0) {
+      const int j = q - 1 - i;
+      p.tasks.push_back(task({coupled(j, j + 1, XC_UPPER, -1)}, j, OUT_ADD));
+    }
+    if (q + 1 + i <= R - 1) {
+      const int j = q + 1 + i;
+      p.tasks.push_back(task({coupled(bd.iTw + j - q - 1, j - 1, XC_LOWER, -1)}, j, OUT_ADD));
+    }
+    prog.push_back(p);
+  }
+}
+
 std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form, const BlockDir& bd, int depth) {
   std::vector<SweepPhase> prog;
   const int R = n / N;
@@ -259,7 +332,9 @@ std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form,
     return p;
   };
   const std::vector<SweepStep> legacy = build_steps(n, N, double_sweep);
-  if (depth > 0) append_bcr_f1(prog, R, N, depth, bd);
+  const bool twisted = depth == PROG_TWISTED;
+  if (twisted) append_twisted_f1(prog, R, N, bd);
+  else if (depth > 0) append_bcr_f1(prog, R, N, depth, bd);
   else
     for (int q = 0; q < 2 * R + 1; ++q) prog.push_back(as_step(legacy[q]));  // F1
   if (form == 0 || N < 2) {
@@ -290,7 +365,23 @@ std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form,
     src_line = 0;
   }
   // F3
-  {
+  if (twisted) {
+    // F1 solved the first R lines of the last strip like every other strip, so its first-line
+    // correction uses the same Y_j; then its extra line R by the Schur complement of lines
+    // 0..R-1, whose inverse is F_R: x_R = F_R (r_R - L v[R-1]), and x_j = v[j] - Z_j x_R with
+    // Z_j = D_int^{-1}[j, R-1] U (the coupling of line R-1 to line R)
+    SweepPhase p;
+    p.kind = PH_GROUP;
+    for (int j = 0; j < R; ++j)
+      p.tasks.push_back(task1(bd.iY + j, src_arr, src_line, -1, 1, SB_V, j, SB_NONE, 0, OUT_ADD, 1, N - 1));
+    prog.push_back(p);
+    prog.push_back(as_step(legacy[R]));
+    SweepPhase c;
+    c.kind = PH_GROUP;
+    for (int j = 0; j < R; ++j)
+      c.tasks.push_back(task1(j == 0 ? bd.iZ0 : bd.iZ + j - 1, SB_V, R, 0, 1, SB_V, j, SB_NONE, 0, OUT_ADD, N - 1, 1));
+    prog.push_back(c);
+  } else {
     SweepPhase p;
     p.kind = PH_GROUP;
     if (N >= 3)
@@ -695,9 +786,14 @@ __global__ void __launch_bounds__(1024) chain_kernel(const typename Cx<R>::T* __
   }
 }
 
+bool Engine::twisted_ok(int C) const {
+  return bdir.iTw >= 0 && precision == HH_PREC_FP32 && tc_ready && C % 2 == 0 && !prog_double_d[PROG_TWISTED].empty();
+}
+
 int Engine::depth_for(int C) const {
   const auto it = bcr_tuned.find(C);
   if (it != bcr_tuned.end()) return it->second;
+  if (opts.twisted == 1 && twisted_ok(C)) return PROG_TWISTED;
   return opts.bcr_depth > 0 ? opts.bcr_depth : 0;
 }
 
@@ -708,7 +804,7 @@ const std::vector<SweepPhase>& Engine::program(int C, bool single) const {
 
 int Engine::upload_programs() {
   std::vector<GTask> all;
-  for (int d = 0; d < 8; ++d)
+  for (int d = 0; d < NPROG; ++d)
     for (std::vector<SweepPhase>* prog : {&prog_double_d[d], &prog_single_d[d]})
       for (SweepPhase& ph : *prog) {
         ph.dev_off = all.size();
@@ -971,6 +1067,7 @@ static double group_bytes(const Engine& E, const SweepPhase& ph, int C) {
   for (const GTask& t : ph.tasks) {
     const double line = (double)E.m * t.ns * C * e;
     b += t.nterm * (blkb + line) + line * (1 + (t.base_arr != SB_NONE || t.mode == OUT_ADD));
+    for (int q = 0; q < t.nterm; ++q) b += t.term[q].barr ? line : 0.0;  // a term's own base line
   }
   return b;
 }
@@ -1066,7 +1163,7 @@ int Engine::run_sweep_untimed(const void* Rin, void* V, void* W, int C, bool sin
     const int rc = tune_tc(C, Rin, V, W, partial, partial_bytes);
     if (rc) return rc;
   }
-  if (opts.bcr_depth < 0 && allow_graph && !bcr_tuned.count(C)) {
+  if ((opts.bcr_depth < 0 || (opts.twisted < 0 && twisted_ok(C))) && allow_graph && !bcr_tuned.count(C)) {
     const int rc = tune_depth(C, Rin, V, W, partial, partial_bytes);
     if (rc) return rc;
   }
@@ -1143,20 +1240,22 @@ int Engine::ensure_tuned(int C) {
     const int rc = tune_tc(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
     if (rc) return rc;
   }
-  if (opts.bcr_depth < 0 && !bcr_tuned.count(C)) {
+  if ((opts.bcr_depth < 0 || (opts.twisted < 0 && twisted_ok(C))) && !bcr_tuned.count(C)) {
     const int rc = tune_depth(C, w_rin, w_v, w_w, w_partial, w_partial_bytes);
     if (rc) return rc;
   }
   return prepare_persistent(*this, C, w_partial_bytes);
 }
 
-// Autotuner of the cyclic-reduction depth for C columns per strip: every depth whose blocks
-// are stored runs whole sweeps (one warm-up, three timed with CUDA events, on the arrays of the
-// call, whose outputs the real sweep overwrites next) and the fastest is kept.
+// Autotuner of the strip-solve form for C columns per strip: block Thomas, every cyclic-reduction
+// depth whose blocks are stored and the twisted factorisation (when it can run C columns) run
+// whole sweeps (one warm-up, three timed with CUDA events, on the arrays of the call, whose
+// outputs the real sweep overwrites next) and the fastest is kept.
 int Engine::tune_depth(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes) {
   std::vector<int> cand = {0};
   for (int d = 1; d <= bdir.dmax; ++d)
     if (bdir.iDeep[d] >= 0) cand.push_back(d);
+  if (twisted_ok(C)) cand.push_back(PROG_TWISTED);
   if (cand.size() == 1) {
     bcr_tuned[C] = 0;
     return HH_OK;

@@ -41,15 +41,17 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "hh.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hh_opts), sizeof(hh_result),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hh_opts), sizeof(hh_result),'
                     ' sizeof(hh_stats), offsetof(hh_opts, stream), offsetof(hh_stats, sweep_steps),'
-                    ' offsetof(hh_result, status), offsetof(hh_stats, gemm_flops), offsetof(hh_stats, gs_flops));return 0;}\n')
+                    ' offsetof(hh_result, status), offsetof(hh_stats, gemm_flops), offsetof(hh_stats, gs_flops),'
+                    ' offsetof(hh_opts, twisted), offsetof(hh_stats, twisted));return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(hh.hh_opts), ctypes.sizeof(hh.hh_result), ctypes.sizeof(hh.hh_stats),
                     hh.hh_opts.stream.offset, hh.hh_stats.sweep_steps.offset, hh.hh_result.status.offset,
-                    hh.hh_stats.gemm_flops.offset, hh.hh_stats.gs_flops.offset]
+                    hh.hh_stats.gemm_flops.offset, hh.hh_stats.gs_flops.offset, hh.hh_opts.twisted.offset,
+                    hh.hh_stats.twisted.offset]
 
 
 def test_default_opts(lib):
@@ -57,7 +59,7 @@ def test_default_opts(lib):
     assert o.precision == hh.HH_PREC_FP64 and o.maxit == 200 and o.deflate_eta == 1e-10
     assert o.use_graph == 1 and o.timeout_cycles > 0 and o.bcr_depth == 0 and o.gs_passes == 2
     assert o.serve_slots == 8 and o.tensor_cores == 1 and o.autotune == 1 and o.fuse_chains == 1
-    assert o.overlap_steps == 1
+    assert o.overlap_steps == 1 and o.twisted == 0
 
 
 @pytest.mark.parametrize("k,n,strips,dirs,kw", [
@@ -73,6 +75,8 @@ def test_default_opts(lib):
     (10.0, 32, 4, 15, {"bcr_depth": -2}),
     (10.0, 32, 4, 15, {"gs_passes": 3}),
     (10.0, 32, 4, 15, {"gs_tensor": 2}),
+    (10.0, 32, 4, 15, {"twisted": 2}),
+    (10.0, 32, 4, 15, {"twisted": -2}),
     (10.0, 32, 4, 15, {"discretization": 2}),
     (10.0, 32, 4, 15, {"discretization": 1, "precision": 1}),   # the five-point mode is FP64 only
     (10.0, 32, 4, 15, {"serve_slots": 0}),

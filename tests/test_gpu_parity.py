@@ -564,6 +564,82 @@ def test_cyclic_reduction_solve_fp64_matches_oracle():
     assert rel(x, ref.x) < 1e-10
 
 
+# (k, n, strips): R = 8, 16, 4, 6, 5 (odd: the ends meet unevenly), 45 (two strips), 32
+TWIST_CASES = [(20.0, 32, 4), (30.0, 48, 3), (25.0, 64, 16), (20.0, 36, 6), (15.0, 40, 8), (30.0, 90, 2),
+               (60.0, 256, 8)]
+
+
+@pytest.mark.parametrize("k,n,N", TWIST_CASES)
+def test_twisted_strip_solves(k, n, N):
+    """The strip solves by the twisted block factorisation (both ends of every strip eliminated
+    at once, meeting at line R/2; the last strip's extra line by its Schur complement after the
+    interface corrections): the double and the single complex64 sweep equal block Thomas to
+    1e-4 and the oracle's (banded LU in FP64) to the complex64 bar, in all four directions; an
+    odd column count (CUDA-core kernels) keeps block Thomas; the chain is shorter."""
+    A, *_ = fem.global_system(k, n)
+    for ncols in (4, 2, 3):
+        r = hh_inputs.random_vector(A.shape[0], ncols, seed=70 + ncols)
+        rr = np.ascontiguousarray(r.ravel())
+        for single in (0, 1):
+            with hh.Handle(k, n, N, precision="fp32", twisted=1, single_sweep=single) as ht, \
+                    hh.Handle(k, n, N, precision="fp32", twisted=0, single_sweep=single) as h0:
+                for d in sweep.DIRECTIONS:
+                    zt = ht.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                    z0 = h0.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                    assert ht.stats()["twisted"] == (1 if ncols % 2 == 0 else 0), ncols
+                    assert rel(zt, z0) < 1e-4, (d, ncols, single)
+                    sw = sweep.Sweeper(A, k, n, N, d)
+                    for c in range(ncols):
+                        assert rel(zt[c], sw.apply(r[c], not single)) < 2e-4, (d, c, single)
+                if ncols % 2 == 0:
+                    assert ht.stats()["sweep_steps"] < h0.stats()["sweep_steps"]
+
+
+@pytest.mark.parametrize("k,n,N,ncols", [(20.0, 32, 4, 4), (60.0, 256, 8, 8), (30.0, 90, 2, 2)])
+def test_twisted_strip_solves_persistent_and_bf16(k, n, N, ncols):
+    """The twisted program in the one-launch persistent sweep equals its phase-by-phase launches;
+    with bf16 factor products it stays within the bf16 bar of the oracle's sweep."""
+    A, *_ = fem.global_system(k, n)
+    r = hh_inputs.random_vector(A.shape[0], ncols, seed=80 + ncols)
+    rr = np.ascontiguousarray(r.ravel())
+    for single in (0, 1):
+        with hh.Handle(k, n, N, precision="fp32", twisted=1, single_sweep=single, persistent=1) as hp, \
+                hh.Handle(k, n, N, precision="fp32", twisted=1, single_sweep=single, persistent=0) as hl, \
+                hh.Handle(k, n, N, precision="bf16", twisted=1, single_sweep=single) as hb:
+            for d in sweep.DIRECTIONS:
+                zp = hp.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                zl = hl.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                zb = hb.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                assert hp.stats()["twisted"] == 1 and hb.stats()["twisted"] == 1
+                assert rel(zp, zl) < 1e-5, (d, single)
+                sw = sweep.Sweeper(A, k, n, N, d)
+                for c in range(ncols):
+                    ref = sw.apply(r[c], not single)
+                    assert rel(zl[c], ref) < 2e-4, (d, c, single)
+                    assert rel(zb[c], ref) < BF16_SWEEP_BAR, (d, c, single)
+
+
+@pytest.mark.parametrize("twisted", [1, -1])
+def test_twisted_solve(twisted):
+    """A complex64 solve with the twisted strip solves (forced, or timed against block Thomas
+    per column count): tol 1e-6 in explicit residual within the oracle's iterations + 2, the
+    solution within 1e-4 of the oracle's."""
+    k, n, N = 40.0, 128, 8
+    P = solver.Problem(k, n, N)
+    b = P.rhs(hh_inputs.centre_source())
+    ref = P.solve(b, tol=1e-6)
+    with hh.Handle(k, n, N, precision="fp32", twisted=twisted) as h:
+        x, res = h.solve(b, tol=1e-6)
+        st = h.stats()
+    assert res.status == hh.HH_OK
+    assert res.iterations <= ref.iterations + 2 and res.rel_res_explicit < 1.5e-6
+    assert rel(x, ref.x) < 1e-4
+    if twisted == 1:
+        assert st["twisted"] == 1 and st["bcr_depth"] == 0
+    else:
+        assert st["twisted"] in (0, 1)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("dirs", ["LR+RL", "LR+RL+BT+TB"])
 def test_single_sweep_combinations_solve(precision, dirs):
