@@ -150,23 +150,28 @@ def measured_peaks() -> dict:
 PROFILE_SAMPLE = 16
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(extra=()) -> str:
     h = hashlib.sha256()
-    for f in ("gemm.cuh", "tc_gemm.cuh", "common.cuh"):
+    for f in ("gemm.cuh", "tc_gemm.cuh", "common.cuh") + tuple(extra):
         h.update(open(os.path.join(ROOT, "paper_2408_11929_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(workload: str, kind: str = "simt", bnc=None, cluster=None):
-    """DRAM bytes of one wide sweep GEMM step (all its kernels) from the committed ncu summary,
-    if it was taken on the current kernel source and, for the tensor-core step, on the tile
-    shape and reduction the autotuner chose (else None)."""
-    p = os.path.join(ROOT, "profiles", "line_gemm_traffic.json" if kind == "simt" else "tc_line_gemm_traffic.json")
+    """DRAM bytes of one wide sweep GEMM step (all its kernels), or the mean of one sweep's grouped
+    launches (kind "group"), from the committed ncu summary, if it was taken on the current kernel
+    source and, for the tensor-core step, on the tile shape and reduction the autotuner chose
+    (else None)."""
+    name = {"simt": "line_gemm_traffic.json", "tc": "tc_line_gemm_traffic.json", "group": "tc_group_traffic.json"}[kind]
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash(("group.cu",) if kind == "group" else ()):
         return None
+    if kind == "group":
+        e = d.get("workloads", {}).get(workload)
+        return None if e is None else float(e["dram_bytes_per_launch"])
     if kind == "tc":
         for cap in d.get("captures", []):
             if (cap["workload"] == workload and cap["complex_columns_per_cta"] == bnc
@@ -347,13 +352,18 @@ def run_gpu(args, ws, rank, local):
         gemm_peak = peaks["tf32_tflops"] if tc_on else peaks["fp32_alu_tflops"]
         gemm_line = {
             "bound": "tensor" if tc_on else "alu",
-            "kernel": (("tc_line_gemm_kernel (tcgen05 kind::tf32, 3 products per K step)" +
-                        (", K slices summed in a thread-block cluster" if st["tc_cluster"]
-                         else " + split_reduce_kernel"))
-                       if tc_on else "line_gemm_kernel<float> + split_reduce_kernel") + ": wide sweep GEMM step",
+            "kernel": ("tc_group_kernel (tcgen05 kind::tf32, 3 products per K step): the sweep's grouped "
+                       "steps (two-task steps of the twisted strip solves, interface scans, one-shot corrections); "
+                       "achieved = their algorithmic flops / their CUDA-event time, over every grouped launch of "
+                       "the sampled sweeps" if st["twisted"] else
+                       (("tc_line_gemm_kernel (tcgen05 kind::tf32, 3 products per K step)" +
+                         (", K slices summed in a thread-block cluster" if st["tc_cluster"]
+                          else " + split_reduce_kernel"))
+                        if tc_on else "line_gemm_kernel<float> + split_reduce_kernel") + ": wide sweep GEMM step"),
             "achieved": achieved, "peak": gemm_peak, "unit": "TFLOP/s",
             "frac": (achieved / gemm_peak) if achieved else None,
-            "traffic": (ncu_traffic(WORKLOAD, "tc", st["tc_bnc"], st["tc_cluster"]) if tc_on
+            "traffic": (ncu_traffic(WORKLOAD, "group") if st["twisted"] else
+                        ncu_traffic(WORKLOAD, "tc", st["tc_bnc"], st["tc_cluster"]) if tc_on
                         else ncu_traffic(WORKLOAD)),
             "algorithmic_flops_per_launch": gemm_flops, "avg_launch_ms": gemm_ms,
             "launches_timed": st["gemm_launches"],
@@ -483,12 +493,14 @@ def run_serving(nreq: int, rate_hz, seed: int = 0) -> dict:
     rate_hz (None: all at once, which measures the capacity), through one hh_server (complex64
     sweeps on the tensor cores, 2 slots per problem, iteration cap SERVE_MAXIT).  Latency =
     submission to completion (queueing, setup of an uncached problem and the solve);
-    throughput = requests / (last completion - first arrival)."""
+    throughput = requests / (last completion - first arrival).  The stream's problems are nearly
+    all distinct (each solved about once), so the server keeps block Thomas (twisted = 0): the
+    twisted strip solves' extra setup (58 ms at k = 400) exceeds what they save in one solve."""
     import paper_2408_11929_gb300 as hh
     reqs = hh_inputs.serving_stream(nreq, seed=seed, rate_hz=rate_hz if rate_hz else 1e12)
     xs = [np.zeros((q["n"] + 1) ** 2, dtype=np.complex128) for q in reqs]
     done, tickets = {}, []
-    with hh.Server(precision="fp32", serve_slots=2, maxit=SERVE_MAXIT) as srv:
+    with hh.Server(precision="fp32", serve_slots=2, maxit=SERVE_MAXIT, twisted=0) as srv:
         t0 = time.perf_counter()
         i = 0
         while len(done) < len(reqs):

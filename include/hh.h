@@ -148,14 +148,19 @@ typedef struct {
                              per node for every basis vector); 0: on the FP64 pipe */
   int twisted;            /* the strip solves with a full right-hand side by a twisted block
                              factorisation (complex64 tensor-core sweeps, interface_form 1,
-                             strips >= 2, n / strips >= 4; other sweeps keep block Thomas): the
+                             strips >= 2, n / strips >= 4; other sweeps, bf16 ones included, keep
+                             block Thomas): the
                              first R = n / strips lines of every strip are eliminated from both
                              ends at once, meeting at line R/2, so that each dependent step carries
                              a top and a bottom task and the chain is R + 1 steps instead of
                              2R + 1, with the same factor bytes; the last strip's extra line R
                              follows by its Schur complement after the interface corrections.
-                             1: used; -1: stored and timed against block Thomas (and the stored
-                             cyclic-reduction depths) per column count; 0 (default): not stored */
+                             It needs 2 + R/2 more m x m blocks, whose setup takes longer (their
+                             Newton-Schulz iterations start farther from the inverse: 58 ms more
+                             at k = 400, n = 1024), and saves 13 % of every sweep there.
+                             1 (default): used; -1: stored and timed against block Thomas (and
+                             the stored cyclic-reduction depths) per column count; 0: not stored
+                             (streams of problems that are each solved once) */
 } hh_opts;
 
 typedef struct {

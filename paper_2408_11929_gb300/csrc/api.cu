@@ -160,7 +160,7 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
     else if (opts.bcr_depth < 0)
       for (int d = 1; d <= dl; ++d) depths |= 1u << d;
     // the twisted strip solves run on the complex64 tensor-core kernels only
-    const bool twisted = opts.twisted != 0 && precision == HH_PREC_FP32 && opts.tensor_cores;
+    const bool twisted = opts.twisted != 0 && precision == HH_PREC_FP32 && !lowp && opts.tensor_cores;
     bdir = block_directory(R, N, opts.interface_form, depths, twisted);
   }
   static const int bitcode[4] = {DC_LR, DC_RL, DC_BT, DC_TB};
@@ -492,7 +492,7 @@ void hh_default_opts(hh_opts* o) {
   o->gs_first_fp32 = 1;
   o->gs_tensor = 1;
   o->group_wide_tiles = 1;
-  o->twisted = 0;
+  o->twisted = 1;
 }
 
 hh_status hh_setup(double k, int n, int strips, uint32_t dirs, const hh_opts* opts, hh_handle** out) {

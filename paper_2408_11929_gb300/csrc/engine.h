@@ -182,6 +182,9 @@ class Engine {
     double us = 0;
   };
   std::map<int, TcChoice> tc_tuned;
+  // clusters of the grouped tensor-core step that fit on the device at once, per (tile shape,
+  // cluster size) (group.cu)
+  std::map<int, int> group_clusters;
   int tune_tc(int C, const void* Rin, void* V, void* W, void* partial, size_t partial_bytes);
   // sweeps replayed as CUDA graphs (opts.use_graph), one per (arrays, columns, kind)
   struct SweepGraph {

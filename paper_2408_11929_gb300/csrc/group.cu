@@ -582,8 +582,42 @@ cudaError_t launch_group_simt(Engine& E, const SweepPhase& ph, const GArrays& ar
   return cudaGetLastError();
 }
 
-// Tensor-core grouped step: tile shape CF, K split until the SMs are filled (at most 8 slices,
-// summed in a cluster).
+// Clusters of nsplit CTAs of the grouped step with tile shape CF that the device holds at once
+// (one CTA per SM; a cluster needs its CTAs within one GPC, so fewer SMs are usable as the
+// cluster grows), queried once per shape and size.
+template <class CF>
+static int group_cluster_fit(Engine& E, int nsplit) {
+  const int key = CF::BNC * 16 + nsplit;
+  const auto it = E.group_clusters.find(key);
+  if (it != E.group_clusters.end()) return it->second;
+  int n = E.num_sms / nsplit;
+  if (nsplit > 1) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(1, 1, nsplit);
+    cfg.blockDim = dim3(tc::THREADS);
+    cfg.dynamicSmemBytes = CF::SMEM;
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeClusterDimension;
+    a[0].val.clusterDim.x = 1;
+    a[0].val.clusterDim.y = 1;
+    a[0].val.clusterDim.z = nsplit;
+    cfg.attrs = a;
+    cfg.numAttrs = 1;
+    int q = 0;
+    if (cudaOccupancyMaxActiveClusters(&q, (const void*)tc_group_kernel<CF, true>, &cfg) == cudaSuccess && q > 0)
+      n = q;
+    else
+      cudaGetLastError();
+  }
+  n = std::max(1, n);
+  E.group_clusters[key] = n;
+  return n;
+}
+
+// Tensor-core grouped step: tile shape CF, K split into at most 8 slices summed in a cluster;
+// the split minimises waves x (stages per slice + a fixed prologue / epilogue cost of about 6
+// stages), the waves counted against the clusters that fit at once (18 clusters of 8 do not
+// fit in one wave on 152 SMs: a two-task step of 9 row tiles each took twice its time so).
 template <class CF>
 static cudaError_t launch_tc_group_shape(Engine& E, const SweepPhase& ph, const GArrays& arrs, int C) {
   GMaps maps;
@@ -599,7 +633,20 @@ static cudaError_t launch_tc_group_shape(Engine& E, const SweepPhase& ph, const 
   const int ntask = (int)ph.tasks.size();
   const int gx = (E.m + tc::BM - 1) / tc::BM, gy = total_tiles(ph, C, CF::BNC);
   const int nst = max_terms(ph) * ((E.m + tc::BKC - 1) / tc::BKC);
-  int nsplit = std::max(1, std::min(8, (E.num_sms - 4) / (gx * gy)));
+  int nsplit = 1;
+  {
+    double best = 1e30;
+    for (int ns = 1; ns <= 8; ++ns) {
+      const int k_ns = (nst + ns - 1) / ns;
+      const int fit = group_cluster_fit<CF>(E, ns);
+      const int waves = (gx * gy + fit - 1) / fit;
+      const double cost = waves * (k_ns + 6.0);
+      if (cost < best) {
+        best = cost;
+        nsplit = ns;
+      }
+    }
+  }
   const int kst = (nst + nsplit - 1) / nsplit;
   nsplit = (nst + kst - 1) / kst;
   cudaLaunchConfig_t cfg{};
@@ -645,13 +692,19 @@ static cudaError_t launch_tc_group_shape(Engine& E, const SweepPhase& ph, const 
 cudaError_t launch_tc_group(Engine& E, int shape, const SweepPhase& ph, const GArrays& arrs, int C) {
   // a task wider than one 64-column tile but within one 128-column tile: the 128-column shape
   // reads each of its factor tiles once instead of once per column tile
+  // (a phase with many tasks: the one-shot corrections; the scans and the two-task steps of
+  // the twisted strip solves have too few tiles to fill the SMs without a K split, where the
+  // 128-column tile's MMAs, twice as long per stage, set the pace: 1.86 against 2.02 ms per
+  // k = 400 sweep with the twisted strip solves)
   if (shape == 0 && E.opts.group_wide_tiles) {
     int wmin = 1 << 30, wmax = 0;
     for (const GTask& g : ph.tasks) {
       wmin = std::min(wmin, g.ns * C);
       wmax = std::max(wmax, g.ns * C);
     }
-    if (wmin > tc::Wide::BNC && wmax <= tc::Huge::BNC) shape = 2;
+    const int row_tiles = (E.m + tc::BM - 1) / tc::BM;
+    if (wmin > tc::Wide::BNC && wmax <= tc::Huge::BNC && 2 * row_tiles * (int)ph.tasks.size() >= E.num_sms)
+      shape = 2;
     // every task within one 32-column tile (the last strip's corrections of the twisted strip
     // solves at one right-hand side): the narrow shape, half the MMA work of the wide one
     if (wmax <= tc::Narrow::BNC) shape = 1;

@@ -766,6 +766,8 @@ int twisted_blocks_impl(Engine& E) {
       rc = inv.invert(S, B(q), B(bd.iTwM));
     }
     E.tick_end(Engine::K_SETUP, 0.0, 0.0);
+    E.ns_blocks += inv.inversions;
+    E.ns_iterations += inv.ns_iters;
   }
   const cudaError_t ce = cudaStreamSynchronize(E.stream);
   E.dfree(S);

@@ -786,8 +786,13 @@ __global__ void __launch_bounds__(1024) chain_kernel(const typename Cx<R>::T* __
   }
 }
 
+// bf16 factor products keep block Thomas: the bottom-up factors G_j belong to sub-strips whose
+// ends are both cut (no absorbing line), their norms are larger, and with 8-bit factor entries
+// the twisted sweep erred 8 times as much as block Thomas on 45-line strips (6.3 against
+// 0.76 per cent); in complex64 both stay within the same bar.
 bool Engine::twisted_ok(int C) const {
-  return bdir.iTw >= 0 && precision == HH_PREC_FP32 && tc_ready && C % 2 == 0 && !prog_double_d[PROG_TWISTED].empty();
+  return bdir.iTw >= 0 && precision == HH_PREC_FP32 && !lowp && tc_ready && C % 2 == 0 &&
+         !prog_double_d[PROG_TWISTED].empty();
 }
 
 int Engine::depth_for(int C) const {

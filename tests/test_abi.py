@@ -59,7 +59,7 @@ def test_default_opts(lib):
     assert o.precision == hh.HH_PREC_FP64 and o.maxit == 200 and o.deflate_eta == 1e-10
     assert o.use_graph == 1 and o.timeout_cycles > 0 and o.bcr_depth == 0 and o.gs_passes == 2
     assert o.serve_slots == 8 and o.tensor_cores == 1 and o.autotune == 1 and o.fuse_chains == 1
-    assert o.overlap_steps == 1 and o.twisted == 0
+    assert o.overlap_steps == 1 and o.twisted == 1
 
 
 @pytest.mark.parametrize("k,n,strips,dirs,kw", [

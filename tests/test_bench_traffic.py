@@ -27,5 +27,6 @@ def test_traffic_matches_tuned_variant():
 
 
 def test_traffic_null_when_kernel_source_changed(monkeypatch):
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda extra=(): "0000000000000000")
     assert bench.ncu_traffic(bench.WORKLOAD, "tc", 64, False) is None
+    assert bench.ncu_traffic(bench.WORKLOAD, "group") is None

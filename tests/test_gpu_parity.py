@@ -597,26 +597,31 @@ def test_twisted_strip_solves(k, n, N):
 
 @pytest.mark.parametrize("k,n,N,ncols", [(20.0, 32, 4, 4), (60.0, 256, 8, 8), (30.0, 90, 2, 2)])
 def test_twisted_strip_solves_persistent_and_bf16(k, n, N, ncols):
-    """The twisted program in the one-launch persistent sweep equals its phase-by-phase launches;
-    with bf16 factor products it stays within the bf16 bar of the oracle's sweep."""
+    """The twisted program in the one-launch persistent sweep equals its phase-by-phase launches
+    (complex64 both, K slices summed in another order: 5e-5, the longer chains through the
+    meeting line's Schur complement amplify it more than block Thomas does).  bf16 factor
+    products keep block Thomas: the handle reports no twisted solves and the same sweep as a
+    handle without them."""
     A, *_ = fem.global_system(k, n)
     r = hh_inputs.random_vector(A.shape[0], ncols, seed=80 + ncols)
     rr = np.ascontiguousarray(r.ravel())
     for single in (0, 1):
         with hh.Handle(k, n, N, precision="fp32", twisted=1, single_sweep=single, persistent=1) as hp, \
                 hh.Handle(k, n, N, precision="fp32", twisted=1, single_sweep=single, persistent=0) as hl, \
-                hh.Handle(k, n, N, precision="bf16", twisted=1, single_sweep=single) as hb:
+                hh.Handle(k, n, N, precision="bf16", twisted=1, single_sweep=single) as hb, \
+                hh.Handle(k, n, N, precision="bf16", twisted=0, single_sweep=single) as hb0:
             for d in sweep.DIRECTIONS:
                 zp = hp.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
                 zl = hl.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
                 zb = hb.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
-                assert hp.stats()["twisted"] == 1 and hb.stats()["twisted"] == 1
-                assert rel(zp, zl) < 1e-5, (d, single)
+                zb0 = hb0.apply_preconditioner(d, rr, ncols).reshape(ncols, -1)
+                assert hp.stats()["twisted"] == 1 and hb.stats()["twisted"] == 0
+                assert rel(zp, zl) < 5e-5, (d, single)
                 sw = sweep.Sweeper(A, k, n, N, d)
                 for c in range(ncols):
                     ref = sw.apply(r[c], not single)
                     assert rel(zl[c], ref) < 2e-4, (d, c, single)
-                    assert rel(zb[c], ref) < BF16_SWEEP_BAR, (d, c, single)
+                    assert rel(zb[c], zb0[c]) < 1e-6, (d, c, single)
 
 
 @pytest.mark.parametrize("twisted", [1, -1])
