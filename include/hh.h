@@ -148,8 +148,8 @@ typedef struct {
                              per node for every basis vector); 0: on the FP64 pipe */
   int twisted;            /* the strip solves with a full right-hand side by a twisted block
                              factorisation (complex64 tensor-core sweeps, interface_form 1,
-                             strips >= 2, n / strips >= 4; other sweeps, bf16 ones included, keep
-                             block Thomas): the
+                             strips >= 2, n / strips >= 4, bcr_depth <= 0; other sweeps, bf16
+                             ones included, keep block Thomas or the fixed depth): the
                              first R = n / strips lines of every strip are eliminated from both
                              ends at once, meeting at line R/2, so that each dependent step carries
                              a top and a bottom task and the chain is R + 1 steps instead of
@@ -286,7 +286,10 @@ hh_status hh_gram_schmidt_pass(hh_handle* h, int p, const double* V, int t, doub
  */
 hh_status hh_apply_preconditioner_noalloc(hh_handle* h, uint32_t dir, int ncols, const double* r, double* z);
 
-/* Copy the stored inverse S_j^{-1} (j = 0..R) as complex128 row-major m x m into out. */
+/* Copy block j of the factor store as complex128 row-major m x m into out: j = 0..R the
+   block-Thomas inverses S_j^{-1} (Section 2's strip solves); j = R+1 .. factor_blocks-1 (see
+   hh_stats) the blocks derived from them in the order of the store; with the twisted strip
+   solves (hh_opts.twisted) the last R/2 + 1 blocks are G_{R/2+1} .. G_{R-1}, M and Z_0. */
 hh_status hh_get_factor(hh_handle* h, int j, double* out);
 
 hh_status hh_get_stats(hh_handle* h, hh_stats* st);

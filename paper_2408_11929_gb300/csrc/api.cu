@@ -159,8 +159,10 @@ int Engine::init(double k_, int n_, int strips, uint32_t dirs, const hh_opts* o)
     if (opts.bcr_depth > 0) depths = 1u << opts.bcr_depth;
     else if (opts.bcr_depth < 0)
       for (int d = 1; d <= dl; ++d) depths |= 1u << d;
-    // the twisted strip solves run on the complex64 tensor-core kernels only
-    const bool twisted = opts.twisted != 0 && precision == HH_PREC_FP32 && !lowp && opts.tensor_cores;
+    // the twisted strip solves run on the complex64 tensor-core kernels only, and a fixed
+    // cyclic-reduction depth replaces them
+    const bool twisted =
+        opts.twisted != 0 && opts.bcr_depth <= 0 && precision == HH_PREC_FP32 && !lowp && opts.tensor_cores;
     bdir = block_directory(R, N, opts.interface_form, depths, twisted);
   }
   static const int bitcode[4] = {DC_LR, DC_RL, DC_BT, DC_TB};
@@ -582,7 +584,7 @@ hh_status hh_get_factor(hh_handle* h, int j, double* out) {
   if (!h || !out) return (set_error("bad arguments"), HH_EINVAL);
   Engine& E = *h->E;
   if (E.fd) return (set_error("the five-point mode keeps no P1 strip factors"), HH_EINVAL);
-  if (j < 0 || j > E.R) return (set_error("factor index out of range"), HH_EINVAL);
+  if (j < 0 || j >= E.factor_blocks()) return (set_error("factor index out of range"), HH_EINVAL);
   std::lock_guard<std::mutex> lk(E.solve_mu);
   cudaSetDevice(E.device);
   const size_t cnt = (size_t)E.m * E.ldf;

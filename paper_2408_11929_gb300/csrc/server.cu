@@ -98,7 +98,8 @@ struct hh_server {
     if (opts.bcr_depth > 0) depths = 1u << opts.bcr_depth;
     else if (opts.bcr_depth < 0)
       for (int d = 1; d <= hh::max_bcr_depth((int)R); ++d) depths |= 1u << d;
-    const bool twisted = opts.twisted != 0 && opts.precision == HH_PREC_FP32 && opts.tensor_cores;
+    const bool twisted =
+        opts.twisted != 0 && opts.bcr_depth <= 0 && opts.precision == HH_PREC_FP32 && opts.tensor_cores;
     const size_t blocks = (size_t)hh::block_directory((int)R, N, opts.interface_form, depths, twisted).total;
     const size_t factors = copies * blocks * m * ldf * elem;
     const size_t C = (size_t)t * opts.serve_slots;

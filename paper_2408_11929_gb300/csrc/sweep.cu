@@ -798,8 +798,9 @@ bool Engine::twisted_ok(int C) const {
 int Engine::depth_for(int C) const {
   const auto it = bcr_tuned.find(C);
   if (it != bcr_tuned.end()) return it->second;
+  if (opts.bcr_depth > 0) return opts.bcr_depth;  // an explicit depth before the default
   if (opts.twisted == 1 && twisted_ok(C)) return PROG_TWISTED;
-  return opts.bcr_depth > 0 ? opts.bcr_depth : 0;
+  return 0;
 }
 
 const std::vector<SweepPhase>& Engine::program(int C, bool single) const {
