@@ -346,25 +346,30 @@ def test_batch_zero_and_nonzero_columns():
 @pytest.mark.parametrize("k,n,N", [(20.0, 32, 4), (15.0, 40, 5), (60.0, 256, 8)])
 def test_tensor_core_sweeps(k, n, N):
     """complex64 sweeps on the tensor cores (TF32 operands split hi + lo, three products, FP32
-    accumulation) against the CUDA-core complex64 sweeps and the FP64 oracle sweep."""
+    accumulation), with the twisted strip solves (grouped steps) and with block Thomas (line
+    steps), against the CUDA-core complex64 sweeps and the FP64 oracle sweep."""
     A, *_ = fem.global_system(k, n)
     r = hh_inputs.random_vector(A.shape[0], 4, seed=5)
     errs = {}
     with hh.Handle(k, n, N, precision="fp32", tensor_cores=1) as ht, \
+            hh.Handle(k, n, N, precision="fp32", tensor_cores=1, twisted=0) as ht0, \
             hh.Handle(k, n, N, precision="fp32", tensor_cores=0) as hc:
         assert ht.stats()["tensor_cores"] == 1 and hc.stats()["tensor_cores"] == 0
         for d in sweep.DIRECTIONS:
             sw = sweep.Sweeper(A, k, n, N, d)
             zt = ht.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
+            zt0 = ht0.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
             zc = hc.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
+            assert ht.stats()["twisted"] == 1 and ht0.stats()["twisted"] == 0
             for c in range(4):
                 ref = sw.apply(r[c])
-                errs[(d, c)] = (rel(zt[c], ref), rel(zc[c], ref))
+                errs[(d, c)] = (rel(zt[c], ref), rel(zt0[c], ref), rel(zc[c], ref))
     worst_t = max(e[0] for e in errs.values())
-    worst_c = max(e[1] for e in errs.values())
-    print(f"tensor-core vs oracle {worst_t:.2e}, CUDA-core vs oracle {worst_c:.2e}")
+    worst_t0 = max(e[1] for e in errs.values())
+    worst_c = max(e[2] for e in errs.values())
+    print(f"tensor-core vs oracle {worst_t:.2e} (twisted) {worst_t0:.2e} (Thomas), CUDA-core {worst_c:.2e}")
     assert worst_c < 2e-4
-    assert worst_t < 2e-4
+    assert worst_t < 2e-4 and worst_t0 < 2e-4
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -388,11 +393,12 @@ def test_step_graphs_replayed_and_equal_to_eager(precision):
 def test_tensor_core_step_candidates(cand):
     """Every candidate of the tensor-core step's autotuner (three tile shapes; K split by a
     reduction kernel or in a thread-block cluster) gives the complex64 sweep within the bar.
-    8 strips x 4 columns: 32 columns, a partial tile of every shape."""
+    8 strips x 4 columns: 32 columns, a partial tile of every shape.  Block Thomas, whose
+    strip-solve steps are the line steps the candidates apply to."""
     k, n, N = 60.0, 256, 8
     A, *_ = fem.global_system(k, n)
     r = hh_inputs.random_vector(A.shape[0], 4, seed=9)
-    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + cand)) as h:
+    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + cand), twisted=0) as h:
         for d in ("BT", "LR"):
             sw = sweep.Sweeper(A, k, n, N, d)
             z = h.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 4).reshape(4, -1)
@@ -409,7 +415,7 @@ def test_tensor_core_128_column_tiles(variant):
     k, n, N = 60.0, 256, 32
     A, *_ = fem.global_system(k, n)
     r = hh_inputs.random_vector(A.shape[0], 8, seed=10)
-    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + 14 + variant)) as h:
+    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + 14 + variant), twisted=0) as h:
         for d in ("TB", "RL"):
             sw = sweep.Sweeper(A, k, n, N, d)
             z = h.apply_preconditioner(d, np.ascontiguousarray(r.ravel()), 8).reshape(8, -1)
@@ -466,17 +472,18 @@ def test_fused_interface_chain_many_rows():
             assert rel(zf, zu) < 1e-4
 
 
-@pytest.mark.parametrize("autotune", [0, -(1 + 7 + 5), -(1 + 14 + 0)])
-def test_overlapped_tensor_core_steps_equal_plain_order(autotune):
+@pytest.mark.parametrize("autotune,twisted", [(0, 1), (0, 0), (-(1 + 7 + 5), 0), (-(1 + 14 + 0), 0)])
+def test_overlapped_tensor_core_steps_equal_plain_order(autotune, twisted):
     """Programmatic dependent launch of the tensor-core steps (prologue and factor tiles of a
     step overlapping the end of the previous kernel) changes only the schedule: the sweeps
     are bit-identical to plain stream order and a whole solve agrees to rounding, for the
-    default shape, a cluster candidate and the 128-column shape."""
+    default shape, a cluster candidate and the 128-column shape of the line steps (block
+    Thomas), and for the grouped steps of the twisted strip solves."""
     k, n, N = 60.0, 256, 8
     rr = np.ascontiguousarray(hh_inputs.random_vector((n + 1) ** 2, 4, seed=13).ravel())
     src = hh_inputs.centre_source()
-    with hh.Handle(k, n, N, precision="fp32", autotune=autotune) as ho, \
-            hh.Handle(k, n, N, precision="fp32", autotune=autotune, overlap_steps=0) as hp:
+    with hh.Handle(k, n, N, precision="fp32", autotune=autotune, twisted=twisted) as ho, \
+            hh.Handle(k, n, N, precision="fp32", autotune=autotune, twisted=twisted, overlap_steps=0) as hp:
         for d in sweep.DIRECTIONS:
             assert np.array_equal(ho.apply_preconditioner(d, rr, 4), hp.apply_preconditioner(d, rr, 4)), d
         b = ho.assemble_rhs(src)
@@ -485,7 +492,8 @@ def test_overlapped_tensor_core_steps_equal_plain_order(autotune):
     assert ro.iterations == rp.iterations and rel(xo, xp) < 1e-12
 
 
-def test_tensor_map_cache_turnover():
+@pytest.mark.parametrize("twisted", [0, 1])
+def test_tensor_map_cache_turnover(twisted):
     """The tensor maps of the sweep arrays are cached in a ring keyed by (array, columns,
     tile shape); sweeps over many column counts on one handle turn the ring over several
     times, and every sweep still equals the oracle's (a step whose two maps were looked up
@@ -493,7 +501,7 @@ def test_tensor_map_cache_turnover():
     k, n, N = 20.0, 64, 4
     A, *_ = fem.global_system(k, n)
     sw = sweep.Sweeper(A, k, n, N, "LR")
-    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + 7 + 5)) as h:
+    with hh.Handle(k, n, N, precision="fp32", autotune=-(1 + 7 + 5), twisted=twisted) as h:
         for ncols in (2, 4, 6, 8, 10, 12, 14, 16, 2, 4):
             r = hh_inputs.random_vector(A.shape[0], ncols, seed=20 + ncols)
             z = h.apply_preconditioner("LR", np.ascontiguousarray(r.ravel()), ncols).reshape(ncols, -1)
@@ -549,7 +557,7 @@ def test_cyclic_reduction_depths(precision, k, n, N):
             rr = np.ascontiguousarray(r.ravel())
             for single in (0, 1):
                 with hh.Handle(k, n, N, precision=precision, bcr_depth=d, single_sweep=single) as hd, \
-                        hh.Handle(k, n, N, precision=precision, bcr_depth=0, single_sweep=single) as h0:
+                        hh.Handle(k, n, N, precision=precision, bcr_depth=0, twisted=0, single_sweep=single) as h0:
                     for dd in ("BT", "LR", "TB", "RL"):
                         zd = hd.apply_preconditioner(dd, rr, ncols).reshape(ncols, -1)
                         z0 = h0.apply_preconditioner(dd, rr, ncols).reshape(ncols, -1)
