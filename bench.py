@@ -387,7 +387,8 @@ def run_gpu(args, ws, rank, local):
             "share_of_step": (gsdot_ms or 0.0) * 2 * its * args.steps / step_total_ms if step_total_ms > 0 else None,
             "peak_src": "measured HBM copy bandwidth (MEASURED_PEAKS.json)",
             "note": "algorithmic bytes = 32 per node and basis vector (its eight digit planes in bf16) "
-                    "+ 64 t per node (the new columns' digit image), each read once; the FP64-pipe form "
+                    "+ 16 t per node (the new columns in FP64, sliced into digits inside the kernel; read "
+                    "once per plane, twice in all), each read once; the FP64-pipe form "
                     "of the same products ran at 1.1-1.4 TFLOP/s, bound by GB300's FP64 rate"}
         ranked = sorted([gemm_line, gsdot_line], key=lambda r: -(r["share_of_step"] or 0))
         dominant, others = ranked[0], ranked[1:]

@@ -206,8 +206,8 @@ typedef struct {
   int bcr_depth;            /* cyclic-reduction depth of the strip solves for the last column
                                count (fixed by opts.bcr_depth or autotuned) */
   double gsdot_bytes;       /* algorithmic bytes of the timed inner-product launches (the
-                               tensor-core form: the basis slice images and the new columns'
-                               image, read once) */
+                               tensor-core form: the basis slice images and the new columns,
+                               read once) */
   int twisted;              /* 1 when the strip solves of the last column count use the twisted
                                factorisation (opts.twisted) */
 } hh_stats;

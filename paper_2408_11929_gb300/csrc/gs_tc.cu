@@ -27,14 +27,16 @@
 //   NI  the "node image": for every 128-node tile, 4 KB = 128 rows (node) of 16 bf16 (plane c,
 //       digit i), K-major without swizzle: 8x8 core matrices, cores along K 128 B apart, 8-row
 //       groups 256 B apart.
-// Per pass: the new columns' image WI (B operand of the inner products: rows (b, part, digit j),
-// 64 nodes per 128-byte row, SW128), and the coefficient image CB of every basis vector (B
+// Per pass: the new columns' B operand of the inner products (rows (b, part, digit j), 64 nodes
+// per 128-byte row, SW128), formed in shared memory by the inner-product kernel from W itself,
+// and the coefficient image CB of every basis vector (B
 // operand of the update: rows (b, part, weight group w), K = (plane, digit i), value digit
 // w - i of G 2^{e_a} when 0 <= w - i < 8; pairs of weight group w >= 10, 2^-70 of the leading
 // pair and below, are dropped).
 //
 // Kernels: gst_dot_kernel (one CTA per SM, a contiguous node range each; stages of 128 nodes,
-// one 2 KB copy per basis vector; rows (vector, digit) of up to 8 tiles of 16 vectors in
+// one 2 KB copy per basis vector, the new columns' digits sliced from W by four warps of the
+// CTA; rows (vector, digit) of up to 8 tiles of 16 vectors in
 // tensor memory, read out every 1024 products and summed exactly in int64), gst_upd_kernel
 // (persistent over tiles of 384 nodes; per basis vector one 12 KB node-image copy and three
 // MMAs of M = 128 nodes, N = rows of CB, K = 16; accumulators read out after every 64
@@ -57,12 +59,15 @@ namespace hh {
 namespace gst {
 
 constexpr int SL = 8;          // digits per value
-constexpr int THREADS = 192;   // warp 0 producer, warp 1 MMA + tensor memory, warps 2-5 epilogue
+// inner products: warp 0 producer, warp 1 MMA + tensor memory, warps 2-5 epilogue, warps 6-9
+// slicer (the new columns' B operand, formed from W in shared memory)
+constexpr int THREADS = 320;
 constexpr int EPI_THREADS = 128;
+constexpr int SLICE_THREADS = 128;  // one node of the stage's 128 each
 // inner products
 constexpr int DOT_SC = 2;      // 64-node chunks per stage (one 2 KB copy per basis vector)
 constexpr int DOT_NA = 4;      // A ring: 32 KB tiles (16 vectors x 8 digits x 128 nodes)
-constexpr int DOT_NB = 3;      // B ring: two WI blocks per stage
+constexpr int DOT_NB = 3;      // B ring: the new columns' digits of a stage (two 64-node blocks)
 constexpr int DOT_FL = 16 / DOT_SC;  // stages per exact accumulation period (1024 products)
 constexpr int DOT_MAXT = 8;    // tiles per tensor-memory round (8 x 16 t columns <= 512)
 constexpr int ATILE = 16 * DOT_SC * 1024;
@@ -282,56 +287,6 @@ __global__ void __launch_bounds__(256) gst_wscan_kernel(KState S, const double2*
   }
 }
 
-// Slice image WI of the new columns: stage (plane c, chunk q of 64 nodes) holds rows
-// n = (2 b + part) 8 + j (digit j) of 64 bf16 each, 128-byte swizzled.  Plane 0 of part 0 /
-// part 1 holds Re w / Im w, plane 1 holds Im w / -Re w.  A CTA takes 256 nodes (four chunks):
-// the digits are placed in shared memory in the image's layout, then written out with 16-byte
-// stores (the four chunks of a plane are contiguous).  Grid (blocks over Dp / 256, slots).
-template <int TT>
-__global__ void __launch_bounds__(256) gst_wslice_kernel(KState S, const double2* __restrict__ W) {
-  const int r = blockIdx.y;
-  if (S.done[r]) return;
-  extern __shared__ __align__(16) unsigned char wsm[];  // [plane][4 chunks][BB]
-  const size_t D = S.D, chunks = (size_t)S.Dp / 64;
-  constexpr int BB = gst::dot_bbytes(TT);
-  const double2* Wr = W + (size_t)r * TT * D;
-  unsigned char* WI = S.WI + (size_t)r * 64 * TT * S.Dp;
-  int e[TT];
-#pragma unroll
-  for (int b = 0; b < TT; ++b) e[b] = gst::frexp_exp_bits(S.wmaxb[(size_t)r * TT + b]);
-  for (size_t g0 = (size_t)blockIdx.x * 256; g0 < (size_t)S.Dp; g0 += (size_t)gridDim.x * 256) {
-    const size_t g = g0 + threadIdx.x;
-    const int kk = threadIdx.x & 63, qq = threadIdx.x >> 6;
-    unsigned char* blk0 = wsm + (size_t)qq * BB;
-    unsigned char* blk1 = wsm + (size_t)(4 + qq) * BB;
-#pragma unroll
-    for (int b = 0; b < TT; ++b) {
-      const double2 w = (g < D && e[b] != 0x7FFFFFFF) ? Wr[b * D + g] : make_double2(0, 0);
-      int dr[gst::SL], di[gst::SL];
-      gst::digits8(w.x, e[b], dr);
-      gst::digits8(w.y, e[b], di);
-#pragma unroll
-      for (int j = 0; j < gst::SL; ++j) {
-        const int n0 = (2 * b) * 8 + j, n1 = n0 + 8;  // part 0, part 1 (n & 7 = j)
-        const int col = ((((kk >> 3) ^ j)) << 4) + (kk & 7) * 2;
-        *reinterpret_cast<__nv_bfloat16*>(blk0 + n0 * 128 + col) = __float2bfloat16_rn((float)dr[j]);
-        *reinterpret_cast<__nv_bfloat16*>(blk0 + n1 * 128 + col) = __float2bfloat16_rn((float)di[j]);
-        *reinterpret_cast<__nv_bfloat16*>(blk1 + n0 * 128 + col) = __float2bfloat16_rn((float)di[j]);
-        *reinterpret_cast<__nv_bfloat16*>(blk1 + n1 * 128 + col) = __float2bfloat16_rn((float)-dr[j]);
-      }
-    }
-    __syncthreads();
-    const size_t q0 = g0 / 64;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      uint4* dst = reinterpret_cast<uint4*>(WI + ((size_t)c * chunks + q0) * BB);
-      const uint4* src = reinterpret_cast<const uint4*>(wsm + (size_t)c * 4 * BB);
-      for (int q = threadIdx.x; q < 4 * BB / 16; q += 256) dst[q] = src[q];
-    }
-    __syncthreads();
-  }
-}
-
 // Coefficient images CB of this pass's H (one CTA per slot): per new column b the exponent E_b
 // with max_a |h_ab 2^{e_a}| < 2^{E_b} (a scale per output column keeps each column's update
 // relative to its own coefficients), then for every basis vector a the rows
@@ -458,7 +413,8 @@ __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
 // H partials of this pass: CTA x of slot r takes stages [s0, s1) of the 2 Dp / 64 (plane, node
 // chunk) stages and writes <v_a, w_b> over its nodes to Hpart[((r maxV + a) t + b) GX + x].
 template <int TT>
-__global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, int* err, long long budget) {
+__global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, const double2* __restrict__ W, int* err,
+                                                                  long long budget) {
   using namespace gst;
   constexpr int N = 16 * TT, BB = dot_bbytes(TT), NCOL = 2 * TT;
   constexpr uint32_t IDESC =
@@ -506,29 +462,16 @@ __global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, int*
   const int s0 = min(NST, (int)blockIdx.x * per), s1 = min(NST, s0 + per), ns = s1 - s0;
   const int nT = (p + 15) / 16, rounds = (nT + DOT_MAXT - 1) / DOT_MAXT;
   unsigned char* const* vs = S.VSptr + (size_t)r * S.maxV;
-  const unsigned char* WI = S.WI + (size_t)r * 64 * TT * S.Dp;
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     // lane 0 waits for the ring slot and posts the byte count; lane v then issues the copy of
     // vector v of the tile (16 copies in parallel instead of one after another)
-    int ka = 0, kb = 0;
+    int ka = 0;
     bool ok = true;
     for (int rd = 0; rd < rounds && ok; ++rd) {
       const int T0 = rd * DOT_MAXT, nt = min(DOT_MAXT, nT - T0);
       for (int s = s0; s < s1 && ok; ++s) {
-        if (lane == 0) {
-          const int slot = kb % DOT_NB;
-          if (kb >= DOT_NB && !mbar_wait(&empty_b[slot], ((unsigned)(kb / DOT_NB) & 1u) ^ 1u, err, budget)) ok = false;
-          if (tc::aborted(&abort_s)) ok = false;
-          if (ok) {
-            mbar_expect_tx(&full_b[slot], DOT_SC * BB);
-            bulk_g2s(sb + slot * DOT_SC * BB, WI + (size_t)s * DOT_SC * BB, DOT_SC * BB, &full_b[slot]);
-          }
-        }
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-        if (!ok) break;
-        ++kb;
         for (int T = 0; T < nt; ++T) {
           const int slot = ka % DOT_NA;
           const int v0 = (T0 + T) * 16, nv = min(16, p - v0);
@@ -553,8 +496,6 @@ __global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, int*
       // let the copies in flight land before the CTA leaves
       for (int k = max(0, ka - DOT_NA); k < ka; ++k)
         mbar_wait(&full_a[k % DOT_NA], (unsigned)(k / DOT_NA) & 1u, err, budget);
-      for (int k = max(0, kb - DOT_NB); k < kb; ++k)
-        mbar_wait(&full_b[k % DOT_NB], (unsigned)(k / DOT_NB) & 1u, err, budget);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
@@ -579,7 +520,7 @@ __global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, int*
             if (tc::aborted(&abort_s)) { ok = false; break; }
             tc::fence_after();
             // A: vector v's DOT_SC 1 KB atoms at v DOT_SC KB (8-row groups DOT_SC KB apart);
-            // B: the stage's DOT_SC WI blocks one after the other
+            // B: the stage's DOT_SC blocks of the new columns' digits one after the other
             const uint32_t a0 = smem_u32(sa + slot * ATILE), b0 = smem_u32(sb + bslot * DOT_SC * BB);
 #pragma unroll
             for (int k = 0; k < DOT_SC; ++k)
@@ -603,7 +544,7 @@ __global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, int*
       tc::commit(fin);  // arrives once every MMA issued above has completed
       mbar_wait(fin, 0, err, budget);
     }
-  } else {
+  } else if (warp < 2 + EPI_THREADS / 32) {
     // ---------------------------------------------------------------- epilogue
     // Exact integer accumulation: a flush holds, in this thread's lane (vector a, digit i), the
     // sums acc_j (|acc_j| < 2^24, exact in FP32) for every column b' and digit j.  They are
@@ -707,6 +648,77 @@ __global__ void __launch_bounds__(gst::THREADS, 1) gst_dot_kernel(KState S, int*
         S.Hpart[((size_t)(r * S.maxV + a) * TT + b) * S.GX + blockIdx.x] = h;
       }
       epi_sync();
+    }
+  } else {
+    // ---------------------------------------------------------------- slicer
+    // The B operand of every stage (plane c, the 128 nodes from g0), formed here from W instead
+    // of a stored image: thread i takes node g0 + i and, for every new column b, the eight
+    // digits of Re w_b and Im w_b relative to 2^{f_b} (f_b from the column maxima); plane 0
+    // gives rows (2b, j) = Re, (2b + 1, j) = Im, plane 1 rows (2b, j) = Im, (2b + 1, j) = -Re,
+    // 128-byte swizzled as the MMA reads them.  The next stage's entries of W are requested
+    // before this stage is sliced.
+    const int i = threadIdx.x - (2 + EPI_THREADS / 32) * 32;
+    const int kk = i & 63, qq = i >> 6;
+    const int chunks = S.Dp / 64;  // a multiple of DOT_SC: no stage straddles the two planes
+    const size_t D = S.D;
+    const double2* Wr = W + (size_t)r * TT * D;
+    int fe[TT];
+#pragma unroll
+    for (int b = 0; b < TT; ++b) fe[b] = frexp_exp_bits(S.wmaxb[(size_t)r * TT + b]);
+    auto fetch = [&](int s, double2 (&w)[TT]) {
+      const size_t g = (size_t)((s * DOT_SC) % chunks) * 64 + i;
+#pragma unroll
+      for (int b = 0; b < TT; ++b) w[b] = (g < D && fe[b] != 0x7FFFFFFF) ? Wr[b * D + g] : make_double2(0, 0);
+    };
+    double2 cur[TT], nxt[TT];
+    if (ns > 0) fetch(s0, cur);
+    int kb = 0;
+    bool stop = false;
+    for (int rd = 0; rd < rounds && !stop; ++rd) {
+      for (int s = s0; s < s1; ++s) {
+        fetch(s + 1 < s1 ? s + 1 : s0, nxt);  // after the last stage: the next round's first
+        const int slot = kb % DOT_NB;
+        const int bad =
+            ((kb >= DOT_NB && !mbar_wait(&empty_b[slot], ((unsigned)(kb / DOT_NB) & 1u) ^ 1u, err, budget)) ||
+             tc::aborted(&abort_s))
+                ? 1
+                : 0;
+        // the slicers decide together, so that all of them meet at the barrier below
+        int any_bad;
+        asm volatile(
+            "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 2, %2, q;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(any_bad)
+            : "r"(bad), "n"(SLICE_THREADS)
+            : "memory");
+        if (any_bad) {
+          *(volatile int*)&abort_s = 1;
+          stop = true;
+          break;
+        }
+        const bool im_plane = (s * DOT_SC) / chunks != 0;
+        unsigned char* blk = sb + slot * DOT_SC * BB + qq * BB;
+#pragma unroll
+        for (int b = 0; b < TT; ++b) {
+          int dr[SL], di[SL];
+          digits8(cur[b].x, fe[b], dr);
+          digits8(cur[b].y, fe[b], di);
+#pragma unroll
+          for (int j = 0; j < SL; ++j) {
+            const int n0 = (2 * b) * 8 + j, n1 = n0 + 8;
+            const int col = (((kk >> 3) ^ j) << 4) + (kk & 7) * 2;
+            const int v0 = im_plane ? di[j] : dr[j], v1 = im_plane ? -dr[j] : di[j];
+            *reinterpret_cast<__nv_bfloat16*>(blk + n0 * 128 + col) = __float2bfloat16_rn((float)v0);
+            *reinterpret_cast<__nv_bfloat16*>(blk + n1 * 128 + col) = __float2bfloat16_rn((float)v1);
+          }
+        }
+        fence_proxy_async_smem();  // the tensor cores read the tile through the async proxy
+        asm volatile("bar.sync 2, %0;" ::"n"(SLICE_THREADS) : "memory");
+        if (i == 0) mbar_arrive(&full_b[slot]);
+        ++kb;
+#pragma unroll
+        for (int b = 0; b < TT; ++b) cur[b] = nxt[b];
+      }
     }
   }
   tc::fence_before();
@@ -924,9 +936,6 @@ static cudaError_t set_attrs_t() {
   cudaError_t e = cudaFuncSetAttribute((const void*)gst_dot_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)gst::dot_smem(TT));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)gst_wslice_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             8 * gst::dot_bbytes(TT));
-  if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)gst_upd_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)gst::upd_smem(TT));
   return e;
@@ -962,13 +971,10 @@ static void prep_w_t(Engine& E, const KState& K, int S, const double2* W, bool f
     gst_wscan_kernel<TT><<<dim3(K.GX, S), 256, 0, E.stream>>>(K, W, 1);
     E.count_launch(1);
   }
-  const int gs = std::max(1, std::min(E.num_sms * 4 / std::max(1, S), K.Dp / 256));
-  gst_wslice_kernel<TT><<<dim3(gs, S), 256, 8 * gst::dot_bbytes(TT), E.stream>>>(K, W);
-  E.count_launch(1);
 }
 template <int TT>
-static void dot_t(Engine& E, const KState& K, int S, int gd) {
-  gst_dot_kernel<TT><<<dim3(gd, S), gst::THREADS, gst::dot_smem(TT), E.stream>>>(K, E.err, E.opts.timeout_cycles);
+static void dot_t(Engine& E, const KState& K, int S, const double2* W, int gd) {
+  gst_dot_kernel<TT><<<dim3(gd, S), gst::THREADS, gst::dot_smem(TT), E.stream>>>(K, W, E.err, E.opts.timeout_cycles);
   E.count_launch(1);
 }
 
@@ -989,8 +995,8 @@ int gst_upd_ctas(const Engine& E, const KState& K, int S) {
   return std::max(1, std::min(E.num_sms / std::max(1, S), K.Dp / gst::UPD_NODES));
 }
 
-// First part of a Gram-Schmidt pass: (first pass) the new columns' maxima and the deflation
-// reference, then their slice image.
+// First part of a Gram-Schmidt pass (the first pass only): the new columns' maxima and the
+// deflation reference.
 void gst_prepare_columns(Engine& E, const KState& K, int S, const double2* W, bool first) {
   switch (K.t) {
     case 1: prep_w_t<1>(E, K, S, W, first); break;
@@ -1000,14 +1006,15 @@ void gst_prepare_columns(Engine& E, const KState& K, int S, const double2* W, bo
   }
 }
 
-// Second part: the inner-product partials (gst_dot_ctas CTAs per slot).
-void gst_inner_products(Engine& E, const KState& K, int S) {
+// Second part: the inner-product partials (gst_dot_ctas CTAs per slot), the new columns sliced
+// from W inside the kernel.
+void gst_inner_products(Engine& E, const KState& K, int S, const double2* W) {
   const int gd = gst_dot_ctas(E, K, S);
   switch (K.t) {
-    case 1: dot_t<1>(E, K, S, gd); break;
-    case 2: dot_t<2>(E, K, S, gd); break;
-    case 3: dot_t<3>(E, K, S, gd); break;
-    default: dot_t<4>(E, K, S, gd); break;
+    case 1: dot_t<1>(E, K, S, W, gd); break;
+    case 2: dot_t<2>(E, K, S, W, gd); break;
+    case 3: dot_t<3>(E, K, S, W, gd); break;
+    default: dot_t<4>(E, K, S, W, gd); break;
   }
 }
 
@@ -1022,10 +1029,8 @@ void gst_pass_update(Engine& E, const KState& K, int S, double2* W, bool track_m
   }
 }
 
-// bytes of the slice images of one basis vector, of a slot's new-column image, of a slot's
-// coefficient images
+// bytes of the slice images of one basis vector, of a slot's coefficient images
 size_t gst_vector_bytes(size_t Dp) { return 64 * Dp; }
-size_t gst_wimage_bytes(size_t Dp, int t) { return 64 * (size_t)t * Dp; }
 size_t gst_cimage_bytes(int maxV, int t) { return (size_t)maxV * gst::nu_rows(t) * 32; }
 int gst_nu_rows(int t) { return gst::nu_rows(t); }
 

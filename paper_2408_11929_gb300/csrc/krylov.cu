@@ -30,11 +30,10 @@ void launch_unpack(Engine& E, const void* X, int C, int t, int4 codes, double2* 
 cudaError_t gst_set_attributes(int t);
 void gst_slice_basis(Engine& E, const KState& K, int S, int mode);
 void gst_prepare_columns(Engine& E, const KState& K, int S, const double2* W, bool first);
-void gst_inner_products(Engine& E, const KState& K, int S);
+void gst_inner_products(Engine& E, const KState& K, int S, const double2* W);
 void gst_pass_update(Engine& E, const KState& K, int S, double2* W, bool track_max);
 int gst_dot_ctas(const Engine& E, const KState& K, int S);
 size_t gst_vector_bytes(size_t Dp);
-size_t gst_wimage_bytes(size_t Dp, int t);
 size_t gst_cimage_bytes(int maxV, int t);
 int gst_nu_rows(int t);
 
@@ -1190,11 +1189,10 @@ struct SlotSolver::Impl {
       K.vnew1 = dev<int>(S);
       K.vmaxb = dev<unsigned long long>((size_t)S * t);
       K.wmaxb = dev<unsigned long long>((size_t)S * t);
-      K.WI = dev<unsigned char>((size_t)S * gst_wimage_bytes(K.Dp, t));
       K.CB = dev<unsigned char>((size_t)S * gst_cimage_bytes(K.maxV, t));
       K.cexp = dev<int>((size_t)S * t);
       h_vscur = host<unsigned char*>(S);
-      if (!K.VSptr || !K.V0S || !K.WI || !K.CB || !K.cexp || !h_vscur) return HH_ENOMEM;
+      if (!K.VSptr || !K.V0S || !K.CB || !K.cexp || !h_vscur) return HH_ENOMEM;
     } else {
       K.Wp = dev<double>((size_t)S * t * 3 * D);
       if (!K.Wp) return HH_ENOMEM;
@@ -1283,11 +1281,11 @@ struct SlotSolver::Impl {
       for (int pass = 0; pass < K.passes; ++pass) {
         gst_prepare_columns(E, K, S, W, pass == 0);
         if (tick) E.tick_begin(Engine::K_GSDOT);
-        gst_inner_products(E, K, S);
-        // algorithmic: the basis slice images (32 bytes per node and vector) and the new
-        // columns' image (64 t bytes per node), each read once; one complex multiply-add per
-        // basis element and new column
-        if (tick) E.tick_end(Engine::K_GSDOT, nv * (double)K.Dp * 32.0 + (double)t * K.Dp * 64.0, 8.0 * nv * t * D);
+        gst_inner_products(E, K, S, W);
+        // algorithmic: the basis slice images (32 bytes per node and vector) and the new columns
+        // (16 t bytes per node, sliced inside the kernel), each read once; one complex
+        // multiply-add per basis element and new column
+        if (tick) E.tick_end(Engine::K_GSDOT, nv * (double)K.Dp * 32.0 + (double)t * D * 16.0, 8.0 * nv * t * D);
         gs_reduce_kernel<<<dim3((K.maxV * t + 7) / 8, S), 256, 0, E.stream>>>(K, pass == 0, gst_dot_ctas(E, K, S));
         E.count_launch();
         gst_pass_update(E, K, S, W, pass + 1 < K.passes);
@@ -1729,7 +1727,7 @@ static int gs_pass_t(Engine& E, KState& K, double2* W, unsigned char* tmp_slices
       cudaStreamSynchronize(E.stream);  // range lives on this stack frame
     }
     gst_prepare_columns(E, K, 1, W, true);
-    gst_inner_products(E, K, 1);
+    gst_inner_products(E, K, 1, W);
     gs_reduce_kernel<<<dim3((K.maxV * TT + 7) / 8, 1), 256, 0, E.stream>>>(K, 1, gst_dot_ctas(E, K, 1));
     gst_pass_update(E, K, 1, W, false);
   } else {
@@ -1787,11 +1785,10 @@ int gram_schmidt_pass(Engine& E, int p, const double2* V, int t, double2* W, dou
     K.vnew1 = (int*)dev(sizeof(int));
     K.vmaxb = (unsigned long long*)dev(sizeof(unsigned long long) * t);
     K.wmaxb = (unsigned long long*)dev(sizeof(unsigned long long) * t);
-    K.WI = (unsigned char*)dev(gst_wimage_bytes(K.Dp, t));
     K.CB = (unsigned char*)dev(gst_cimage_bytes(p, t));
     K.cexp = (int*)dev(sizeof(int) * t);
     slices = (unsigned char*)dev((size_t)p * gst_vector_bytes(K.Dp));
-    if (!slices || !K.CB || !K.WI) return HH_ENOMEM;
+    if (!slices || !K.CB) return HH_ENOMEM;
   } else {
     K.Wp = (double*)dev(sizeof(double) * t * 3 * D);
     if (!K.Wp) return HH_ENOMEM;

@@ -39,7 +39,6 @@ struct KState {
   int *vnew0, *vnew1;      // per slot: basis vectors [vnew0, vnew1) still to be sliced
   unsigned long long* vmaxb;  // per slot, vector of the block: bits of max |entry|
   unsigned long long* wmaxb;  // per slot, new column: bits of max |entry|
-  unsigned char* WI;       // per slot: slice image of the new columns (64 t Dp bytes)
   unsigned char* CB;       // per slot, basis vector a: coefficient image (NU x 32 bytes)
   int* cexp;               // per slot, new column: exponent of its coefficient images
 };

@@ -106,11 +106,11 @@ struct hh_server {
     const size_t sweep = 3 * (R + 1) * m * N * C * elem + 10 * m * N * C * elem;
     const size_t D = m * m;
     // per slot: t-column W and its three planes, b, staging x, and 2 t basis / search vectors
-    // per iteration up to the cap; with the tensor-core Gram-Schmidt no planes, but the new
-    // columns' slice image (64 t bytes per node) and 64 bytes per node for every basis vector
+    // per iteration up to the cap; with the tensor-core Gram-Schmidt no planes, but 64 bytes
+    // per node for every basis vector's slice images
     const size_t iters = (size_t)opts.maxit * t;
     const size_t krylov =
-        opts.gs_tensor ? (size_t)opts.serve_slots * (D * 8 * (2 * t + 4 + 4 * iters) + 64 * D * (t + 1 + iters))
+        opts.gs_tensor ? (size_t)opts.serve_slots * (D * 8 * (2 * t + 4 + 4 * iters) + 64 * D * (1 + iters))
                        : (size_t)opts.serve_slots * D * 8 * (2 * t + 3 * t + 4 + 4 * iters);
     return factors + sweep + krylov + (64u << 20);
   }
