@@ -352,7 +352,11 @@ std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form,
     return t;
   };
   const int FG = R + 1, FK = R + 2;
-  // F2
+  // F2.  With the twisted strip solves and R even, the top chain is one step longer than the
+  // bottom one: line R-1, all the scan reads, is final a step before line 0, so the first scan
+  // step joins that last step of F1 (two tasks on disjoint lines) instead of following it.
+  const bool join_first = twisted && bd.LF > 0 && !prog.empty() && prog.back().kind == PH_GROUP &&
+                          prog.back().tasks.size() == 1 && prog.back().tasks[0].out_line == 0 && R - 1 > 1;
   int src_arr = SB_V, src_line = R - 1;
   for (int l = 0; l < bd.LF; ++l) {
     SweepPhase p;
@@ -360,7 +364,8 @@ std::vector<SweepPhase> build_program(int n, int N, bool double_sweep, int form,
     const int dst = (l & 1) ? SB_T1 : SB_T0;
     p.tasks.push_back(task1(l == 0 ? FG : bd.iGp + l - 1, src_arr, src_line, -(1 << l), l == 0 ? 1 : 0, dst, 0,
                             src_arr, src_line, OUT_SET, 0, N - 1));
-    prog.push_back(p);
+    if (l == 0 && join_first) prog.back().tasks.push_back(p.tasks[0]);
+    else prog.push_back(p);
     src_arr = dst;
     src_line = 0;
   }
