@@ -76,7 +76,9 @@ typedef struct {
                              block Thomas on the reduced system of R / 2^d lines, 2d + 2R/2^d + 1
                              dependent steps, every level one grouped step over its lines and all
                              strips; -1: the blocks of every usable depth are stored and the
-                             fastest depth is picked by timing whole sweeps, per column count */
+                             fastest depth is picked by timing whole sweeps, per column count
+                             (together with the twisted strip solves when they are stored, see
+                             twisted); a fixed depth d >= 1 takes precedence over twisted */
   int64_t timeout_cycles; /* SM clock budget of every device-side wait (default 4e9) */
   void* stream;           /* cudaStream_t to run on, or NULL for the handle's own stream */
   int use_graph;          /* 1 (default): every Arnoldi step (table gather, pack, the sweep's
@@ -139,9 +141,11 @@ typedef struct {
                              overlapping by 2h that exchange Robin data, every node taking the most
                              recent subdomain solve; FP64 only (HH_PREC_FP64), sweeps on the CUDA cores */
   int group_wide_tiles;   /* complex64 tensor-core sweeps: 1 (default): a grouped step whose tasks are
-                             wider than 64 columns and at most 128 (the one-shot corrections of
-                             interface form 1 at one right-hand side) runs with 128-column tiles,
-                             reading each factor tile once; 0: the autotuned line-step shape */
+                             wider than 64 columns and at most 128 and whose tiles fill the SMs
+                             without a K split (the one-shot corrections of interface form 1 at
+                             one right-hand side) runs with 128-column tiles, reading each factor
+                             tile once, and a step whose tasks are all within 32 columns with
+                             32-column tiles; 0: the autotuned line-step shape */
   int gs_tensor;          /* 1 (default): the inner products and updates of Gram-Schmidt against the
                              basis run on the tensor cores as exact integer products of 7-bit slices
                              of the FP64 data (FP64-accurate; about 64 more bytes of device memory
